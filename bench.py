@@ -1,0 +1,430 @@
+"""Benchmark: de-cluttering iterations per second on one GB300 (per rank).
+
+Workload: 1,000,000 float32 samples from a mixture of 20 Gaussians plus 10 %
+uniform background, 512x512 grid, Gaussian radius r = 4, 8 iterations of the
+method (Sec. 4.3) per step.  One step = one ``regularize(8)`` call through the
+C ABI on a fresh copy of the input positions resident in HBM; L2 is flushed
+(a 256 MB write) between timed steps.  Metric: Mpoints*iter/s =
+samples x iterations / step time, summed over ranks (each rank regularises its
+own scatterplot: independent problems, no collective in the data path).
+
+Also reported on the same JSON line:
+  e2e          -- the same metric through regularize_host(): pinned host
+                  samples copied in and out inside the timed region;
+  roofline     -- the dominant kernel's algorithmic bytes per launch over its
+                  CUDA-event duration, against the measured HBM copy peak;
+  cpu_baseline -- the CPU oracle timed on this host on a bounded sample;
+  clocks       -- nvidia-smi samples taken during the timed region.
+
+``--impl reference`` times the CPU oracle (the reference arm) instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="gmm20_512", n=1_000_000, log2_res=9, kernel_r=4, iters=8)
+METRIC = "Mpoints·iter/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_config():
+    return {
+        "workload": "gmm20_512: 1M samples (20 Gaussians + 10% uniform), 512x512 grid, r=4, 8 iterations",
+        "samples": WORKLOAD["n"],
+        "grid": 1 << WORKLOAD["log2_res"],
+        "iterations": WORKLOAD["iters"],
+        "kernel_r": WORKLOAD["kernel_r"],
+        "l2": "flushed between steps (256 MB write)",
+    }
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as tdist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        tdist.init_process_group(backend=backend)
+        pg = tdist
+    return world, rank, local, pg
+
+
+def max_over_ranks(pg, value: float, device=None) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap,utilization.gpu")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        def f(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        loaded = [s for s in self.samples if (f(s[7]) or 0) > 0] or self.samples
+        sm = [f(s[0]) for s in loaded if f(s[0]) is not None]
+        mx = [f(s[1]) for s in loaded if f(s[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in loaded for k in range(4) if s[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(loaded)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per launch (see the design notes for the derivation)
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(kind: str, n: int, N: int, info) -> float:
+    NN = N * N
+    T, nb = info.band_rows, info.n_bands
+    agg = nb * (3 * N + 2 * T + 1) * 4
+    carry = (nb + 1) * 5 * N * 4
+    table = {
+        "splat": 8.0 * n,                       # read the samples (atomics are the bound)
+        "smooth": 8.0 * NN,                     # read counts, write d_r
+        "band_aggregate": 4.0 * NN + agg,       # read d_r, write the compact aggregates
+        "band_carry": agg + carry,              # read aggregates, write carries
+        "band_final": 12.0 * NN,                # read d_r, write the float2 displacement
+        "advect": 16.0 * n,                     # read + write the samples
+        "quality": 4.0 * NN,
+        "memset": 4.0 * NN,
+    }
+    return table[kind]
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2408_06513_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("csrc_sha") != csrc_digest():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------
+
+def time_oracle(z, iters: int, budget_s: float, min_steps: int = 1):
+    """Run the oracle's iterations on ``z`` repeatedly for about ``budget_s``;
+    returns (Mpoints*iter/s, seconds per step, steps, cores)."""
+    import oracle
+    oracle.build()
+    p = oracle.Params(log2_res=WORKLOAD["log2_res"], kernel_r=WORKLOAD["kernel_r"])
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        cur = z
+        for _ in range(iters):
+            cur = oracle.iterate(cur, p)
+        steps += 1
+        el = time.perf_counter() - t0
+        if steps >= min_steps and el >= budget_s:
+            break
+    per = el / steps
+    return z.shape[0] * iters / per / 1e6, per, steps, oracle.max_threads()
+
+
+def oracle_sample_size(z_full, iters, target_step_s):
+    """Number of samples whose oracle step takes about target_step_s."""
+    import oracle
+    oracle.build()
+    p = oracle.Params(log2_res=WORKLOAD["log2_res"], kernel_r=WORKLOAD["kernel_r"])
+    probe = z_full[: min(len(z_full), 200_000)]
+    t0 = time.perf_counter()
+    oracle.iterate(probe, p)
+    t_iter = time.perf_counter() - t0
+    # the grid part does not shrink with n; scale the sample part only
+    est_full = t_iter * (len(z_full) / len(probe)) * iters
+    if est_full <= target_step_s:
+        return len(z_full)
+    return max(10_000, int(len(z_full) * target_step_s / est_full))
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import synth
+    z_full, _ = synth.gmm20(WORKLOAD["n"])
+    iters = WORKLOAD["iters"]
+    total_steps = args.steps + args.warmup
+    n_s = oracle_sample_size(z_full, iters, target_step_s=max(0.5, 150.0 / max(total_steps, 1)))
+    z = np.ascontiguousarray(z_full[:n_s])
+    import oracle
+    p = oracle.Params(log2_res=WORKLOAD["log2_res"], kernel_r=WORKLOAD["kernel_r"])
+    for _ in range(args.warmup):
+        cur = z
+        for _ in range(iters):
+            cur = oracle.iterate(cur, p)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cur = z
+        for _ in range(iters):
+            cur = oracle.iterate(cur, p)
+        times.append(time.perf_counter() - t0)
+    per = sum(times) / len(times)
+    value = n_s * iters / per / 1e6
+    sample = f"first {n_s} of the 1M samples, 512x512, r=4, 8 iterations per step"
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, world, rank, local, pg):
+    import torch
+
+    import synth
+    from paper_2408_06513_gb300 import build as dc_build
+    from paper_2408_06513_gb300 import declutter as dc
+
+    dc_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    n, k, r, iters = WORKLOAD["n"], WORKLOAD["log2_res"], WORKLOAD["kernel_r"], WORKLOAD["iters"]
+    N = 1 << k
+    z, _ = synth.gmm20(n, seed=2 + rank)
+    ctx = dc.declutter_create(k, kernel_r=r, device=local, stream=stream)
+    info = dc.declutter_get_info(ctx)
+    src = torch.from_numpy(z).to(dev)
+    pos = torch.empty_like(src)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def reset_and_flush():
+        with torch.cuda.stream(stream):
+            pos.copy_(src)
+            flush.fill_(1.0)
+
+    # warm-up (also captures the graph)
+    for _ in range(args.warmup):
+        reset_and_flush()
+        dc.regularize(ctx, pos, iters)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.2)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(pg)
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        reset_and_flush()
+        starts[s].record(stream)
+        dc.regularize(ctx, pos, iters)
+        ends[s].record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    ms_max = max_over_ranks(pg, ms, dev if pg is not None and torch.distributed.get_backend() == "nccl" else None)
+    dc.declutter_sync(ctx)
+
+    # end-to-end through host buffers (pinned), copies inside the timed region
+    host = torch.from_numpy(z.copy()).pin_memory()
+    e2e_times = []
+    for s in range(args.warmup + args.steps):
+        host.numpy()[:] = z
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dc.regularize_host(ctx, host, iters)
+        t1 = time.perf_counter()
+        if s >= args.warmup:
+            e2e_times.append(t1 - t0)
+    clocks.stop()
+    e2e_s = max_over_ranks(pg, sum(e2e_times) / len(e2e_times),
+                           dev if pg is not None and torch.distributed.get_backend() == "nccl" else None)
+
+    # per-kernel device times: the same kernels and launch shapes, one event
+    # pair around each launch (declutter_profile_regularize)
+    prof_steps = max(1, min(args.steps, 5))
+    tot = {}
+    for _ in range(prof_steps):
+        reset_and_flush()
+        torch.cuda.synchronize()
+        prof = dc.declutter_profile_regularize(ctx, pos, iters)
+        for kname, v in prof.items():
+            t = tot.setdefault(kname, {"ms": 0.0, "launches": 0})
+            t["ms"] += v["ms"]
+            t["launches"] += v["launches"]
+    kernels = {}
+    for kname, v in tot.items():
+        if v["launches"] == 0 or kname == "memset":
+            continue
+        avg_ms = v["ms"] / v["launches"]
+        by = algorithmic_bytes(kname, n, N, info)
+        kernels[kname] = {"avg_us": avg_ms * 1e3, "launches_per_step": v["launches"] // prof_steps,
+                          "GBps": by / (avg_ms * 1e-3) / 1e9}
+    dominant = max(kernels, key=lambda kk: kernels[kk]["avg_us"] * kernels[kk]["launches_per_step"])
+    peaks, peak_src = measured_peaks()
+    dk = kernels[dominant]
+    achieved = dk["GBps"]
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_src,
+                "traffic": ncu_traffic(dominant),
+                "algorithmic_bytes_per_launch": algorithmic_bytes(dominant, n, N, info)}
+
+    launches_per_step = iters * info.kernels_per_iter
+    value = world * n * iters / (ms_max * 1e-3) / 1e6
+    e2e_value = world * n * iters / e2e_s / 1e6
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_s = oracle_sample_size(z, iters, target_step_s=3.0)
+        v, per, steps, cores = time_oracle(np.ascontiguousarray(z[:n_s]), iters, budget_s=args.cpu_budget)
+        cpu = {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
+               "sample": f"{steps} step(s) of 8 iterations on the first {n_s} samples, 512x512, r=4"}
+
+    dc.declutter_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(),
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline,
+            "kernels": kernels,
+            "cpu_baseline": cpu,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local, pg = dist_init()
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_gpu(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

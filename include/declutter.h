@@ -1,0 +1,205 @@
+/*
+ * declutter.h -- C ABI of the GB300 (sm_103a) implementation of one
+ * de-cluttering iteration from Rave, Molchanov and Linsen, "De-cluttering
+ * Scatterplots with Integral Images" (arXiv 2408.06513):
+ *
+ *   (a) splat the n samples into a 2^k x 2^k count grid and smooth it
+ *       (Sec. 4.1, Sec. 4.3 step 1),
+ *   (b) build the axis-aligned and 45-degree tilted integral images of the
+ *       density (Sec. 3.1, Sec. 4.3 step 2),
+ *   (c) evaluate the defect-corrected per-pixel displacement of eq. (map_res)
+ *       built on eq. (map) (Sec. 3.2, Sec. 4.2),
+ *   (d) move every sample by bilinear interpolation of that field
+ *       (Sec. 4.2, Sec. 4.3 step 3),
+ * repeated for a number of iterations (Sec. 4.3 step 4).
+ *
+ * Conventions used by every call.
+ *   - Grid resolution N = 2^log2_res, 16 <= N <= 8192.  Pixel (i, j): i is
+ *     the column (x), j the row (y, pointing down), origin top-left
+ *     (Sec. 4.1).  Every grid is row-major: element (i, j) at j * N + i.
+ *   - Samples are float32 pairs (x, y) in the unit square (Sec. 4.1),
+ *     interleaved: pos_xy[2p] = x_p, pos_xy[2p + 1] = y_p.  A sample splats
+ *     to pixel (floor(x N), floor(y N)) after clamping x and y to [0, 1]
+ *     (NaN counts as 0); the index N is clamped to N - 1.
+ *   - Pixel (i, j) sits at (i, j) / N (Sec. 3.2, text under eq. (map)), or at
+ *     (i + 1/2, j + 1/2) / N when dc_params.pixel_center is set.
+ *   - Displacements are in domain units (multiply by N for pixels).
+ *
+ * Memory and ownership.
+ *   - Every pointer argument named *_out, pos_xy or grid is a DEVICE pointer
+ *     owned by the caller (for instance the data pointer of a CUDA tensor),
+ *     except where a comment says "host".  Device arrays of samples must be
+ *     8-byte aligned; grids must be 16-byte aligned.
+ *   - The context owns its internal grids (counts, density, displacement,
+ *     band aggregates and carries), allocated once by declutter_create.
+ *   - All calls are asynchronous on the context's stream unless stated.
+ *
+ * Errors.
+ *   - Every call returns a dc_status; nothing throws or aborts across the
+ *     ABI.  declutter_last_error() gives a message for the last failure of
+ *     the calling thread.
+ *   - Kernels report device-side problems in a sticky status word;
+ *     declutter_sync() waits for the stream and returns it.
+ *   - There is no CPU path: without a usable CUDA device every call that
+ *     needs one fails with DC_ERR_CUDA.
+ */
+#ifndef DECLUTTER_H
+#define DECLUTTER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dc_ctx dc_ctx;
+
+typedef enum {
+    DC_OK = 0,
+    DC_ERR_INVALID_ARG = 1, /* null or misaligned pointer, bad size or parameter */
+    DC_ERR_NOT_POW2 = 2,    /* resolution outside 2^4 .. 2^13 */
+    DC_ERR_OOM = 3,         /* device allocation failed */
+    DC_ERR_CUDA = 4,        /* a CUDA runtime call or launch failed */
+    DC_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired */
+    DC_ERR_RANGE = 6,       /* a device-side range check failed */
+    DC_ERR_STATE = 7        /* call order: e.g. displacement before any splat */
+} dc_status;
+
+/* Carry arithmetic of the float (smoothed-density) integral images. */
+enum {
+    DC_CARRY_COMPENSATED = 0, /* FP32 two-sum (compensated) cross-band carries */
+    DC_CARRY_F64 = 1          /* FP64 cross-band carries, rounded once to FP32 */
+};
+
+typedef struct {
+    uint32_t log2_res;       /* N = 1 << log2_res, 4..13 */
+    int32_t kernel_r;        /* Gaussian taps |k| <= r (Sec. 4.1): 0 = no smoothing,
+                                exact integer mode; < 0 = N/128, at least 2; max 64, < N */
+    float sigma;             /* Gaussian width; <= 0 = r / 3 */
+    float d0;                /* regularising constant of eq. (d0); < 0 = n / N^2 */
+    int32_t pixel_center;    /* 0: pixel at (i, j)/N; 1: at (i + 1/2, j + 1/2)/N */
+    int32_t clamp_positions; /* 1: clamp each updated sample to [0, 1]^2 */
+    int32_t carry_mode;      /* DC_CARRY_* (float mode only) */
+    int32_t band_rows;       /* rows per band of the integral-image kernels, a
+                                power of two dividing N; 0 = automatic */
+    int32_t reserved[4];     /* must be zero */
+} dc_params;
+
+/* Read-back of the configuration a context settled on. */
+typedef struct {
+    int32_t N;               /* resolution */
+    int32_t kernel_r;        /* effective radius (0 = exact integer mode) */
+    float sigma;             /* effective Gaussian width */
+    int32_t band_rows;       /* rows per band */
+    int32_t n_bands;         /* N / band_rows */
+    int32_t band_threads;    /* threads per band CTA */
+    int32_t kernels_per_iter;/* kernel launches per iteration of regularize */
+    int32_t device;          /* CUDA device ordinal */
+    int64_t scratch_bytes;   /* device bytes held by the context */
+} dc_info;
+
+/* Create a context for one resolution and parameter set.
+ *   params : host pointer, read once.
+ *   device : CUDA device ordinal; made current for the call.
+ *   cuda_stream : a cudaStream_t to run on, or NULL for a stream the library
+ *                 creates (ordered with the legacy default stream).
+ *   out    : host pointer receiving the context.
+ * Fails with DC_ERR_NOT_POW2 for a resolution outside 2^4..2^13 and with
+ * DC_ERR_INVALID_ARG for any other bad parameter. */
+dc_status declutter_create(const dc_params *params, int device, void *cuda_stream, dc_ctx **out);
+
+/* Wait for outstanding work and free the context (NULL is accepted). */
+dc_status declutter_destroy(dc_ctx *ctx);
+
+/* Effective configuration (host pointer out). */
+dc_status declutter_get_info(const dc_ctx *ctx, dc_info *out);
+
+/* Step (a), Sec. 4.1 and Sec. 4.3 step 1: single-pixel accumulation of the n
+ * samples into the context's uint32 count grid, then (kernel_r > 0) the
+ * separable Gaussian smoothing with reflect border into its float density
+ * d_r.  The regularising constant d0 of eq. (d0) is applied analytically by
+ * the later steps and is not added to d_r.
+ *   pos_xy     : device float[2n].
+ *   n          : 0 <= n < 2^32.
+ *   counts_out : device uint32[N*N] receiving a copy of the counts, or NULL.
+ *   density_out: device float[N*N] receiving d_r (float mode), or NULL. */
+dc_status splat_density(dc_ctx *ctx, const float *pos_xy, int64_t n, uint32_t *counts_out,
+                        float *density_out);
+
+/* Step (b), Sec. 3.1: alpha (sum over i' <= i, j' <= j) and alpha_t (sum over
+ * i'+j' <= i+j, i'-j' >= i-j) of the density of the last splat_density call.
+ * The other six images follow from these two and their marginals
+ * (Sec. 3.1, Fig. 2 caption) and are not stored.
+ *   exact mode (kernel_r = 0): alpha_out, alpha_t_out are device uint64[N*N],
+ *       bit-exact sums of the counts;
+ *   float mode: device float[N*N] sums of d_r (without d0).
+ * Either output may be NULL. */
+dc_status integral_images(dc_ctx *ctx, void *alpha_out, void *alpha_t_out);
+
+/* Step (b) on an arbitrary grid: exact uint64 alpha and alpha_t of the
+ * device uint32[N*N] array grid (N of the context).  Independent of the
+ * context's splat state; uses the context's scratch.  Either output may be
+ * NULL. */
+dc_status integral_images_u32(dc_ctx *ctx, const uint32_t *grid, uint64_t *alpha_out,
+                              uint64_t *alpha_t_out);
+
+/* Step (c), eqs. (map), (d0), (map_res): per-pixel displacement
+ * D = t(x, y; d_r + d0) - t(x, y; d0) of the density of the last
+ * splat_density call, into the context's field and, if disp_xy_out is not
+ * NULL, into device float[2*N*N] (interleaved x, y; domain units).
+ * Exact mode evaluates the numerator in exact integer arithmetic and rounds
+ * once, so an even count grid gives exactly zero. */
+dc_status displacement_field(dc_ctx *ctx, float *disp_xy_out);
+
+/* Step (d), Sec. 4.2: in place, z <- z + bilinear(D)(z) for the n samples,
+ * with the field of the last displacement_field call; corner indices are
+ * clamped to the grid, and with clamp_positions the result to [0, 1]^2. */
+dc_status advect_samples(dc_ctx *ctx, float *pos_xy, int64_t n);
+
+/* Sec. 4.3: iters full iterations (a)-(d) in place on pos_xy, launched as
+ * one CUDA graph captured on the first call for this (pos_xy, n, iters,
+ * metrics) combination and replayed afterwards.
+ *   uniformity_out: host double[iters], or NULL.  When given, entry k is the
+ *   Sec. 6.2 regularity measure (std of the sample counts of 4x4-pixel bins)
+ *   after iteration k + 1, and the call synchronises and returns the device
+ *   status; otherwise the call is asynchronous. */
+dc_status regularize(dc_ctx *ctx, float *pos_xy, int64_t n, int32_t iters, double *uniformity_out);
+
+/* regularize() on HOST samples: copies host float[2n] to a context-owned
+ * device buffer, runs the iterations, copies the result back into the same
+ * host array and synchronises.  Pinned host memory gives asynchronous
+ * copies.  uniformity_out as for regularize(). */
+dc_status regularize_host(dc_ctx *ctx, float *host_pos_xy, int64_t n, int32_t iters,
+                          double *uniformity_out);
+
+/* Sec. 6.2 quality measures of the count grid of the last splat_density
+ * call; synchronises.  out (host double[3]): [0] std of the 4x4-bin counts,
+ * [1] that std over the mean bin count, [2] overplotting =
+ * (n - occupied pixels) / n. */
+dc_status quality_metrics(dc_ctx *ctx, double *out);
+
+/* Wait for the context's stream; returns the first CUDA error or the sticky
+ * device status, and clears the latter. */
+dc_status declutter_sync(dc_ctx *ctx);
+
+/* Instrumented run of regularize(): the same kernels with the same launch
+ * shapes on the same stream, launched one by one with a CUDA event pair
+ * around each.  kernel_ms_out (host float[DC_KERNEL_KINDS]) receives the
+ * summed device time per kernel kind and launches_out (host
+ * int32[DC_KERNEL_KINDS]) the launch count; either may be NULL.
+ * Synchronises. */
+#define DC_KERNEL_KINDS 8
+dc_status declutter_profile_regularize(dc_ctx *ctx, float *pos_xy, int64_t n, int32_t iters,
+                                       float *kernel_ms_out, int32_t *launches_out);
+
+/* Name of kernel kind k (0 <= k < DC_KERNEL_KINDS), or NULL. */
+const char *declutter_kernel_name(int32_t k);
+
+const char *declutter_status_string(dc_status s);
+const char *declutter_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DECLUTTER_H */

@@ -1,0 +1,653 @@
+// Grid kernels: Gaussian smoothing (Sec. 4.1), the integral images of
+// Sec. 3.1 and the defect-corrected displacement of eq. (map_res).
+//
+// Integral images by full-width row bands.  With P(j, c) the row prefix of
+// row j (P(j, -1) = 0, P(j, c >= N) = row total), every quantity the mapping
+// needs is a running sum of P down one of three line families:
+//   alpha(i, j) = sum_{j' <= j} P(j', i)                    (vertical)
+//   U(i, j)     = sum_{j' <= j} P(j', i + j - j')           (anti-diagonal)
+//   V(i, j)     = sum_{j' <= j} P(j', i - j + j' - 1)       (diagonal)
+//   alpha_t = U - V  (the clipped upward cone, Sec. 3.1).
+// Inside a band each of the three is a one-row recurrence
+//   a(i, j) = a(i, j-1) + P(j, i)
+//   U(i, j) = U(i+1, j-1) + P(j, i)
+//   V(i, j) = V(i-1, j-1) + P(j, i-1)
+// and the rows above the band enter as carries, one value per line: the band
+// kernels are run twice (aggregate, then final), with an exclusive scan of
+// the per-band aggregates over bands in between.  A band's aggregate along
+// every line follows from the recurrence state at its last row plus one value
+// per row at its left and right edges (compact form, 3N + 2T + 1 values).
+//
+// The marginals R(i) = alpha(i, N-1), Cc(j) = alpha(N-1, j),
+// A(u) = sum over i'+j' <= u, B(v) = sum over i'-j' >= v and the total C give
+// beta, gamma, delta and their tilted versions from alpha and alpha_t
+// (Sec. 3.1 partition identities; Fig. 2 caption).
+#include "dc_internal.cuh"
+
+namespace dc {
+
+BandGeom make_band_geom(int log2N, int band_rows)
+{
+    BandGeom g;
+    g.log2N = log2N;
+    g.N = 1 << log2N;
+    int T = band_rows;
+    if (T <= 0) {
+        T = g.N / 128;
+        if (T < 1) T = 1;
+        if (T > 64) T = 64;
+    }
+    g.T = T;
+    g.nb = g.N / T;
+    // at most 512 threads per band CTA (128 registers a thread)
+    g.CPT = g.N >= 128 ? (g.N / 512 > 4 ? g.N / 512 : 4) : 1;
+    g.NT = g.N / g.CPT;
+    if (g.NT < 32) g.NT = 32;
+    g.agg_stride = (3 * g.N + 2 * T + 1 + 3) & ~3;
+    g.lanes = 5 * g.N;
+    return g;
+}
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------------
+// Smoothing: one 2D tile per CTA with a halo of r on each side, vertical
+// then horizontal pass in shared memory; reflect border (-1 -> 0, N -> N-1).
+// ------------------------------------------------------------------------
+__device__ __forceinline__ int reflect_index(int k, int N)
+{
+    return k < 0 ? -1 - k : (k >= N ? 2 * N - 1 - k : k);
+}
+
+__global__ void __launch_bounds__(256) smooth_kernel(const uint32_t *__restrict__ counts,
+                                                     float *__restrict__ dens, int log2N, GaussW w)
+{
+    extern __shared__ float s_sm[];
+    const int N = 1 << log2N;
+    const int TW = N < 32 ? N : 32;
+    const int r = w.r;
+    const int W = TW + 2 * r;
+    float *s_in = s_sm;          // W x W
+    float *s_mid = s_sm + W * W; // TW x W
+    const int ox = blockIdx.x * TW, oy = blockIdx.y * TW;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < W * W; idx += blockDim.x) {
+        const int yy = idx / W, xx = idx - yy * W;
+        const int gy = reflect_index(oy + yy - r, N), gx = reflect_index(ox + xx - r, N);
+        s_in[idx] = (float)counts[((size_t)gy << log2N) + gx];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < TW * W; idx += blockDim.x) {
+        const int y = idx / W, xx = idx - y * W;
+        float s = 0.0f;
+        for (int k = 0; k <= 2 * r; ++k) s += w.g[k] * s_in[(y + k) * W + xx];
+        s_mid[idx] = s;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < TW * TW; idx += blockDim.x) {
+        const int y = idx / TW, x = idx - y * TW;
+        float s = 0.0f;
+        for (int k = 0; k <= 2 * r; ++k) s += w.g[k] * s_mid[y * W + x + k];
+        dens[((size_t)(oy + y) << log2N) + ox + x] = s;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Band kernels.
+// ------------------------------------------------------------------------
+template <int MODE> struct ModeT;
+template <> struct ModeT<MODE_COUNT> { using Acc = uint32_t; using In = uint32_t; };
+template <> struct ModeT<MODE_FLOAT> { using Acc = float; using In = float; };
+template <> struct ModeT<MODE_GRID64> { using Acc = unsigned long long; using In = uint32_t; };
+
+template <int MODE, int CPT>
+__device__ __forceinline__ void load_row(const void *src, int log2N, int j, int c0,
+                                         float mu, typename ModeT<MODE>::Acc (&v)[CPT])
+{
+    using Acc = typename ModeT<MODE>::Acc;
+    using In = typename ModeT<MODE>::In;
+    const int N = 1 << log2N;
+    const In *row = static_cast<const In *>(src) + ((size_t)j << log2N);
+    In x[CPT];
+    if constexpr (CPT % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < CPT / 4; ++q) {
+            if constexpr (MODE == MODE_FLOAT) {
+                const float4 f = *reinterpret_cast<const float4 *>(row + c0 + 4 * q);
+                x[4 * q] = f.x; x[4 * q + 1] = f.y; x[4 * q + 2] = f.z; x[4 * q + 3] = f.w;
+            } else {
+                const uint4 f = *reinterpret_cast<const uint4 *>(row + c0 + 4 * q);
+                x[4 * q] = f.x; x[4 * q + 1] = f.y; x[4 * q + 2] = f.z; x[4 * q + 3] = f.w;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) x[k] = (c0 + k < N) ? row[c0 + k] : In(0);
+    }
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        if constexpr (MODE == MODE_FLOAT) v[k] = (c0 + k < N) ? x[k] - mu : 0.0f;
+        else v[k] = (Acc)x[k];
+    }
+}
+
+// Two-sum accumulation of a float pair (hi, lo) for the compensated carries.
+struct F2 { float hi, lo; };
+__device__ __forceinline__ F2 f2_add(F2 a, float b)
+{
+    const float s = a.hi + b;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b - bb);
+    return {s, a.lo + e};
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    F2 r = f2_add(a, b.hi);
+    r.lo += b.lo;
+    return r;
+}
+
+// Anchor numerators of eq. (map) at grid scale S (position = numerator / S):
+// order alpha, beta, gamma, delta, alpha_t, beta_t, gamma_t, delta_t with
+// anchors q1, q2, q3, q4, (x,1), (1,y), (x,0), (0,y).  Ties as printed:
+// y < x and x + y < 1 tested on the integer numerators.
+__device__ __forceinline__ void anchors(int a, int b, int S, int (&qx)[8], int (&qy)[8])
+{
+    if (b < a) { qx[0] = S; qy[0] = S + b - a; qx[2] = a - b; qy[2] = 0; }
+    else       { qx[0] = S - b + a; qy[0] = S; qx[2] = 0; qy[2] = b - a; }
+    if (a + b < S) { qx[1] = a + b; qy[1] = 0; qx[3] = 0; qy[3] = a + b; }
+    else           { qx[1] = S; qy[1] = a + b - S; qx[3] = a + b - S; qy[3] = S; }
+    qx[4] = a; qy[4] = S;
+    qx[5] = S; qy[5] = b;
+    qx[6] = a; qy[6] = 0;
+    qx[7] = 0; qy[7] = b;
+}
+
+// Pixel counts of the eight regions for the constant texture 1 (the defect
+// t(x, y; d0) of Sec. 4.2 is this mapping, which does not depend on d0).
+__device__ __forceinline__ int lattice_A(int u, int N)
+{
+    return u <= N - 1 ? (u + 1) * (u + 2) / 2 : N * N - (2 * N - 2 - u) * (2 * N - 1 - u) / 2;
+}
+__device__ __forceinline__ int tri(int m) { return m > 0 ? m * (m + 1) / 2 : 0; }
+__device__ __forceinline__ void lattice_counts(int c, int j, int N, int (&w0)[8])
+{
+    w0[0] = (c + 1) * (j + 1);
+    w0[1] = (c + 1) * (N - 1 - j);
+    w0[2] = (N - 1 - c) * (N - 1 - j);
+    w0[3] = (j + 1) * (N - 1 - c);
+    const int at = (j + 1) * (j + 1) - tri(j - (N - 1 - c)) - tri(j - c);
+    const int A = lattice_A(c + j, N);
+    const int B = lattice_A(N - 1 - c + j, N);
+    w0[4] = at;
+    w0[5] = A - at;
+    w0[6] = N * N - A - B + at;
+    w0[7] = B - at;
+}
+
+__device__ __forceinline__ double u128_mag_to_double(unsigned long long hi, unsigned long long lo)
+{
+    return (double)hi * 18446744073709551616.0 + (double)lo;
+}
+
+// Exact-mode displacement: w = exact region sums of the counts, C = n.
+// M = N^2 sum_k w_k Q_k - C sum_k w0_k Q_k is an exact integer (128 bits),
+// D = M / (2 S N^2 (C + d0 N^2)) rounded once.
+__device__ __forceinline__ float exact_component(long long A1, long long A0, int log2NN, long long C,
+                                                 double inv_den)
+{
+    const __int128 M = ((__int128)A1 << log2NN) - (__int128)C * (__int128)A0;
+    const bool neg = M < 0;
+    const unsigned __int128 mag = neg ? (unsigned __int128)(-M) : (unsigned __int128)M;
+    const double dm = u128_mag_to_double((unsigned long long)(mag >> 64), (unsigned long long)mag);
+    return (float)((neg ? -dm : dm) * inv_den);
+}
+
+template <typename T, int CPT>
+__device__ __forceinline__ void store_row(T *dst, const T (&v)[CPT], int c0, int N)
+{
+    if constexpr ((CPT * sizeof(T)) % 16 == 0) {
+        constexpr int per = 16 / sizeof(T);
+#pragma unroll
+        for (int q = 0; q < CPT / per; ++q) {
+            if constexpr (sizeof(T) == 4) {
+                float4 f;
+                f.x = __int_as_float(*(const int *)&v[per * q]);
+                f.y = __int_as_float(*(const int *)&v[per * q + 1]);
+                f.z = __int_as_float(*(const int *)&v[per * q + 2]);
+                f.w = __int_as_float(*(const int *)&v[per * q + 3]);
+                *reinterpret_cast<float4 *>(dst + c0 + per * q) = f;
+            } else {
+                ulonglong2 f;
+                f.x = *(const unsigned long long *)&v[per * q];
+                f.y = *(const unsigned long long *)&v[per * q + 1];
+                *reinterpret_cast<ulonglong2 *>(dst + c0 + per * q) = f;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k)
+            if (c0 + k < N) dst[c0 + k] = v[k];
+    }
+}
+
+// One band per CTA.  FINAL = false: write the band's compact aggregate.
+// FINAL = true: combine with the carries and evaluate the outputs.
+template <int MODE, int CPT, bool FINAL>
+__global__ void __launch_bounds__(CPT == 1 ? 64 : 512) band_kernel(BandArgs a, int log2N, int T)
+{
+    using Acc = typename ModeT<MODE>::Acc;
+    const int N = 1 << log2N;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int nw = blockDim.x >> 5;
+    const int b = blockIdx.x;
+    const int j0 = b * T;
+    const int c0 = t * CPT;
+    const int lanes = 5 * N;
+
+    __shared__ Acc s_wt[2][32];
+    __shared__ Acc s_uf[2][32];
+    __shared__ Acc s_vl[2][32];
+    __shared__ Acc s_U0[64], s_VN[64], s_RT[64];
+
+    Acc arun[CPT], Uo[CPT], Vo[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) { arun[k] = Acc(0); Uo[k] = Acc(0); Vo[k] = Acc(0); }
+    Acc RTcum = Acc(0);
+
+    // per-band constants of the final pass
+    const Acc *cb = nullptr, *ce = nullptr;
+    Acc cvb[CPT], Rk[CPT];
+    Acc Ctot = Acc(0), CVbN = Acc(0);
+    float kappa = 0.f, scale = 0.f;
+    if constexpr (FINAL) {
+        cb = static_cast<const Acc *>(a.carry) + (size_t)b * lanes;
+        ce = static_cast<const Acc *>(a.carry) + (size_t)(N / T) * lanes;
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            const int c = min(c0 + k, N - 1);
+            cvb[k] = cb[c];
+            Rk[k] = ce[c];
+        }
+        Ctot = ce[N - 1];
+        CVbN = cb[N - 1];
+        if constexpr (MODE == MODE_FLOAT) {
+            const float NN = (float)N * (float)N;
+            kappa = Ctot / NN;
+            const float S = a.pixel_center ? 2.0f * N : (float)N;
+            const float Call = Ctot + a.mu * NN + a.d0 * NN;
+            scale = Call > 0.0f ? 1.0f / (2.0f * S * Call) : 0.0f;
+        }
+    }
+
+    for (int r = 0; r < T; ++r) {
+        const int j = j0 + r;
+        const int par = r & 1;
+        Acc v[CPT];
+        load_row<MODE, CPT>(a.src, log2N, j, c0, a.mu, v);
+
+        // neighbour state of the previous row, exchanged before the scan's barrier
+        Acc u_next = __shfl_down_sync(kFull, Uo[0], 1);
+        Acc v_prev = __shfl_up_sync(kFull, Vo[CPT - 1], 1);
+        if (lane == 0) s_uf[par][warp] = Uo[0];
+        if (lane == 31) s_vl[par][warp] = Vo[CPT - 1];
+
+        // row prefix P: thread-local, warp, then block
+#pragma unroll
+        for (int k = 1; k < CPT; ++k) v[k] = v[k] + v[k - 1];
+        const Acc tsum = v[CPT - 1];
+        Acc x = tsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const Acc y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x = x + y;
+        }
+        if (lane == 31) s_wt[par][warp] = x;
+        __syncthreads();
+        Acc wv = lane < nw ? s_wt[par][lane] : Acc(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const Acc y = __shfl_up_sync(kFull, wv, o);
+            if (lane >= o) wv = wv + y;
+        }
+        const Acc wexcl = __shfl_sync(kFull, wv, (warp + 31) & 31);
+        const Acc total = __shfl_sync(kFull, wv, nw - 1);
+        const Acc off = (warp > 0 ? wexcl : Acc(0)) + (x - tsum);
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) v[k] = v[k] + off;
+        if (lane == 31) u_next = (warp + 1 < nw) ? s_uf[par][warp + 1] : Acc(0);
+        if (lane == 0) v_prev = (warp > 0) ? s_vl[par][warp - 1] : Acc(0);
+
+        // the three recurrences
+        const Acc RTprev = RTcum;
+        RTcum = RTcum + total;
+        Acc Un[CPT], Vn[CPT];
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            const int c = c0 + k;
+            Acc ur = (k + 1 < CPT) ? Uo[k + 1] : u_next;
+            if (c == N - 1) ur = RTprev;              // U(N, j-1): row totals only
+            Un[k] = ur + v[k];
+            Acc vl = (k > 0) ? Vo[k - 1] : v_prev;
+            if (c == 0) vl = Acc(0);                  // V(-1, j-1) = 0
+            const Acc pm1 = (k > 0) ? v[k - 1] : off; // P(j, c-1)
+            Vn[k] = vl + pm1;
+            arun[k] = arun[k] + v[k];
+        }
+
+        if constexpr (!FINAL) {
+            if (t == 0) {
+                s_U0[r] = Un[0];
+                s_RT[r] = total;
+            }
+#pragma unroll
+            for (int k = 0; k < CPT; ++k)
+                if (c0 + k == N - 1) s_VN[r] = Vn[k];
+        } else {
+            const Acc Ccj = CVbN + RTcum;
+            float dxy[2 * CPT];
+            Acc oal[CPT], oat[CPT];
+            float fal[CPT], fat[CPT];
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) {
+                const int c = c0 + k;
+                const int cc = min(c, N - 1);
+                const int u = cc + j;
+                const int vi = cc - j + N - 1;
+                const Acc al = cvb[k] + arun[k];
+                const Acc at = (cb[N + u] + Un[k]) - (cb[3 * N + vi] + Vn[k]);
+                const Acc A = ce[N + u];
+                const Acc Bv = Ctot - ce[3 * N + vi];
+                const Acc R = Rk[k];
+                Acc w[8];
+                w[0] = al;
+                w[1] = R - al;
+                w[2] = Ctot - R - Ccj + al;
+                w[3] = Ccj - al;
+                w[4] = at;
+                w[5] = A - at;
+                w[6] = Ctot - A - Bv + at;
+                w[7] = Bv - at;
+                oal[k] = al;
+                oat[k] = at;
+                if constexpr (MODE == MODE_GRID64) {
+                    (void)w;
+                } else {
+                    const int S = a.pixel_center ? 2 * N : N;
+                    const int ai = a.pixel_center ? 2 * cc + 1 : cc;
+                    const int bj = a.pixel_center ? 2 * j + 1 : j;
+                    int qx[8], qy[8], w0[8];
+                    anchors(ai, bj, S, qx, qy);
+                    lattice_counts(cc, j, N, w0);
+                    if constexpr (MODE == MODE_FLOAT) {
+                        float nx = 0.f, ny = 0.f, nx0 = 0.f, ny0 = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            nx = fmaf(w[q], (float)qx[q], nx);
+                            ny = fmaf(w[q], (float)qy[q], ny);
+                            nx0 = fmaf((float)w0[q], (float)qx[q], nx0);
+                            ny0 = fmaf((float)w0[q], (float)qy[q], ny0);
+                        }
+                        dxy[2 * k] = fmaf(-kappa, nx0, nx) * scale;
+                        dxy[2 * k + 1] = fmaf(-kappa, ny0, ny) * scale;
+                        const float muf = a.mu;
+                        fal[k] = al + muf * (float)w0[0];
+                        fat[k] = at + muf * (float)w0[4];
+                    } else {
+                        long long A1x = 0, A1y = 0, A0x = 0, A0y = 0;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const long long wq = (long long)(uint32_t)w[q];
+                            A1x += wq * qx[q];
+                            A1y += wq * qy[q];
+                            A0x += (long long)w0[q] * qx[q];
+                            A0y += (long long)w0[q] * qy[q];
+                        }
+                        const long long C = (long long)(uint32_t)Ctot;
+                        dxy[2 * k] = exact_component(A1x, A0x, 2 * log2N, C, a.inv_den_exact);
+                        dxy[2 * k + 1] = exact_component(A1y, A0y, 2 * log2N, C, a.inv_den_exact);
+                    }
+                }
+            }
+            const size_t rowoff = (size_t)j << log2N;
+            if constexpr (MODE != MODE_GRID64) {
+                if (a.disp) {
+                    float *dd = reinterpret_cast<float *>(a.disp) + 2 * rowoff;
+                    store_row<float, 2 * CPT>(dd, dxy, 2 * c0, 2 * N);
+                }
+            }
+            if constexpr (MODE == MODE_FLOAT) {
+                if (a.alpha_out) store_row<float, CPT>(static_cast<float *>(a.alpha_out) + rowoff, fal, c0, N);
+                if (a.alpha_t_out) store_row<float, CPT>(static_cast<float *>(a.alpha_t_out) + rowoff, fat, c0, N);
+            } else {
+                unsigned long long o1[CPT], o2[CPT];
+#pragma unroll
+                for (int k = 0; k < CPT; ++k) {
+                    o1[k] = (unsigned long long)oal[k];
+                    o2[k] = (unsigned long long)oat[k];
+                }
+                if (a.alpha_out)
+                    store_row<unsigned long long, CPT>(static_cast<unsigned long long *>(a.alpha_out) + rowoff, o1, c0, N);
+                if (a.alpha_t_out)
+                    store_row<unsigned long long, CPT>(static_cast<unsigned long long *>(a.alpha_t_out) + rowoff, o2, c0, N);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) { Uo[k] = Un[k]; Vo[k] = Vn[k]; }
+    }
+
+    if constexpr (!FINAL) {
+        // compact aggregate [alpha N][U N][V N][U0 T][E T][S]:
+        //   alpha, U, V: recurrence state at the band's last row;
+        //   U0[r] = U(0, j0 + r); E[r] = V(N-1, j0 + r) + row totals below row r;
+        //   S = band total.
+        __syncthreads();
+        Acc *ag = static_cast<Acc *>(a.agg) + (size_t)b * a.agg_stride;
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            const int c = c0 + k;
+            if (c < N) {
+                ag[c] = arun[k];
+                ag[N + c] = Uo[k];
+                ag[2 * N + c] = Vo[k];
+            }
+        }
+        for (int rr = t; rr < T; rr += blockDim.x) {
+            Acc below = Acc(0);
+            for (int q = rr + 1; q < T; ++q) below = below + s_RT[q];
+            ag[3 * N + rr] = s_U0[rr];
+            ag[3 * N + T + rr] = s_VN[rr] + below;
+        }
+        if (t == 0) ag[3 * N + 2 * T] = RTcum;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Carries: exclusive scan over bands of every absolute line.
+// Lanes [0, N): vertical line i.  [N, 3N): anti-diagonal u = lane - N.
+// [3N, 5N): diagonal v = lane - 3N - (N - 1).  Row b of the output holds
+// the sum over bands < b; row nb the total (the marginals).
+// ------------------------------------------------------------------------
+template <typename Acc>
+__device__ __forceinline__ Acc band_contrib(const Acc *__restrict__ ab, int b, int lane, int N, int T)
+{
+    const int j0 = b * T, jl = j0 + T - 1;
+    if (lane < N) return ab[lane];
+    if (lane < 3 * N) {
+        const int u = lane - N;
+        if (u < j0) return Acc(0);
+        if (u < jl) return ab[3 * N + (u - j0)];
+        if (u <= jl + N - 1) return ab[N + (u - jl)];
+        return ab[3 * N + 2 * T];
+    }
+    const int v = lane - 3 * N - (N - 1);
+    if (v < -jl) return Acc(0);
+    if (v <= N - 1 - jl) return ab[2 * N + (v + jl)];
+    const int m = v - (N - 1 - jl);
+    if (m <= T - 1) return ab[3 * N + T + (T - 1 - m)];
+    return ab[3 * N + 2 * T];
+}
+
+template <typename Acc> struct ScanSum {
+    Acc s;
+    __device__ void zero() { s = Acc(0); }
+    __device__ void add(Acc x) { s = s + x; }
+    __device__ void add(const ScanSum &o) { s = s + o.s; }
+    __device__ Acc value() const { return s; }
+    __device__ ScanSum shfl_up(int o) const { ScanSum r; r.s = __shfl_up_sync(kFull, s, o); return r; }
+};
+struct ScanF2 {
+    F2 s;
+    __device__ void zero() { s = {0.f, 0.f}; }
+    __device__ void add(float x) { s = f2_add(s, x); }
+    __device__ void add(const ScanF2 &o) { s = f2_add(s, o.s); }
+    __device__ float value() const { return s.hi + s.lo; }
+    __device__ ScanF2 shfl_up(int o) const
+    {
+        ScanF2 r;
+        r.s.hi = __shfl_up_sync(kFull, s.hi, o);
+        r.s.lo = __shfl_up_sync(kFull, s.lo, o);
+        return r;
+    }
+};
+struct ScanF64 {
+    double s;
+    __device__ void zero() { s = 0.0; }
+    __device__ void add(float x) { s += (double)x; }
+    __device__ void add(const ScanF64 &o) { s += o.s; }
+    __device__ float value() const { return (float)s; }
+    __device__ ScanF64 shfl_up(int o) const { ScanF64 r; r.s = __shfl_up_sync(kFull, s, o); return r; }
+};
+
+template <typename Acc, typename Sum>
+__global__ void __launch_bounds__(1024) carry_kernel(const Acc *__restrict__ agg, Acc *__restrict__ carry,
+                                                     int log2N, int T, int nb, int agg_stride)
+{
+    const int N = 1 << log2N;
+    const int lanes = 5 * N;
+    const int lx = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int lane = blockIdx.x * 32 + lx;
+    const bool active = lane < lanes;
+    const int bpg = (nb + 31) / 32;
+    const int b_beg = g * bpg;
+    const int b_end = min(nb, b_beg + bpg);
+    __shared__ Sum s_sum[32][33];
+
+    Sum s;
+    s.zero();
+    if (active)
+        for (int b = b_beg; b < b_end; ++b) s.add(band_contrib(agg + (size_t)b * agg_stride, b, lane, N, T));
+    s_sum[g][lx] = s;
+    __syncthreads();
+    {
+        // warp g scans column (lane) g over the 32 groups held by its lanes
+        Sum x = s_sum[lx][g];
+        Sum inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            Sum y = inc.shfl_up(o);
+            if (lx >= o) inc.add(y);
+        }
+        Sum ex = inc.shfl_up(1);
+        if (lx == 0) ex.zero();
+        s_sum[lx][g] = ex;
+    }
+    __syncthreads();
+    if (!active) return;
+    Sum pre = s_sum[g][lx];
+    for (int b = b_beg; b < b_end; ++b) {
+        carry[(size_t)b * lanes + lane] = pre.value();
+        pre.add(band_contrib(agg + (size_t)b * agg_stride, b, lane, N, T));
+    }
+    if (b_beg < nb && b_end == nb) carry[(size_t)nb * lanes + lane] = pre.value();
+}
+
+}  // namespace
+
+int smooth_smem_bytes(int r)
+{
+    const int TW = 32;
+    const int W = TW + 2 * r;
+    return (W * W + TW * W) * (int)sizeof(float);
+}
+
+cudaError_t prepare_kernels()
+{
+    // dynamic shared memory of the smoothing tile for the largest radius
+    return cudaFuncSetAttribute(smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smooth_smem_bytes(64));
+}
+
+cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, int log2N, const GaussW &w)
+{
+    const int N = 1 << log2N;
+    const int TW = N < 32 ? N : 32;
+    const int bytes = smooth_smem_bytes(w.r);
+    dim3 grid(N / TW, N / TW);
+    smooth_kernel<<<grid, 256, bytes, s>>>(counts, dens, log2N, w);
+    return cudaGetLastError();
+}
+
+template <int MODE, bool FINAL>
+static cudaError_t launch_band_mode(cudaStream_t s, const BandGeom &g, const BandArgs &a)
+{
+    switch (g.CPT) {
+    case 1: band_kernel<MODE, 1, FINAL><<<g.nb, g.NT, 0, s>>>(a, g.log2N, g.T); break;
+    case 4: band_kernel<MODE, 4, FINAL><<<g.nb, g.NT, 0, s>>>(a, g.log2N, g.T); break;
+    case 8: band_kernel<MODE, 8, FINAL><<<g.nb, g.NT, 0, s>>>(a, g.log2N, g.T); break;
+    case 16: band_kernel<MODE, 16, FINAL><<<g.nb, g.NT, 0, s>>>(a, g.log2N, g.T); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_agg(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a)
+{
+    switch (mode) {
+    case MODE_COUNT: return launch_band_mode<MODE_COUNT, false>(s, g, a);
+    case MODE_FLOAT: return launch_band_mode<MODE_FLOAT, false>(s, g, a);
+    case MODE_GRID64: return launch_band_mode<MODE_GRID64, false>(s, g, a);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_band_final(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a)
+{
+    switch (mode) {
+    case MODE_COUNT: return launch_band_mode<MODE_COUNT, true>(s, g, a);
+    case MODE_FLOAT: return launch_band_mode<MODE_FLOAT, true>(s, g, a);
+    case MODE_GRID64: return launch_band_mode<MODE_GRID64, true>(s, g, a);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const void *agg, void *carry)
+{
+    const int blocks = (g.lanes + 31) / 32;
+    switch (mode) {
+    case MODE_COUNT:
+        carry_kernel<uint32_t, ScanSum<uint32_t>><<<blocks, 1024, 0, s>>>(
+            static_cast<const uint32_t *>(agg), static_cast<uint32_t *>(carry), g.log2N, g.T, g.nb, g.agg_stride);
+        break;
+    case MODE_GRID64:
+        carry_kernel<unsigned long long, ScanSum<unsigned long long>><<<blocks, 1024, 0, s>>>(
+            static_cast<const unsigned long long *>(agg), static_cast<unsigned long long *>(carry), g.log2N, g.T,
+            g.nb, g.agg_stride);
+        break;
+    case MODE_FLOAT:
+        if (carry_mode == DC_CARRY_F64)
+            carry_kernel<float, ScanF64><<<blocks, 1024, 0, s>>>(static_cast<const float *>(agg),
+                                                                  static_cast<float *>(carry), g.log2N, g.T, g.nb,
+                                                                  g.agg_stride);
+        else
+            carry_kernel<float, ScanF2><<<blocks, 1024, 0, s>>>(static_cast<const float *>(agg),
+                                                                 static_cast<float *>(carry), g.log2N, g.T, g.nb,
+                                                                 g.agg_stride);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace dc

@@ -1,0 +1,120 @@
+// Internal declarations shared by the translation units of libdeclutter.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "declutter.h"
+
+namespace dc {
+
+// Kernel kinds, in the order reported by declutter_profile_regularize().
+enum KernelKind {
+    K_SPLAT = 0,
+    K_SMOOTH = 1,
+    K_BAND_AGG = 2,
+    K_CARRY = 3,
+    K_BAND_FINAL = 4,
+    K_ADVECT = 5,
+    K_QUALITY = 6,
+    K_MEMSET = 7,
+};
+
+// Accumulation mode of the integral-image kernels.
+enum Mode {
+    MODE_COUNT = 0,  // uint32 counts, uint32 arithmetic (exact: all sums < 2^32)
+    MODE_FLOAT = 1,  // float d_r minus the mean mu, float arithmetic
+    MODE_GRID64 = 2, // arbitrary uint32 grid, uint64 arithmetic
+};
+
+// Band decomposition of the N x N grid for the integral-image kernels:
+// nb bands of T full-width rows; each band is one CTA of NT threads, thread t
+// owning columns [t*CPT, t*CPT + CPT).
+struct BandGeom {
+    int N = 0, log2N = 0;
+    int T = 0, nb = 0;
+    int NT = 0, CPT = 0;
+    int agg_stride = 0; // elements per band in the compact aggregate array
+    int lanes = 0;      // 5N absolute carry lanes
+};
+
+BandGeom make_band_geom(int log2N, int band_rows);
+
+// Gaussian weights passed by value (kernel parameter space).
+struct GaussW {
+    float g[129];
+    int r;
+};
+
+// Per-launch arguments of the band kernels.
+struct BandArgs {
+    const void *src;          // uint32 (COUNT, GRID64) or float (FLOAT), N*N
+    float mu;                 // FLOAT: mean subtracted from d_r
+    void *agg;                // compact aggregates [nb][agg_stride]
+    int agg_stride;
+    const void *carry;        // carries [nb + 1][lanes]
+    // final-kernel outputs (any may be null)
+    float2 *disp;             // domain units
+    void *alpha_out;          // uint64 (COUNT, GRID64) or float (FLOAT)
+    void *alpha_t_out;
+    // displacement constants
+    int pixel_center;
+    float d0;                 // regularising constant (>= 0)
+    double inv_den_exact;     // COUNT: 1 / (2 S N^2 (n + d0 N^2))
+};
+
+struct GraphEntry {
+    const void *pos = nullptr;
+    int64_t n = 0;
+    int iters = 0;
+    int metrics = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
+// Launchers (all enqueue on `s`; return cudaGetLastError()).
+cudaError_t launch_splat(cudaStream_t s, const float2 *pos, int64_t n, uint32_t *counts, int log2N);
+cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *disp, int log2N,
+                          int pixel_center, int clamp);
+cudaError_t launch_quality(cudaStream_t s, const uint32_t *counts, int log2N, unsigned long long *acc);
+cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, int log2N, const GaussW &w);
+cudaError_t launch_band_agg(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a);
+cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const void *agg,
+                         void *carry);
+cudaError_t launch_band_final(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a);
+int smooth_smem_bytes(int r);
+cudaError_t prepare_kernels();  // per-device kernel attributes; call with the device current
+
+}  // namespace dc
+
+struct dc_ctx {
+    dc_params p{};
+    int device = 0;
+    cudaStream_t stream = nullptr;      // where everything runs
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+    dc::BandGeom g;
+    int r = 0;
+    float sigma = 0.f;
+    dc::GaussW w{};
+    int mode = dc::MODE_COUNT;          // MODE_COUNT (r == 0) or MODE_FLOAT
+
+    uint32_t *counts = nullptr;
+    float *dens = nullptr;
+    float2 *disp = nullptr;
+    void *agg = nullptr;
+    void *carry = nullptr;
+    unsigned *status = nullptr;
+    unsigned long long *qacc = nullptr; // [3 * (qslots)]
+    int qslots = 0;
+    float *hpos = nullptr;              // device staging for regularize_host
+    int64_t hpos_cap = 0;
+    int64_t scratch_bytes = 0;
+
+    int64_t n_last = -1;                // n of the last splat
+    bool have_disp = false;
+
+    std::vector<dc::GraphEntry> graphs;
+    cudaEvent_t prof_ev[2 * 64] = {};
+};

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of ``libdeclutter.so`` (C ABI in ``include/declutter.h``).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Tensors are PyTorch CUDA tensors used as device memory; their data
+pointers go straight to the C calls.  There is no CPU fallback: if the
+library is missing, importing this module's functions raises.
+
+The function names are those of the C ABI:
+
+    declutter_create, declutter_destroy, declutter_get_info,
+    splat_density, integral_images, integral_images_u32,
+    displacement_field, advect_samples, regularize, regularize_host,
+    quality_metrics, declutter_sync, declutter_profile_regularize,
+    declutter_kernel_name, declutter_status_string, declutter_last_error
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "DeclutterError", "Context", "dc_params", "dc_info", "load_library", "exported_symbols",
+    "declutter_create", "declutter_destroy", "declutter_get_info", "splat_density", "integral_images",
+    "integral_images_u32", "displacement_field", "advect_samples", "regularize", "regularize_host",
+    "quality_metrics", "declutter_sync", "declutter_profile_regularize", "declutter_kernel_name",
+    "declutter_status_string", "declutter_last_error", "DC_CARRY_COMPENSATED", "DC_CARRY_F64",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdeclutter.so")
+KERNEL_KINDS = 8
+
+DC_CARRY_COMPENSATED = 0
+DC_CARRY_F64 = 1
+
+
+class DeclutterError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status}: {message}")
+        self.status = status
+
+
+class dc_params(ctypes.Structure):
+    _fields_ = [
+        ("log2_res", ctypes.c_uint32),
+        ("kernel_r", ctypes.c_int32),
+        ("sigma", ctypes.c_float),
+        ("d0", ctypes.c_float),
+        ("pixel_center", ctypes.c_int32),
+        ("clamp_positions", ctypes.c_int32),
+        ("carry_mode", ctypes.c_int32),
+        ("band_rows", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
+    ]
+
+
+class dc_info(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int32),
+        ("kernel_r", ctypes.c_int32),
+        ("sigma", ctypes.c_float),
+        ("band_rows", ctypes.c_int32),
+        ("n_bands", ctypes.c_int32),
+        ("band_threads", ctypes.c_int32),
+        ("kernels_per_iter", ctypes.c_int32),
+        ("device", ctypes.c_int32),
+        ("scratch_bytes", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported symbol
+_P = ctypes.c_void_p
+_SIGS = [
+    ("declutter_create", ctypes.c_int, [ctypes.POINTER(dc_params), ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    ("declutter_destroy", ctypes.c_int, [_P]),
+    ("declutter_get_info", ctypes.c_int, [_P, ctypes.POINTER(dc_info)]),
+    ("splat_density", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    ("integral_images", ctypes.c_int, [_P, _P, _P]),
+    ("integral_images_u32", ctypes.c_int, [_P, _P, _P, _P]),
+    ("displacement_field", ctypes.c_int, [_P, _P]),
+    ("advect_samples", ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    ("regularize", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
+    ("regularize_host", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
+    ("quality_metrics", ctypes.c_int, [_P, _P]),
+    ("declutter_sync", ctypes.c_int, [_P]),
+    ("declutter_profile_regularize", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]),
+    ("declutter_kernel_name", ctypes.c_char_p, [ctypes.c_int32]),
+    ("declutter_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("declutter_last_error", ctypes.c_char_p, []),
+]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+            "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGS:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return [s[0] for s in _SIGS]
+
+
+def declutter_status_string(status: int) -> str:
+    return load_library().declutter_status_string(int(status)).decode()
+
+
+def declutter_last_error() -> str:
+    return load_library().declutter_last_error().decode()
+
+
+def declutter_kernel_name(k: int):
+    r = load_library().declutter_kernel_name(int(k))
+    return None if r is None else r.decode()
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise DeclutterError(status, where, f"{declutter_status_string(status)}: {declutter_last_error()}")
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    """Device pointer of a CUDA tensor (or None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Context:
+    """Owner of a ``dc_ctx*``; call :func:`declutter_destroy` (or use ``with``)."""
+    handle: ctypes.c_void_p
+    params: dc_params
+    device: int
+
+    @property
+    def N(self) -> int:
+        return 1 << int(self.params.log2_res)
+
+    def info(self) -> dc_info:
+        return declutter_get_info(self)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        declutter_destroy(self)
+
+
+def declutter_create(log2_res: int, kernel_r: int = -1, sigma: float = 0.0, d0: float = -1.0,
+                     pixel_center: bool = False, clamp_positions: bool = True,
+                     carry_mode: int = DC_CARRY_COMPENSATED, band_rows: int = 0,
+                     device: int | None = None, stream=None) -> Context:
+    """Create a context.  ``stream``: a ``torch.cuda.Stream`` or None for the
+    current torch stream (the library makes its own stream, ordered with the
+    legacy default stream, when that is the default stream)."""
+    import torch
+    lib = load_library()
+    if device is None:
+        device = torch.cuda.current_device()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    sp = getattr(stream, "cuda_stream", stream) or 0
+    p = dc_params()
+    p.log2_res = int(log2_res)
+    p.kernel_r = int(kernel_r)
+    p.sigma = float(sigma)
+    p.d0 = float(d0)
+    p.pixel_center = int(bool(pixel_center))
+    p.clamp_positions = int(bool(clamp_positions))
+    p.carry_mode = int(carry_mode)
+    p.band_rows = int(band_rows)
+    h = ctypes.c_void_p()
+    _check(lib.declutter_create(ctypes.byref(p), int(device), ctypes.c_void_p(sp) if sp else None,
+                                ctypes.byref(h)), "declutter_create")
+    return Context(h, p, int(device))
+
+
+def declutter_destroy(ctx: Context) -> None:
+    if ctx.handle:
+        _check(load_library().declutter_destroy(ctx.handle), "declutter_destroy")
+        ctx.handle = ctypes.c_void_p()
+
+
+def declutter_get_info(ctx: Context) -> dc_info:
+    out = dc_info()
+    _check(load_library().declutter_get_info(ctx.handle, ctypes.byref(out)), "declutter_get_info")
+    return out
+
+
+def _pos_args(pos):
+    import torch
+    if pos.dim() != 2 or pos.shape[1] != 2:
+        raise ValueError("pos must have shape [n, 2]")
+    return _ptr(pos, torch.float32, name="pos"), int(pos.shape[0])
+
+
+def splat_density(ctx: Context, pos, counts_out=None, density_out=None) -> None:
+    import torch
+    pp, n = _pos_args(pos)
+    NN = ctx.N * ctx.N
+    _check(load_library().splat_density(ctx.handle, pp, n,
+                                        _ptr(counts_out, torch.int32, NN, "counts_out"),
+                                        _ptr(density_out, torch.float32, NN, "density_out")), "splat_density")
+
+
+def _u64(t, NN, name):
+    import torch
+    if t is None:
+        return None
+    if t.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        raise TypeError(f"{name} must be a 64-bit integer tensor")
+    return _ptr(t, None, NN, name)
+
+
+def integral_images(ctx: Context, alpha_out=None, alpha_t_out=None) -> None:
+    """Exact mode: int64/uint64 outputs; float mode: float32 outputs."""
+    import torch
+    NN = ctx.N * ctx.N
+    if int(ctx.params.kernel_r) == 0:
+        a, b = _u64(alpha_out, NN, "alpha_out"), _u64(alpha_t_out, NN, "alpha_t_out")
+    else:
+        a = _ptr(alpha_out, torch.float32, NN, "alpha_out")
+        b = _ptr(alpha_t_out, torch.float32, NN, "alpha_t_out")
+    _check(load_library().integral_images(ctx.handle, a, b), "integral_images")
+
+
+def integral_images_u32(ctx: Context, grid, alpha_out=None, alpha_t_out=None) -> None:
+    """``grid``: CUDA int32 tensor holding uint32 bit patterns, N*N."""
+    import torch
+    NN = ctx.N * ctx.N
+    g = _ptr(grid, torch.int32, NN, "grid")
+    _check(load_library().integral_images_u32(ctx.handle, g, _u64(alpha_out, NN, "alpha_out"),
+                                              _u64(alpha_t_out, NN, "alpha_t_out")), "integral_images_u32")
+
+
+def displacement_field(ctx: Context, disp_out=None) -> None:
+    import torch
+    _check(load_library().displacement_field(ctx.handle, _ptr(disp_out, torch.float32, 2 * ctx.N * ctx.N,
+                                                              "disp_out")), "displacement_field")
+
+
+def advect_samples(ctx: Context, pos) -> None:
+    pp, n = _pos_args(pos)
+    _check(load_library().advect_samples(ctx.handle, pp, n), "advect_samples")
+
+
+def regularize(ctx: Context, pos, iters: int, uniformity: bool = False):
+    pp, n = _pos_args(pos)
+    out = (ctypes.c_double * max(int(iters), 1))() if uniformity else None
+    _check(load_library().regularize(ctx.handle, pp, n, int(iters), out), "regularize")
+    return list(out)[:iters] if uniformity else None
+
+
+def regularize_host(ctx: Context, host_pos, iters: int, uniformity: bool = False):
+    """``host_pos``: numpy float32 [n, 2] or a CPU torch tensor (pinned for
+    asynchronous copies); updated in place."""
+    if isinstance(host_pos, np.ndarray):
+        if host_pos.dtype != np.float32 or not host_pos.flags["C_CONTIGUOUS"]:
+            raise TypeError("host_pos must be C-contiguous float32")
+        ptr, n = host_pos.ctypes.data, host_pos.shape[0]
+    else:
+        if host_pos.is_cuda or not host_pos.is_contiguous():
+            raise TypeError("host_pos must be a contiguous CPU tensor")
+        ptr, n = host_pos.data_ptr(), host_pos.shape[0]
+    out = (ctypes.c_double * max(int(iters), 1))() if uniformity else None
+    _check(load_library().regularize_host(ctx.handle, ctypes.c_void_p(ptr), int(n), int(iters), out),
+           "regularize_host")
+    return list(out)[:iters] if uniformity else None
+
+
+def quality_metrics(ctx: Context) -> dict:
+    out = (ctypes.c_double * 3)()
+    _check(load_library().quality_metrics(ctx.handle, out), "quality_metrics")
+    return {"bin_std": out[0], "bin_cv": out[1], "overplot": out[2]}
+
+
+def declutter_sync(ctx: Context) -> None:
+    _check(load_library().declutter_sync(ctx.handle), "declutter_sync")
+
+
+def declutter_profile_regularize(ctx: Context, pos, iters: int) -> dict:
+    pp, n = _pos_args(pos)
+    ms = (ctypes.c_float * KERNEL_KINDS)()
+    cnt = (ctypes.c_int32 * KERNEL_KINDS)()
+    _check(load_library().declutter_profile_regularize(ctx.handle, pp, n, int(iters), ms, cnt),
+           "declutter_profile_regularize")
+    return {declutter_kernel_name(k): {"ms": float(ms[k]), "launches": int(cnt[k])} for k in range(KERNEL_KINDS)}

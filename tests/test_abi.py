@@ -1,0 +1,86 @@
+"""The C-ABI library loads, exports every symbol its header declares, and
+validates arguments on the host (no GPU needed, no compute calls)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2408_06513_gb300 import build as dc_build
+from paper_2408_06513_gb300 import declutter as dc
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "declutter.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    dc_build.build()
+    return dc.load_library()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("declutter_create", "splat_density", "integral_images", "displacement_field",
+                     "advect_samples", "regularize"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(dc.exported_symbols()) == names
+
+
+def test_status_strings(lib):
+    assert dc.declutter_status_string(0) == "ok"
+    for s in range(1, 8):
+        assert dc.declutter_status_string(s) not in ("ok", "unknown status")
+    assert dc.declutter_kernel_name(0) == "splat"
+    assert dc.declutter_kernel_name(99) is None
+
+
+def _params(**kw):
+    p = dc.dc_params()
+    p.log2_res = kw.get("log2_res", 9)
+    p.kernel_r = kw.get("kernel_r", -1)
+    p.sigma = kw.get("sigma", 0.0)
+    p.d0 = kw.get("d0", -1.0)
+    p.pixel_center = kw.get("pixel_center", 0)
+    p.clamp_positions = kw.get("clamp_positions", 1)
+    p.carry_mode = kw.get("carry_mode", 0)
+    p.band_rows = kw.get("band_rows", 0)
+    return p
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(log2_res=3), 2),
+    (dict(log2_res=14), 2),
+    (dict(kernel_r=65), 1),
+    (dict(log2_res=4, kernel_r=16), 1),
+    (dict(pixel_center=2), 1),
+    (dict(carry_mode=5), 1),
+    (dict(band_rows=3), 1),
+    (dict(band_rows=128), 1),
+])
+def test_create_rejects_bad_parameters(lib, kw, status):
+    h = ctypes.c_void_p()
+    p = _params(**kw)
+    st = lib.declutter_create(ctypes.byref(p), 0, None, ctypes.byref(h))
+    assert st == status
+    assert not h.value
+    assert dc.declutter_last_error()
+
+
+def test_calls_on_null_context_fail_cleanly(lib):
+    assert lib.regularize(None, None, 0, 1, None) == 1
+    assert lib.declutter_sync(None) == 1
+    assert lib.declutter_destroy(None) == 0

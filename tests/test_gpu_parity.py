@@ -1,0 +1,414 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bars (written here, derived in the design notes):
+  * counts and integer integral images: bit-exact;
+  * float displacement: max abs error <= 1e-4 pixel per iteration against the
+    FP64 oracle on the same float32 inputs;
+  * exact-mode displacement: within half an ulp of float32 (relative 2^-24)
+    plus 1e-12 of the FP64 value;
+  * positions: the displacement bound plus one float32 ulp of storage rounding.
+Multi-iteration runs are teacher-forced: every GPU iteration starts from the
+oracle's float32 positions of the previous iteration.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu]
+
+DISP_TOL_PX = 1e-4
+
+
+@pytest.fixture(scope="module")
+def dc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_06513_gb300 import build as dc_build
+    dc_build.build()
+    from paper_2408_06513_gb300 import declutter
+    declutter.load_library()
+    return declutter
+
+
+DEV = "cuda:0"
+
+
+def to_dev(z):
+    return torch.from_numpy(np.ascontiguousarray(z, dtype=np.float32)).to(DEV)
+
+
+def u32(t, N):
+    return t.cpu().numpy().view(np.uint32).reshape(N, N)
+
+
+def u64(t, N):
+    return t.cpu().numpy().view(np.uint64).reshape(N, N)
+
+
+def gpu_step(dc, ctx, z, want_inims=False):
+    """One GPU iteration step by step; returns dict of intermediates."""
+    N = ctx.N
+    pos = to_dev(z)
+    counts = torch.empty(N * N, dtype=torch.int32, device=DEV)
+    dens = torch.empty(N * N, dtype=torch.float32, device=DEV) if ctx.params.kernel_r != 0 else None
+    disp = torch.empty(2 * N * N, dtype=torch.float32, device=DEV)
+    dc.splat_density(ctx, pos, counts_out=counts, density_out=dens)
+    out = {}
+    if want_inims:
+        if ctx.params.kernel_r == 0:
+            a = torch.empty(N * N, dtype=torch.int64, device=DEV)
+            at = torch.empty(N * N, dtype=torch.int64, device=DEV)
+        else:
+            a = torch.empty(N * N, dtype=torch.float32, device=DEV)
+            at = torch.empty(N * N, dtype=torch.float32, device=DEV)
+        dc.integral_images(ctx, a, at)
+        out["alpha"], out["alpha_t"] = a, at
+    dc.displacement_field(ctx, disp)
+    dc.advect_samples(ctx, pos)
+    dc.declutter_sync(ctx)
+    out["counts"] = u32(counts, N).astype(np.uint64)
+    out["density"] = None if dens is None else dens.cpu().numpy().reshape(N, N).astype(np.float64)
+    out["D"] = disp.cpu().numpy().reshape(N, N, 2).astype(np.float64)
+    out["pos"] = pos.cpu().numpy()
+    return out
+
+
+def pos_tol_px(N):
+    return DISP_TOL_PX + N * float(np.spacing(np.float32(1.0)))
+
+
+def check_iteration(dc, ctx, z, p, exact_disp=False):
+    N = ctx.N
+    ref_new, aux = oracle.iterate(z, p, keep=True)
+    g = gpu_step(dc, ctx, z)
+    assert np.array_equal(g["counts"], aux["counts"])
+    if g["density"] is not None:
+        scale = max(1.0, float(aux["d_r"].max()))
+        assert np.max(np.abs(g["density"] - aux["d_r"])) <= 2e-6 * scale
+    err = np.abs(g["D"] - aux["D"])
+    if exact_disp:
+        assert np.all(err <= 6e-8 * np.abs(aux["D"]) + 1e-12), float(err.max() * N)
+    else:
+        assert float(err.max()) * N <= DISP_TOL_PX, float(err.max()) * N
+    perr = float(np.max(np.abs(g["pos"].astype(np.float64) - ref_new))) * N
+    assert perr <= pos_tol_px(N), perr
+    return float(err.max()) * N
+
+
+# --------------------------------------------------------------------------
+# Step by step on the 128x128 workload, exact and smoothed
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("r", [0, 2])
+def test_tiny_teacher_forced_iterations(dc, r):
+    z, _ = synth.tiny_mixture()
+    p = oracle.Params(log2_res=7, kernel_r=r)
+    traj = oracle.regularize(z, p, 4)
+    ctx = dc.declutter_create(7, kernel_r=r)
+    try:
+        for k in range(4):
+            check_iteration(dc, ctx, traj[k], p, exact_disp=(r == 0))
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+@pytest.mark.parametrize("k,r,band_rows", [(4, 0, 0), (4, 2, 1), (5, 0, 2), (6, 3, 4), (7, 0, 8),
+                                           (8, 2, 16), (9, 0, 64), (9, 4, 1)])
+def test_sizes_and_band_heights(dc, k, r, band_rows):
+    z, _ = synth.tiny_mixture(5003, seed=k + r)
+    p = oracle.Params(log2_res=k, kernel_r=r)
+    ctx = dc.declutter_create(k, kernel_r=r, band_rows=band_rows)
+    try:
+        check_iteration(dc, ctx, z, p, exact_disp=(r == 0))
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+@pytest.mark.parametrize("r", [0, 2])
+def test_integral_images_match_oracle(dc, r):
+    k = 7
+    N = 1 << k
+    z, _ = synth.tiny_mixture(20_000, seed=4)
+    ctx = dc.declutter_create(k, kernel_r=r)
+    try:
+        g = gpu_step(dc, ctx, z, want_inims=True)
+    finally:
+        dc.declutter_destroy(ctx)
+    p = oracle.Params(log2_res=k, kernel_r=r)
+    c, d_r = oracle.density(z, p)
+    if r == 0:
+        a_ref, at_ref = oracle.sat_u64(c.astype(np.uint32))
+        assert np.array_equal(u64(g["alpha"], N), a_ref)
+        assert np.array_equal(u64(g["alpha_t"], N), at_ref)
+    else:
+        ims = oracle.inims(d_r)
+        C = d_r.sum()
+        a = g["alpha"].cpu().numpy().reshape(N, N)
+        at = g["alpha_t"].cpu().numpy().reshape(N, N)
+        assert np.max(np.abs(a - ims["alpha"])) <= 2e-6 * C
+        assert np.max(np.abs(at - ims["alpha_t"])) <= 2e-6 * C
+
+
+@pytest.mark.parametrize("k", [4, 8, 9, 10, 11])
+def test_integral_images_u32_sweep_exact(dc, k):
+    N = 1 << k
+    grid = synth.sat_grid(k)
+    a_ref, at_ref = oracle.sat_u64(grid)
+    ctx = dc.declutter_create(k, kernel_r=0)
+    try:
+        g = torch.from_numpy(grid.view(np.int32)).to(DEV)
+        a = torch.empty(N * N, dtype=torch.int64, device=DEV)
+        at = torch.empty(N * N, dtype=torch.int64, device=DEV)
+        dc.integral_images_u32(ctx, g, a, at)
+        dc.declutter_sync(ctx)
+    finally:
+        dc.declutter_destroy(ctx)
+    assert np.array_equal(u64(a, N), a_ref)
+    assert np.array_equal(u64(at, N), at_ref)
+
+
+@pytest.mark.parametrize("k", [12, 13])
+def test_integral_images_u32_large_exact(dc, k):
+    # the largest grids of the sweep: full comparison, values beyond 2^32
+    N = 1 << k
+    grid = synth.sat_grid(k)
+    a_ref, at_ref = oracle.sat_u64(grid)
+    if k == 13:
+        assert int(a_ref[-1, -1]) > 2**32
+    ctx = dc.declutter_create(k, kernel_r=0)
+    try:
+        g = torch.from_numpy(grid.view(np.int32)).to(DEV)
+        a = torch.empty(N * N, dtype=torch.int64, device=DEV)
+        at = torch.empty(N * N, dtype=torch.int64, device=DEV)
+        dc.integral_images_u32(ctx, g, a, at)
+        dc.declutter_sync(ctx)
+        assert np.array_equal(u64(a, N), a_ref)
+        assert np.array_equal(u64(at, N), at_ref)
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
+# Options and edge cases
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("opts", [
+    dict(pixel_center=True),
+    dict(clamp_positions=False),
+    dict(d0=0.25),
+    dict(sigma=1.1),
+    dict(carry_mode=1),
+])
+@pytest.mark.parametrize("r", [0, 3])
+def test_options(dc, opts, r):
+    if r == 0 and ("sigma" in opts or "carry_mode" in opts):
+        pytest.skip("smoothing option")
+    k = 7
+    z, _ = synth.tiny_mixture(8000, seed=21)
+    p = oracle.Params(log2_res=k, kernel_r=r, sigma=opts.get("sigma", 0.0), d0=opts.get("d0", -1.0),
+                      pixel_center=opts.get("pixel_center", False),
+                      clamp_positions=opts.get("clamp_positions", True))
+    ctx = dc.declutter_create(k, kernel_r=r, **opts)
+    try:
+        check_iteration(dc, ctx, z, p, exact_disp=(r == 0))
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+@pytest.mark.parametrize("case", ["empty", "one", "one_pixel", "borders", "ragged"])
+@pytest.mark.parametrize("r", [0, 2])
+def test_edge_cases(dc, case, r):
+    k = 6
+    rng = np.random.default_rng(3)
+    if case == "empty":
+        z = np.zeros((0, 2), np.float32)
+    elif case == "one":
+        z = np.array([[0.3, 0.7]], np.float32)
+    elif case == "one_pixel":
+        z = np.full((100_000, 2), 0.41, np.float32)
+    elif case == "borders":
+        z = np.array([[0, 0], [1, 1], [1, 0], [0, 1], [-0.2, 0.5], [0.5, 1.7], [0.999999, 0.5]] * 50,
+                     np.float32)
+    else:
+        z = rng.uniform(0, 1, size=(10_007, 2)).astype(np.float32)
+    p = oracle.Params(log2_res=k, kernel_r=r)
+    ctx = dc.declutter_create(k, kernel_r=r)
+    try:
+        if case == "empty":
+            g = gpu_step(dc, ctx, z)
+            assert g["counts"].sum() == 0 and np.all(g["D"] == 0)
+        else:
+            check_iteration(dc, ctx, z, p, exact_disp=(r == 0))
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+@pytest.mark.parametrize("pixel_center", [False, True])
+def test_even_layout_is_exact_fixed_point(dc, pixel_center):
+    # Sec. 4.2: the defect-corrected mapping is the identity for an even
+    # layout; the exact path gives exactly zero displacement.
+    k = 6
+    z = synth.uniform_grid_samples(k, per_pixel=3, pixel_center=pixel_center)
+    ctx = dc.declutter_create(k, kernel_r=0, pixel_center=pixel_center)
+    try:
+        g = gpu_step(dc, ctx, z)
+        assert np.all(g["D"] == 0.0)
+        assert np.array_equal(g["pos"], z)
+    finally:
+        dc.declutter_destroy(ctx)
+    ctx = dc.declutter_create(k, kernel_r=2, pixel_center=pixel_center)
+    try:
+        g = gpu_step(dc, ctx, z)
+        assert float(np.max(np.abs(g["D"]))) * (1 << k) <= 1e-6
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
+# regularize(): graph path, determinism, host path, metrics
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("r", [0, 2])
+def test_regularize_graph_teacher_forced(dc, r):
+    z, _ = synth.tiny_mixture()
+    k = 7
+    N = 1 << k
+    p = oracle.Params(log2_res=k, kernel_r=r)
+    traj = oracle.regularize(z, p, 4)
+    ctx = dc.declutter_create(k, kernel_r=r)
+    try:
+        pos = to_dev(z)
+        for it in range(4):
+            pos.copy_(to_dev(traj[it]))
+            dc.regularize(ctx, pos, 1)
+            dc.declutter_sync(ctx)
+            err = float(np.max(np.abs(pos.cpu().numpy().astype(np.float64) - traj[it + 1]))) * N
+            assert err <= pos_tol_px(N), (it, err)
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+@pytest.mark.parametrize("r", [0, 2])
+def test_regularize_free_running_and_metrics(dc, r):
+    z, _ = synth.tiny_mixture()
+    k = 7
+    N = 1 << k
+    p = oracle.Params(log2_res=k, kernel_r=r)
+    traj = oracle.regularize(z, p, 4)
+    ref_u = [oracle.quality(oracle.splat(t, k))["bin_std"] for t in traj[1:]]
+    ctx = dc.declutter_create(k, kernel_r=r)
+    try:
+        pos = to_dev(z)
+        u = dc.regularize(ctx, pos, 4, uniformity=True)
+        q = dc.quality_metrics(ctx)
+    finally:
+        dc.declutter_destroy(ctx)
+    assert all(a > b for a, b in zip(u, u[1:])), u
+    assert np.allclose(u, ref_u, rtol=0.02), (u, ref_u)
+    d = np.abs(pos.cpu().numpy().astype(np.float64) - traj[-1]) * N
+    assert np.median(d) < 1e-3 and np.percentile(d, 99) < 0.1, (np.median(d), np.percentile(d, 99))
+    qo = oracle.quality(oracle.splat(pos.cpu().numpy(), k))
+    assert abs(q["bin_std"] - qo["bin_std"]) <= 1e-9 * max(1.0, qo["bin_std"])
+    assert abs(q["overplot"] - qo["overplot"]) <= 1e-12
+
+
+@pytest.mark.parametrize("r", [0, 2])
+def test_regularize_split_is_bitwise_identical(dc, r):
+    # resume: regularize(4) == regularize(1) + regularize(3), bit for bit
+    z, _ = synth.tiny_mixture()
+    ctx = dc.declutter_create(7, kernel_r=r)
+    try:
+        a = to_dev(z)
+        b = to_dev(z)
+        dc.regularize(ctx, a, 4)
+        dc.regularize(ctx, b, 1)
+        dc.regularize(ctx, b, 3)
+        dc.declutter_sync(ctx)
+        assert torch.equal(a, b)
+        c = to_dev(z)
+        dc.regularize(ctx, c, 4)
+        dc.declutter_sync(ctx)
+        assert torch.equal(a, c)
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+def test_regularize_host_matches_device(dc):
+    z, _ = synth.tiny_mixture()
+    ctx = dc.declutter_create(7, kernel_r=2)
+    try:
+        a = to_dev(z)
+        dc.regularize(ctx, a, 3)
+        dc.declutter_sync(ctx)
+        h = torch.from_numpy(z.copy()).pin_memory()
+        dc.regularize_host(ctx, h, 3)
+        assert torch.equal(a.cpu(), h)
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+def test_profile_counts_launches(dc):
+    z, _ = synth.tiny_mixture()
+    ctx = dc.declutter_create(7, kernel_r=2)
+    try:
+        pos = to_dev(z)
+        prof = dc.declutter_profile_regularize(ctx, pos, 3)
+    finally:
+        dc.declutter_destroy(ctx)
+    for name in ("splat", "smooth", "band_aggregate", "band_carry", "band_final", "advect"):
+        assert prof[name]["launches"] == 3 and prof[name]["ms"] > 0
+
+
+def test_bad_arguments_are_rejected(dc):
+    ctx = dc.declutter_create(6, kernel_r=0)
+    try:
+        pos = torch.zeros(10, 2, device=DEV)
+        with pytest.raises(dc.DeclutterError):
+            dc.advect_samples(ctx, pos)          # before any displacement
+        with pytest.raises(dc.DeclutterError):
+            dc.displacement_field(ctx)           # before any splat
+        lib = dc.load_library()
+        import ctypes
+        mis = ctypes.c_void_p(pos.data_ptr() + 4)
+        assert lib.splat_density(ctx.handle, mis, 4, None, None) == 1
+        assert lib.splat_density(ctx.handle, ctypes.c_void_p(pos.data_ptr()), -1, None, None) == 1
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
+# Full-size workloads
+# --------------------------------------------------------------------------
+
+def test_gmm20_512_full_size_one_iteration(dc):
+    # 1M samples, 512x512, r = 4: the launch configuration the benchmark times
+    z, _ = synth.gmm20()
+    p = oracle.Params(log2_res=9, kernel_r=4)
+    ctx = dc.declutter_create(9, kernel_r=4)
+    try:
+        check_iteration(dc, ctx, z, p)
+        traj = oracle.regularize(z, p, 2)
+        pos = to_dev(traj[1])
+        dc.regularize(ctx, pos, 1)
+        dc.declutter_sync(ctx)
+        err = float(np.max(np.abs(pos.cpu().numpy().astype(np.float64) - traj[2]))) * 512
+        assert err <= pos_tol_px(512), err
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+@pytest.mark.parametrize("carry_mode", [0, 1])
+def test_student_t_2048_full_size_one_iteration(dc, carry_mode):
+    # 16M heavy-tailed samples, 2048x2048, r = 16
+    z, _ = synth.student_t_clusters()
+    p = oracle.Params(log2_res=11, kernel_r=16)
+    ctx = dc.declutter_create(11, kernel_r=16, carry_mode=carry_mode)
+    try:
+        err = check_iteration(dc, ctx, z, p)
+        print(f"2048^2 carry_mode={carry_mode}: max |D - D_fp64| = {err:.3e} px")
+    finally:
+        dc.declutter_destroy(ctx)
