@@ -192,6 +192,36 @@ dc_status declutter_sync(dc_ctx *ctx);
 dc_status declutter_profile_regularize(dc_ctx *ctx, float *pos_xy, int64_t n, int32_t iters,
                                        float *kernel_ms_out, int32_t *launches_out);
 
+/* No-allocation variant of integral_images_u32(), for callers that cannot
+ * allocate device memory when they need the result: code running while a
+ * stream is captured into a CUDA graph (where cudaMalloc and cudaFree are not
+ * allowed), loops that cannot afford the synchronisation an allocation may
+ * imply, and hosts whose device memory comes from their own pool.  The paper
+ * has no counterpart; it is a deployment variant of the same computation.
+ *
+ * Needs no context.  Writes the exact uint64 alpha and alpha_t of the device
+ * uint32[N*N] array grid, N = 2^log2_res, into alpha_out / alpha_t_out
+ * (device, 16-byte aligned, either may be NULL), on cuda_stream (NULL = the
+ * legacy default stream), asynchronously, on the calling thread's current
+ * device.  Results are bit-identical to integral_images_u32().
+ *
+ * Scratch: one fixed device array inside the library,
+ * DC_NOALLOC_SCRATCH_BYTES long, held by every GPU that loads the library
+ * until the process exits.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.  log2_res above DC_NOALLOC_MAX_LOG2_RES (grids larger
+ * than 1024 x 1024) is rejected with DC_ERR_INVALID_ARG, below 4 with
+ * DC_ERR_NOT_POW2; declutter_last_error() gives the reason.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents (none of it needs to start at zero): calls that
+ * overlap on the GPU, for instance on two streams, race and must not be
+ * issued. */
+#define DC_NOALLOC_MAX_LOG2_RES 10
+#define DC_NOALLOC_SCRATCH_BYTES 8912896
+dc_status integral_images_u32_noalloc(const uint32_t *grid, uint32_t log2_res, uint64_t *alpha_out,
+                                      uint64_t *alpha_t_out, void *cuda_stream);
+
 /* Name of kernel kind k (0 <= k < DC_KERNEL_KINDS), or NULL. */
 const char *declutter_kernel_name(int32_t k);
 

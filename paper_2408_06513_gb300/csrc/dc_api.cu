@@ -219,6 +219,8 @@ const char *kKernelNames[DC_KERNEL_KINDS] = {"splat",  "smooth", "band_aggregate
 
 }  // namespace
 
+void dc::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
 extern "C" {
 
 const char *declutter_status_string(dc_status s)

@@ -85,6 +85,7 @@ cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_
 cudaError_t launch_band_final(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a);
 int smooth_smem_bytes(int r);
 cudaError_t prepare_kernels();  // per-device kernel attributes; call with the device current
+void set_last_error(const char *msg);  // message returned by declutter_last_error()
 
 }  // namespace dc
 

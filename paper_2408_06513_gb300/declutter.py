@@ -28,6 +28,7 @@ __all__ = [
     "integral_images_u32", "displacement_field", "advect_samples", "regularize", "regularize_host",
     "quality_metrics", "declutter_sync", "declutter_profile_regularize", "declutter_kernel_name",
     "declutter_status_string", "declutter_last_error", "DC_CARRY_COMPENSATED", "DC_CARRY_F64",
+    "integral_images_u32_noalloc", "DC_NOALLOC_MAX_LOG2_RES",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -36,6 +37,7 @@ KERNEL_KINDS = 8
 
 DC_CARRY_COMPENSATED = 0
 DC_CARRY_F64 = 1
+DC_NOALLOC_MAX_LOG2_RES = 10
 
 
 class DeclutterError(RuntimeError):
@@ -90,6 +92,7 @@ _SIGS = [
     ("quality_metrics", ctypes.c_int, [_P, _P]),
     ("declutter_sync", ctypes.c_int, [_P]),
     ("declutter_profile_regularize", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]),
+    ("integral_images_u32_noalloc", ctypes.c_int, [_P, ctypes.c_uint32, _P, _P, _P]),
     ("declutter_kernel_name", ctypes.c_char_p, [ctypes.c_int32]),
     ("declutter_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("declutter_last_error", ctypes.c_char_p, []),
@@ -312,3 +315,20 @@ def declutter_profile_regularize(ctx: Context, pos, iters: int) -> dict:
     _check(load_library().declutter_profile_regularize(ctx.handle, pp, n, int(iters), ms, cnt),
            "declutter_profile_regularize")
     return {declutter_kernel_name(k): {"ms": float(ms[k]), "launches": int(cnt[k])} for k in range(KERNEL_KINDS)}
+
+
+def integral_images_u32_noalloc(grid, log2_res: int, alpha_out=None, alpha_t_out=None, stream=None) -> None:
+    """No-allocation integral images of a uint32 grid (int32 CUDA tensor
+    holding the bit patterns); for callers that cannot allocate device
+    memory at call time.  ``stream``: a ``torch.cuda.Stream`` or None for the
+    current torch stream."""
+    import torch
+    NN = 1 << (2 * int(log2_res))
+    g = _ptr(grid, torch.int32, NN, "grid")
+    if stream is None:
+        stream = torch.cuda.current_stream(grid.device)
+    sp = getattr(stream, "cuda_stream", stream) or 0
+    _check(load_library().integral_images_u32_noalloc(g, int(log2_res), _u64(alpha_out, NN, "alpha_out"),
+                                                      _u64(alpha_t_out, NN, "alpha_t_out"),
+                                                      ctypes.c_void_p(sp) if sp else None),
+           "integral_images_u32_noalloc")
