@@ -162,7 +162,7 @@ def algorithmic_bytes(kind: str, n: int, N: int, info) -> float:
         "band_final": 12.0 * NN,                # read d_r, write the float2 displacement
         "advect": 16.0 * n,                     # read + write the samples
         "quality": 4.0 * NN,
-        "memset": 4.0 * NN,
+        "reorder": 4.0 * NN * 3 + 8.0 * n * 2 + 4.0 * n * 2 + 8.0 * n,  # scan, scatter, way back
     }
     return table[kind]
 
@@ -294,7 +294,8 @@ def run_gpu(args, world, rank, local, pg):
     n, k, r, iters = WORKLOAD["n"], WORKLOAD["log2_res"], WORKLOAD["kernel_r"], WORKLOAD["iters"]
     N = 1 << k
     z, _ = synth.gmm20(n, seed=2 + rank)
-    ctx = dc.declutter_create(k, kernel_r=r, device=local, stream=stream)
+    ctx = dc.declutter_create(k, kernel_r=r, device=local, stream=stream, band_rows=args.band_rows,
+                              keep_order=args.keep_order)
     info = dc.declutter_get_info(ctx)
     src = torch.from_numpy(z).to(dev)
     pos = torch.empty_like(src)
@@ -348,26 +349,19 @@ def run_gpu(args, world, rank, local, pg):
     e2e_s = max_over_ranks(pg, sum(e2e_times) / len(e2e_times),
                            dev if pg is not None and torch.distributed.get_backend() == "nccl" else None)
 
-    # per-kernel device times: the same kernels and launch shapes, one event
-    # pair around each launch (declutter_profile_regularize)
-    prof_steps = max(1, min(args.steps, 5))
-    tot = {}
-    for _ in range(prof_steps):
-        reset_and_flush()
-        torch.cuda.synchronize()
-        prof = dc.declutter_profile_regularize(ctx, pos, iters)
-        for kname, v in prof.items():
-            t = tot.setdefault(kname, {"ms": 0.0, "launches": 0})
-            t["ms"] += v["ms"]
-            t["launches"] += v["launches"]
+    # per-kernel device times inside the graph: the step is captured as in
+    # regularize(); each kernel kind's time is the growth of the step when
+    # every launch of that kind is issued twice (declutter_profile_regularize)
+    prof = dc.declutter_profile_regularize(ctx, pos, iters, reps=max(5, min(args.steps, 20)), reset_src=src)
     kernels = {}
-    for kname, v in tot.items():
-        if v["launches"] == 0 or kname == "memset":
+    for kname, v in prof["kernels"].items():
+        if v["launches"] == 0:
             continue
         avg_ms = v["ms"] / v["launches"]
         by = algorithmic_bytes(kname, n, N, info)
-        kernels[kname] = {"avg_us": avg_ms * 1e3, "launches_per_step": v["launches"] // prof_steps,
-                          "GBps": by / (avg_ms * 1e-3) / 1e9}
+        kernels[kname] = {"avg_us": avg_ms * 1e3, "launches_per_step": v["launches"],
+                          "share": v["ms"] / max(prof["step_ms"], 1e-9),
+                          "GBps": by / max(avg_ms * 1e-3, 1e-12) / 1e9}
     dominant = max(kernels, key=lambda kk: kernels[kk]["avg_us"] * kernels[kk]["launches_per_step"])
     peaks, peak_src = measured_peaks()
     dk = kernels[dominant]
@@ -377,7 +371,7 @@ def run_gpu(args, world, rank, local, pg):
                 "traffic": ncu_traffic(dominant),
                 "algorithmic_bytes_per_launch": algorithmic_bytes(dominant, n, N, info)}
 
-    launches_per_step = iters * info.kernels_per_iter
+    launches_per_step = sum(v["launches"] for v in prof["kernels"].values())
     value = world * n * iters / (ms_max * 1e-3) / 1e6
     e2e_value = world * n * iters / e2e_s / 1e6
 
@@ -412,6 +406,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--band-rows", type=int, default=0, help="rows per band (0 = library default)")
+    ap.add_argument("--keep-order", action="store_true", help="iterate in the caller's sample order")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -82,7 +82,10 @@ typedef struct {
     int32_t carry_mode;      /* DC_CARRY_* (float mode only) */
     int32_t band_rows;       /* rows per band of the integral-image kernels, a
                                 power of two dividing N; 0 = automatic */
-    int32_t reserved[4];     /* must be zero */
+    int32_t keep_order;      /* regularize(): 0 = iterate on an internal copy of the
+                                samples sorted by pixel (faster; results identical),
+                                1 = iterate in the caller's order */
+    int32_t reserved[3];     /* must be zero */
 } dc_params;
 
 /* Read-back of the configuration a context settled on. */
@@ -182,15 +185,29 @@ dc_status quality_metrics(dc_ctx *ctx, double *out);
  * device status, and clears the latter. */
 dc_status declutter_sync(dc_ctx *ctx);
 
-/* Instrumented run of regularize(): the same kernels with the same launch
- * shapes on the same stream, launched one by one with a CUDA event pair
- * around each.  kernel_ms_out (host float[DC_KERNEL_KINDS]) receives the
- * summed device time per kernel kind and launches_out (host
- * int32[DC_KERNEL_KINDS]) the launch count; either may be NULL.
- * Synchronises. */
+/* Per-kernel device time of regularize(), measured with CUDA events on the
+ * context's stream.  The iteration sequence is captured as a graph exactly
+ * as regularize() captures it and run reps times (after two warm-up runs):
+ * its mean duration goes to *step_ms_out.  Then, for each kernel kind, a
+ * graph in which every launch of that kind is issued twice in a row is run
+ * the same way; the increase of the mean duration over the plain graph is
+ * that kind's in-graph device time per regularize() call, written to
+ * kernel_ms_out[kind] (host float[DC_KERNEL_KINDS]).  launches_out[kind]
+ * (host int32[DC_KERNEL_KINDS]) receives the launches per call.
+ *   pos_xy   : device samples, moved in place by every run.
+ *   reset_src: device float[2n] copied into pos_xy before each run (outside
+ *              the timed span), or NULL to let the samples keep moving.
+ * Any output pointer may be NULL.  Synchronises. */
 #define DC_KERNEL_KINDS 8
-dc_status declutter_profile_regularize(dc_ctx *ctx, float *pos_xy, int64_t n, int32_t iters,
+dc_status declutter_profile_regularize(dc_ctx *ctx, float *pos_xy, const float *reset_src, int64_t n,
+                                       int32_t iters, int32_t reps, float *step_ms_out,
                                        float *kernel_ms_out, int32_t *launches_out);
+
+/* Name of kernel kind k (0 <= k < DC_KERNEL_KINDS), or NULL. */
+const char *declutter_kernel_name(int32_t k);
+
+const char *declutter_status_string(dc_status s);
+const char *declutter_last_error(void);
 
 /* No-allocation variant of integral_images_u32(), for callers that cannot
  * allocate device memory when they need the result: code running while a
@@ -221,12 +238,6 @@ dc_status declutter_profile_regularize(dc_ctx *ctx, float *pos_xy, int64_t n, in
 #define DC_NOALLOC_SCRATCH_BYTES 8912896
 dc_status integral_images_u32_noalloc(const uint32_t *grid, uint32_t log2_res, uint64_t *alpha_out,
                                       uint64_t *alpha_t_out, void *cuda_stream);
-
-/* Name of kernel kind k (0 <= k < DC_KERNEL_KINDS), or NULL. */
-const char *declutter_kernel_name(int32_t k);
-
-const char *declutter_status_string(dc_status s);
-const char *declutter_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -46,25 +46,15 @@ struct DeviceGuard {
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-// Records (kind, start, end) event pairs around launches when profiling.
+// Launch helper for the profiler: a kernel of kind `dup` is launched twice
+// in a row, so that the graph's step time grows by that kernel's own
+// in-graph cost.  Every duplicated kernel is idempotent or only changes data
+// values (the advection moves samples twice), not the amount of work.
 struct Recorder {
-    dc_ctx *ctx = nullptr;
-    int used = 0;
-    int kinds[64];
-    bool overflow = false;
-    void before(cudaStream_t s, int kind)
-    {
-        if (!ctx) return;
-        if (used >= 64) { overflow = true; return; }
-        kinds[used] = kind;
-        cudaEventRecord(ctx->prof_ev[2 * used], s);
-    }
-    void after(cudaStream_t s)
-    {
-        if (!ctx || overflow) return;
-        cudaEventRecord(ctx->prof_ev[2 * used + 1], s);
-        ++used;
-    }
+    int dup = -1;
+    int launches[DC_KERNEL_KINDS] = {};
+    int times(int kind) const { return kind == dup ? 2 : 1; }
+    void count(int kind) { launches[kind] += 1; }
 };
 
 double effective_d0(const dc_ctx *c, int64_t n)
@@ -91,75 +81,154 @@ BandArgs band_args(const dc_ctx *c, const void *src, int mode, int64_t n)
     return a;
 }
 
-cudaError_t enqueue_density(dc_ctx *c, cudaStream_t s, const float *pos, int64_t n, Recorder &rec)
+// memset + splat of pos into `counts`, then (float mode) the smoothing.
+cudaError_t enqueue_density(dc_ctx *c, cudaStream_t s, const float *pos, int64_t n, uint32_t *counts,
+                            uint32_t *zero_out, Recorder &rec)
 {
-    cudaError_t e;
-    rec.before(s, K_MEMSET);
-    e = cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * (size_t)c->g.N * c->g.N, s);
-    rec.after(s);
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)c->g.N * c->g.N, s);
     if (e != cudaSuccess) return e;
-    rec.before(s, K_SPLAT);
-    e = launch_splat(s, reinterpret_cast<const float2 *>(pos), n, c->counts, c->g.log2N);
-    rec.after(s);
+    rec.count(K_SPLAT);
+    for (int t = 0; t < rec.times(K_SPLAT) && e == cudaSuccess; ++t)
+        e = launch_splat(s, reinterpret_cast<const float2 *>(pos), n, counts, c->g.log2N);
     if (e != cudaSuccess) return e;
     if (c->mode == MODE_FLOAT) {
-        rec.before(s, K_SMOOTH);
-        e = launch_smooth(s, c->counts, c->dens, c->g.log2N, c->w);
-        rec.after(s);
+        rec.count(K_SMOOTH);
+        for (int t = 0; t < rec.times(K_SMOOTH) && e == cudaSuccess; ++t)
+            e = launch_smooth(s, counts, c->dens, c->g.log2N, c->w, zero_out);
     }
     return e;
 }
 
 cudaError_t enqueue_inims(dc_ctx *c, cudaStream_t s, const BandArgs &a, int mode, Recorder &rec)
 {
-    cudaError_t e;
-    rec.before(s, K_BAND_AGG);
-    e = launch_band_agg(s, c->g, mode, a);
-    rec.after(s);
+    cudaError_t e = cudaSuccess;
+    rec.count(K_BAND_AGG);
+    for (int t = 0; t < rec.times(K_BAND_AGG) && e == cudaSuccess; ++t) e = launch_band_agg(s, c->g, mode, a);
     if (e != cudaSuccess) return e;
-    rec.before(s, K_CARRY);
-    e = launch_carry(s, c->g, mode, c->p.carry_mode, c->agg, c->carry);
-    rec.after(s);
+    rec.count(K_CARRY);
+    for (int t = 0; t < rec.times(K_CARRY) && e == cudaSuccess; ++t)
+        e = launch_carry(s, c->g, mode, c->p.carry_mode, c->agg, c->carry);
     if (e != cudaSuccess) return e;
-    rec.before(s, K_BAND_FINAL);
-    e = launch_band_final(s, c->g, mode, a);
-    rec.after(s);
+    BandArgs f = a;
+    f.zero_out = nullptr;
+    rec.count(K_BAND_FINAL);
+    for (int t = 0; t < rec.times(K_BAND_FINAL) && e == cudaSuccess; ++t) e = launch_band_final(s, c->g, mode, f);
     return e;
 }
 
+// The iteration of Sec. 4.3, `iters` times.  Counts alternate between two
+// grids: the advection of iteration it also splats the moved samples into
+// the other grid, which the smoothing (float mode) or the aggregate kernel
+// (exact mode) of iteration it has zeroed.  Only the first iteration has its
+// own memset and splat.  With metrics, the quality of the counts after
+// iteration it goes to accumulator slot it.
 cudaError_t enqueue_iterations(dc_ctx *c, cudaStream_t s, float *pos, int64_t n, int iters, int metrics,
                                Recorder &rec)
 {
     cudaError_t e = cudaSuccess;
-    const void *src = c->mode == MODE_FLOAT ? (const void *)c->dens : (const void *)c->counts;
-    BandArgs a = band_args(c, src, c->mode, n);
-    a.disp = c->disp;
+    uint32_t *cb[2] = {c->counts_buf[0], c->counts_buf[1]};
+    const bool reorder = c->p.keep_order == 0 && n > 0;
+    float *ipos = reorder ? reinterpret_cast<float *>(c->spos) : pos;  // samples the iterations move
     if (metrics) {
         e = cudaMemsetAsync(c->qacc, 0, sizeof(unsigned long long) * 3 * (size_t)iters, s);
         if (e != cudaSuccess) return e;
     }
+    int cur = 0;
     for (int it = 0; it < iters; ++it) {
-        if ((e = enqueue_density(c, s, pos, n, rec)) != cudaSuccess) return e;
-        if (metrics && it > 0) {
-            rec.before(s, K_QUALITY);
-            e = launch_quality(s, c->counts, c->g.log2N, c->qacc + 3 * (it - 1));
-            rec.after(s);
+        const int nxt = cur ^ 1;
+        const bool need_next = (it + 1 < iters) || metrics;
+        if (it == 0) {
+            // first splat in the caller's order; its counts key the reordering
+            e = cudaMemsetAsync(cb[cur], 0, sizeof(uint32_t) * (size_t)c->g.N * c->g.N, s);
+            if (e != cudaSuccess) return e;
+            rec.count(K_SPLAT);
+            // a profiling duplicate goes to the other grid, which is zeroed
+            // before its next use, so that these counts stay those of pos
+            for (int t = 0; t < rec.times(K_SPLAT) && e == cudaSuccess; ++t)
+                e = launch_splat(s, reinterpret_cast<const float2 *>(pos), n, t == 0 ? cb[cur] : cb[nxt], c->g.log2N);
+            if (e != cudaSuccess) return e;
+            if (reorder) {
+                rec.count(K_REORDER);
+                for (int t = 0; t < rec.times(K_REORDER) && e == cudaSuccess; ++t) {
+                    e = launch_reorder_scan(s, cb[cur], c->g.log2N, c->partials, c->cursor);
+                    if (e == cudaSuccess)
+                        e = launch_reorder_scatter(s, reinterpret_cast<const float2 *>(pos), n, c->g.log2N, c->cursor,
+                                                   c->spos, c->perm, c->status);
+                }
+                if (e != cudaSuccess) return e;
+            }
+        }
+        if (c->mode == MODE_FLOAT) {
+            rec.count(K_SMOOTH);
+            for (int t = 0; t < rec.times(K_SMOOTH) && e == cudaSuccess; ++t)
+                e = launch_smooth(s, cb[cur], c->dens, c->g.log2N, c->w, need_next ? cb[nxt] : nullptr);
             if (e != cudaSuccess) return e;
         }
+        const void *src = c->mode == MODE_FLOAT ? (const void *)c->dens : (const void *)cb[cur];
+        BandArgs a = band_args(c, src, c->mode, n);
+        a.disp = c->disp;
+        a.zero_out = (c->mode != MODE_FLOAT && need_next) ? cb[nxt] : nullptr;
         if ((e = enqueue_inims(c, s, a, c->mode, rec)) != cudaSuccess) return e;
-        rec.before(s, K_ADVECT);
-        e = launch_advect(s, reinterpret_cast<float2 *>(pos), n, c->disp, c->g.log2N, c->p.pixel_center,
-                          c->p.clamp_positions);
-        rec.after(s);
+        rec.count(K_ADVECT);
+        for (int t = 0; t < rec.times(K_ADVECT) && e == cudaSuccess; ++t)
+            e = launch_advect(s, reinterpret_cast<float2 *>(ipos), n, c->disp, c->g.log2N, c->p.pixel_center,
+                              c->p.clamp_positions, need_next ? cb[nxt] : nullptr);
         if (e != cudaSuccess) return e;
+        if (metrics) {
+            rec.count(K_QUALITY);
+            e = launch_quality(s, cb[nxt], c->g.log2N, c->qacc + 3 * it);
+            if (e != cudaSuccess) return e;
+        }
+        if (need_next) cur = nxt;
     }
-    if (metrics && iters > 0) {
-        if ((e = enqueue_density(c, s, pos, n, rec)) != cudaSuccess) return e;
-        rec.before(s, K_QUALITY);
-        e = launch_quality(s, c->counts, c->g.log2N, c->qacc + 3 * (iters - 1));
-        rec.after(s);
+    if (reorder && iters > 0) {
+        for (int t = 0; t < rec.times(K_REORDER) && e == cudaSuccess; ++t)
+            e = launch_reorder_back(s, c->spos, c->perm, n, reinterpret_cast<float2 *>(pos), c->status);
     }
     return e;
+}
+
+// Reordering buffers for n samples; grown outside any capture.  Cached graphs
+// hold the old pointers, so they are dropped when the buffers move.
+dc_status ensure_sort_buffers(dc_ctx *c, int64_t n)
+{
+    if (c->p.keep_order != 0 || n <= c->sort_cap) return DC_OK;
+    DC_CUDA(cudaStreamSynchronize(c->stream));
+    for (auto &ge : c->graphs) cudaGraphExecDestroy(ge.exec);
+    c->graphs.clear();
+    cudaFree(c->spos);
+    cudaFree(c->perm);
+    c->spos = nullptr;
+    c->perm = nullptr;
+    c->sort_cap = 0;
+    if (cudaMalloc(&c->spos, sizeof(float2) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&c->perm, sizeof(uint32_t) * (size_t)n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DC_ERR_OOM, "reordering buffers for %lld samples", (long long)n);
+    }
+    c->sort_cap = n;
+    return DC_OK;
+}
+
+// Capture the iteration sequence into an executable graph.
+dc_status capture_iterations(dc_ctx *c, float *pos, int64_t n, int iters, int metrics, int dup,
+                             cudaGraphExec_t *out, Recorder *rec_out)
+{
+    cudaGraph_t graph = nullptr;
+    DC_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    Recorder rec;
+    rec.dup = dup;
+    cudaError_t e = enqueue_iterations(c, c->cap_stream, pos, n, iters, metrics, rec);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(DC_ERR_CUDA, "graph capture: %s / %s", cudaGetErrorString(e), cudaGetErrorString(e2));
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(DC_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    if (rec_out) *rec_out = rec;
+    return DC_OK;
 }
 
 dc_status ensure_qslots(dc_ctx *c, int slots)
@@ -215,7 +284,7 @@ dc_status check_samples(const dc_ctx *, const void *pos, int64_t n)
 }
 
 const char *kKernelNames[DC_KERNEL_KINDS] = {"splat",  "smooth", "band_aggregate", "band_carry",
-                                             "band_final", "advect", "quality",   "memset"};
+                                             "band_final", "advect", "quality",   "reorder"};
 
 }  // namespace
 
@@ -251,8 +320,9 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
     *out = nullptr;
     const dc_params p = *params;
     if (p.log2_res < 4 || p.log2_res > 13) return fail(DC_ERR_NOT_POW2, "log2_res = %u", p.log2_res);
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 3; ++k)
         if (p.reserved[k] != 0) return fail(DC_ERR_INVALID_ARG, "reserved fields must be zero");
+    if (p.keep_order != 0 && p.keep_order != 1) return fail(DC_ERR_INVALID_ARG, "keep_order");
     const int N = 1 << p.log2_res;
     int r = p.kernel_r;
     if (r < 0) r = N / 128 < 2 ? 2 : N / 128;
@@ -312,11 +382,14 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
         void **p;
         size_t bytes;
     } allocs[] = {
-        {(void **)&c->counts, NN * sizeof(uint32_t)},
+        {(void **)&c->counts_buf[0], NN * sizeof(uint32_t)},
+        {(void **)&c->counts_buf[1], NN * sizeof(uint32_t)},
         {(void **)&c->disp, NN * sizeof(float2)},
         {&c->agg, agg_bytes},
         {&c->carry, carry_bytes},
         {(void **)&c->status, 256},
+        {(void **)&c->cursor, NN * sizeof(uint32_t)},
+        {(void **)&c->partials, 1024 * sizeof(uint32_t)},
     };
     for (auto &al : allocs) {
         if (cudaMalloc(al.p, al.bytes) != cudaSuccess) {
@@ -335,8 +408,6 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
     if (ensure_qslots(c, 1) != DC_OK) return bail(DC_ERR_OOM);
     if (cudaMemset(c->status, 0, 256) != cudaSuccess) return bail(fail(DC_ERR_CUDA, "cudaMemset status"));
     if (prepare_kernels() != cudaSuccess) return bail(fail(DC_ERR_CUDA, "kernel attributes"));
-    for (int k = 0; k < 128; ++k)
-        if (cudaEventCreate(&c->prof_ev[k]) != cudaSuccess) return bail(fail(DC_ERR_CUDA, "cudaEventCreate"));
     *out = c;
     return DC_OK;
 }
@@ -348,9 +419,10 @@ dc_status declutter_destroy(dc_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto &ge : c->graphs)
         if (ge.exec) cudaGraphExecDestroy(ge.exec);
-    for (int k = 0; k < 128; ++k)
+    for (int k = 0; k < 2; ++k)
         if (c->prof_ev[k]) cudaEventDestroy(c->prof_ev[k]);
-    cudaFree(c->counts);
+    cudaFree(c->counts_buf[0]);
+    cudaFree(c->counts_buf[1]);
     cudaFree(c->dens);
     cudaFree(c->disp);
     cudaFree(c->agg);
@@ -358,6 +430,10 @@ dc_status declutter_destroy(dc_ctx *c)
     cudaFree(c->status);
     cudaFree(c->qacc);
     cudaFree(c->hpos);
+    cudaFree(c->spos);
+    cudaFree(c->perm);
+    cudaFree(c->cursor);
+    cudaFree(c->partials);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -373,7 +449,7 @@ dc_status declutter_get_info(const dc_ctx *c, dc_info *out)
     out->band_rows = c->g.T;
     out->n_bands = c->g.nb;
     out->band_threads = c->g.NT;
-    out->kernels_per_iter = c->mode == MODE_FLOAT ? 6 : 5;
+    out->kernels_per_iter = c->mode == MODE_FLOAT ? 5 : 4;  // after the first, which adds a splat
     out->device = c->device;
     out->scratch_bytes = c->scratch_bytes;
     return DC_OK;
@@ -386,9 +462,10 @@ dc_status splat_density(dc_ctx *c, const float *pos, int64_t n, uint32_t *counts
     if (density_out && c->mode != MODE_FLOAT) return fail(DC_ERR_INVALID_ARG, "no density in exact mode");
     DeviceGuard guard(c->device);
     Recorder rec;
-    DC_CUDA(enqueue_density(c, c->stream, pos, n, rec));
+    DC_CUDA(enqueue_density(c, c->stream, pos, n, c->counts_buf[0], nullptr, rec));
+    c->cur_counts = 0;
     const size_t NN = (size_t)c->g.N * c->g.N;
-    if (counts_out) DC_CUDA(cudaMemcpyAsync(counts_out, c->counts, NN * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (counts_out) DC_CUDA(cudaMemcpyAsync(counts_out, c->counts_buf[0], NN * 4, cudaMemcpyDeviceToDevice, c->stream));
     if (density_out) DC_CUDA(cudaMemcpyAsync(density_out, c->dens, NN * 4, cudaMemcpyDeviceToDevice, c->stream));
     c->n_last = n;
     c->have_disp = false;
@@ -402,7 +479,7 @@ dc_status integral_images(dc_ctx *c, void *alpha_out, void *alpha_t_out)
     if ((alpha_out && !aligned(alpha_out, 16)) || (alpha_t_out && !aligned(alpha_t_out, 16)))
         return fail(DC_ERR_INVALID_ARG, "outputs must be 16-byte aligned");
     DeviceGuard guard(c->device);
-    const void *src = c->mode == MODE_FLOAT ? (const void *)c->dens : (const void *)c->counts;
+    const void *src = c->mode == MODE_FLOAT ? (const void *)c->dens : (const void *)c->counts_buf[c->cur_counts];
     BandArgs a = band_args(c, src, c->mode, c->n_last);
     a.alpha_out = alpha_out;
     a.alpha_t_out = alpha_t_out;
@@ -432,7 +509,7 @@ dc_status displacement_field(dc_ctx *c, float *disp_out)
     if (c->n_last < 0) return fail(DC_ERR_STATE, "displacement_field before splat_density");
     if (disp_out && !aligned(disp_out, 16)) return fail(DC_ERR_INVALID_ARG, "output must be 16-byte aligned");
     DeviceGuard guard(c->device);
-    const void *src = c->mode == MODE_FLOAT ? (const void *)c->dens : (const void *)c->counts;
+    const void *src = c->mode == MODE_FLOAT ? (const void *)c->dens : (const void *)c->counts_buf[c->cur_counts];
     BandArgs a = band_args(c, src, c->mode, c->n_last);
     a.disp = c->disp;
     Recorder rec;
@@ -451,7 +528,7 @@ dc_status advect_samples(dc_ctx *c, float *pos, int64_t n)
     if (!c->have_disp) return fail(DC_ERR_STATE, "advect_samples before displacement_field");
     DeviceGuard guard(c->device);
     DC_CUDA(launch_advect(c->stream, reinterpret_cast<float2 *>(pos), n, c->disp, c->g.log2N, c->p.pixel_center,
-                          c->p.clamp_positions));
+                          c->p.clamp_positions, nullptr));
     return DC_OK;
 }
 
@@ -479,6 +556,7 @@ dc_status regularize(dc_ctx *c, float *pos, int64_t n, int32_t iters, double *un
     const int metrics = uniformity_out ? 1 : 0;
     if (metrics)
         if (dc_status st = ensure_qslots(c, iters)) return st;
+    if (dc_status st = ensure_sort_buffers(c, n)) return st;
     cudaGraphExec_t exec = nullptr;
     for (auto &ge : c->graphs)
         if (ge.pos == pos && ge.n == n && ge.iters == iters && ge.metrics == metrics) exec = ge.exec;
@@ -487,18 +565,7 @@ dc_status regularize(dc_ctx *c, float *pos, int64_t n, int32_t iters, double *un
             cudaGraphExecDestroy(c->graphs.front().exec);
             c->graphs.erase(c->graphs.begin());
         }
-        cudaGraph_t graph = nullptr;
-        DC_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-        Recorder rec;
-        cudaError_t e = enqueue_iterations(c, c->cap_stream, pos, n, iters, metrics, rec);
-        cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
-        if (e != cudaSuccess || e2 != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            return fail(DC_ERR_CUDA, "graph capture: %s / %s", cudaGetErrorString(e), cudaGetErrorString(e2));
-        }
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return fail(DC_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        if (dc_status st = capture_iterations(c, pos, n, iters, metrics, -1, &exec, nullptr)) return st;
         GraphEntry ge;
         ge.pos = pos;
         ge.n = n;
@@ -510,6 +577,7 @@ dc_status regularize(dc_ctx *c, float *pos, int64_t n, int32_t iters, double *un
     DC_CUDA(cudaGraphLaunch(exec, c->stream));
     c->n_last = n;
     c->have_disp = true;
+    c->cur_counts = metrics ? (iters & 1) : ((iters - 1) & 1);  // grid of the last splat performed
     if (metrics) {
         std::vector<unsigned long long> acc(3 * (size_t)iters);
         DC_CUDA(cudaMemcpyAsync(acc.data(), c->qacc, acc.size() * sizeof(unsigned long long),
@@ -556,39 +624,61 @@ dc_status quality_metrics(dc_ctx *c, double *out)
     DeviceGuard guard(c->device);
     unsigned long long acc[3];
     DC_CUDA(cudaMemsetAsync(c->qacc, 0, sizeof(acc), c->stream));
-    DC_CUDA(launch_quality(c->stream, c->counts, c->g.log2N, c->qacc));
+    DC_CUDA(launch_quality(c->stream, c->counts_buf[c->cur_counts], c->g.log2N, c->qacc));
     DC_CUDA(cudaMemcpyAsync(acc, c->qacc, sizeof(acc), cudaMemcpyDeviceToHost, c->stream));
     if (dc_status st = declutter_sync(c)) return st;
     metrics_from_acc(c, acc, out);
     return DC_OK;
 }
 
-dc_status declutter_profile_regularize(dc_ctx *c, float *pos, int64_t n, int32_t iters, float *kernel_ms_out,
+dc_status declutter_profile_regularize(dc_ctx *c, float *pos, const float *reset_src, int64_t n, int32_t iters,
+                                       int32_t reps, float *step_ms_out, float *kernel_ms_out,
                                        int32_t *launches_out)
 {
     if (dc_status st = check_ctx(c)) return st;
     if (dc_status st = check_samples(c, pos, n)) return st;
-    if (iters < 0) return fail(DC_ERR_INVALID_ARG, "iters");
+    if (iters < 1 || reps < 1) return fail(DC_ERR_INVALID_ARG, "iters = %d, reps = %d", iters, reps);
+    if (reset_src && !aligned(reset_src, 8)) return fail(DC_ERR_INVALID_ARG, "reset_src alignment");
     DeviceGuard guard(c->device);
-    float ms[DC_KERNEL_KINDS] = {};
-    int32_t cnt[DC_KERNEL_KINDS] = {};
-    for (int it = 0; it < iters; ++it) {
+    if (dc_status st = ensure_sort_buffers(c, n)) return st;
+    if (!c->prof_ev[0])
+        for (int k = 0; k < 2; ++k) DC_CUDA(cudaEventCreate(&c->prof_ev[k]));
+    const size_t bytes = sizeof(float) * 2 * (size_t)n;
+    float base_ms = 0.f;
+    float kernel_ms[DC_KERNEL_KINDS] = {};
+    int32_t launches[DC_KERNEL_KINDS] = {};
+    // dup = -1 first: the plain step; then each kind launched twice
+    for (int dup = -1; dup < DC_KERNEL_KINDS; ++dup) {
+        if (dup >= 0 && launches[dup] == 0) continue;
+        cudaGraphExec_t exec = nullptr;
         Recorder rec;
-        rec.ctx = c;
-        DC_CUDA(enqueue_iterations(c, c->stream, pos, n, 1, 0, rec));
-        if (rec.overflow) return fail(DC_ERR_INVALID_ARG, "too many launches to record");
-        DC_CUDA(cudaStreamSynchronize(c->stream));
-        for (int k = 0; k < rec.used; ++k) {
+        if (dc_status st = capture_iterations(c, pos, n, iters, 0, dup, &exec, &rec)) return st;
+        if (dup < 0) std::memcpy(launches, rec.launches, sizeof(launches));
+        float total = 0.f;
+        cudaError_t e = cudaSuccess;
+        for (int r = -2; r < reps && e == cudaSuccess; ++r) {  // two untimed warm-up runs
+            if (reset_src && n > 0)
+                e = cudaMemcpyAsync(pos, reset_src, bytes, cudaMemcpyDeviceToDevice, c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(c->prof_ev[0], c->stream);
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec, c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(c->prof_ev[1], c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(c->prof_ev[1]);
             float t = 0.f;
-            DC_CUDA(cudaEventElapsedTime(&t, c->prof_ev[2 * k], c->prof_ev[2 * k + 1]));
-            ms[rec.kinds[k]] += t;
-            cnt[rec.kinds[k]] += 1;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, c->prof_ev[0], c->prof_ev[1]);
+            if (r >= 0) total += t;
         }
+        cudaGraphExecDestroy(exec);
+        if (e != cudaSuccess) return fail(DC_ERR_CUDA, "profiling run: %s", cudaGetErrorString(e));
+        const float ms = total / reps;
+        if (dup < 0) base_ms = ms;
+        else kernel_ms[dup] = ms > base_ms ? ms - base_ms : 0.f;
     }
     c->n_last = n;
     c->have_disp = true;
-    if (kernel_ms_out) std::memcpy(kernel_ms_out, ms, sizeof(ms));
-    if (launches_out) std::memcpy(launches_out, cnt, sizeof(cnt));
+    c->cur_counts = (iters - 1) & 1;
+    if (step_ms_out) *step_ms_out = base_ms;
+    if (kernel_ms_out) std::memcpy(kernel_ms_out, kernel_ms, sizeof(kernel_ms));
+    if (launches_out) std::memcpy(launches_out, launches, sizeof(launches));
     return declutter_sync(c);
 }
 

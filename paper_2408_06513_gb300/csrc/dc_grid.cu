@@ -62,7 +62,8 @@ __device__ __forceinline__ int reflect_index(int k, int N)
 }
 
 __global__ void __launch_bounds__(256) smooth_kernel(const uint32_t *__restrict__ counts,
-                                                     float *__restrict__ dens, int log2N, GaussW w)
+                                                     float *__restrict__ dens, int log2N, GaussW w,
+                                                     uint32_t *__restrict__ zero_out)
 {
     extern __shared__ float s_sm[];
     const int N = 1 << log2N;
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(256) smooth_kernel(const uint32_t *__restrict_
         float s = 0.0f;
         for (int k = 0; k <= 2 * r; ++k) s += w.g[k] * s_mid[y * W + x + k];
         dens[((size_t)(oy + y) << log2N) + ox + x] = s;
+        if (zero_out) zero_out[((size_t)(oy + y) << log2N) + ox + x] = 0u;
     }
 }
 
@@ -282,11 +284,23 @@ __global__ void __launch_bounds__(CPT == 1 ? 64 : 512) band_kernel(BandArgs a, i
         }
     }
 
+    Acc vnext[CPT];
+    load_row<MODE, CPT>(a.src, log2N, j0, c0, a.mu, vnext);
     for (int r = 0; r < T; ++r) {
         const int j = j0 + r;
         const int par = r & 1;
         Acc v[CPT];
-        load_row<MODE, CPT>(a.src, log2N, j, c0, a.mu, v);
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) v[k] = vnext[k];
+        if (r + 1 < T) load_row<MODE, CPT>(a.src, log2N, j + 1, c0, a.mu, vnext);  // prefetch
+        if constexpr (!FINAL) {
+            if (a.zero_out) {
+                uint32_t zz[CPT];
+#pragma unroll
+                for (int k = 0; k < CPT; ++k) zz[k] = 0u;
+                store_row<uint32_t, CPT>(a.zero_out + ((size_t)j << log2N), zz, c0, N);
+            }
+        }
 
         // neighbour state of the previous row, exchanged before the scan's barrier
         Acc u_next = __shfl_down_sync(kFull, Uo[0], 1);
@@ -579,13 +593,14 @@ cudaError_t prepare_kernels()
     return cudaFuncSetAttribute(smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smooth_smem_bytes(64));
 }
 
-cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, int log2N, const GaussW &w)
+cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, int log2N, const GaussW &w,
+                          uint32_t *zero_out)
 {
     const int N = 1 << log2N;
     const int TW = N < 32 ? N : 32;
     const int bytes = smooth_smem_bytes(w.r);
     dim3 grid(N / TW, N / TW);
-    smooth_kernel<<<grid, 256, bytes, s>>>(counts, dens, log2N, w);
+    smooth_kernel<<<grid, 256, bytes, s>>>(counts, dens, log2N, w, zero_out);
     return cudaGetLastError();
 }
 

@@ -19,7 +19,7 @@ enum KernelKind {
     K_BAND_FINAL = 4,
     K_ADVECT = 5,
     K_QUALITY = 6,
-    K_MEMSET = 7,
+    K_REORDER = 7,  // counting sort of the samples by pixel, and the way back
 };
 
 // Accumulation mode of the integral-image kernels.
@@ -59,6 +59,7 @@ struct BandArgs {
     float2 *disp;             // domain units
     void *alpha_out;          // uint64 (COUNT, GRID64) or float (FLOAT)
     void *alpha_t_out;
+    uint32_t *zero_out;       // aggregate kernel: zero this N*N grid (band rows), or null
     // displacement constants
     int pixel_center;
     float d0;                 // regularising constant (>= 0)
@@ -75,10 +76,22 @@ struct GraphEntry {
 
 // Launchers (all enqueue on `s`; return cudaGetLastError()).
 cudaError_t launch_splat(cudaStream_t s, const float2 *pos, int64_t n, uint32_t *counts, int log2N);
+// counts_next: if not null, the moved samples are also splatted into it (must be zero)
 cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *disp, int log2N,
-                          int pixel_center, int clamp);
+                          int pixel_center, int clamp, uint32_t *counts_next);
 cudaError_t launch_quality(cudaStream_t s, const uint32_t *counts, int log2N, unsigned long long *acc);
-cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, int log2N, const GaussW &w);
+// reordering of the samples by pixel: exclusive scan of the counts into
+// cursor (partials: at most 1024 entries), scatter into spos / perm, and back
+int64_t reorder_scan_chunk(int log2N);
+cudaError_t launch_reorder_scan(cudaStream_t s, const uint32_t *counts, int log2N, uint32_t *partials,
+                                uint32_t *cursor);
+cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n, int log2N, uint32_t *cursor,
+                                   float2 *spos, uint32_t *perm, unsigned *status);
+cudaError_t launch_reorder_back(cudaStream_t s, const float2 *spos, const uint32_t *perm, int64_t n, float2 *pos,
+                                unsigned *status);
+// zero_out: if not null, the kernel also zeroes this N*N uint32 grid
+cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, int log2N, const GaussW &w,
+                          uint32_t *zero_out);
 cudaError_t launch_band_agg(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a);
 cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const void *agg,
                          void *carry);
@@ -101,7 +114,8 @@ struct dc_ctx {
     dc::GaussW w{};
     int mode = dc::MODE_COUNT;          // MODE_COUNT (r == 0) or MODE_FLOAT
 
-    uint32_t *counts = nullptr;
+    uint32_t *counts_buf[2] = {nullptr, nullptr}; // count grids (regularize alternates them)
+    int cur_counts = 0;                 // which one holds the density the other calls use
     float *dens = nullptr;
     float2 *disp = nullptr;
     void *agg = nullptr;
@@ -110,6 +124,12 @@ struct dc_ctx {
     unsigned long long *qacc = nullptr; // [3 * (qslots)]
     int qslots = 0;
     float *hpos = nullptr;              // device staging for regularize_host
+    // reordering buffers (grown on demand, outside graph capture)
+    float2 *spos = nullptr;             // samples in pixel order
+    uint32_t *perm = nullptr;           // original index of each reordered sample
+    int64_t sort_cap = 0;
+    uint32_t *cursor = nullptr;         // N*N exclusive prefix of the counts
+    uint32_t *partials = nullptr;       // <= 1024 chunk sums
     int64_t hpos_cap = 0;
     int64_t scratch_bytes = 0;
 
@@ -117,5 +137,5 @@ struct dc_ctx {
     bool have_disp = false;
 
     std::vector<dc::GraphEntry> graphs;
-    cudaEvent_t prof_ev[2 * 64] = {};
+    cudaEvent_t prof_ev[2] = {};
 };

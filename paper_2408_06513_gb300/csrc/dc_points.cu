@@ -44,35 +44,241 @@ __global__ void __launch_bounds__(kThreads) splat_kernel(const float2 *__restric
 // i0 = floor(p), f = p - i0, corners clamped to the grid.  px is first
 // limited to [-1, N], which leaves every clamped corner index and every
 // interpolated value unchanged but keeps the integer conversion in range.
-__global__ void __launch_bounds__(kThreads) advect_kernel(float2 *__restrict__ pos, int64_t n,
-                                                          const float2 *__restrict__ D, int log2N,
-                                                          float off, int clamp)
+struct Moved {
+    float2 z;
+    int pix;
+};
+
+__device__ __forceinline__ Moved advect_one(float2 z, const float2 *__restrict__ D, int log2N, float fN, float off,
+                                            int clamp)
 {
     const int N = 1 << log2N;
-    const float fN = (float)N;
+    const float px = fminf(fmaxf(z.x * fN - off, -1.0f), fN);
+    const float py = fminf(fmaxf(z.y * fN - off, -1.0f), fN);
+    const float fx = floorf(px), fy = floorf(py);
+    const float f = px - fx, h = py - fy;
+    const int ix = (int)fx, iy = (int)fy;
+    const int i0 = min(max(ix, 0), N - 1), i1 = min(max(ix + 1, 0), N - 1);
+    const int j0 = min(max(iy, 0), N - 1), j1 = min(max(iy + 1, 0), N - 1);
+    const float2 d00 = __ldg(&D[(j0 << log2N) + i0]);
+    const float2 d01 = __ldg(&D[(j0 << log2N) + i1]);
+    const float2 d10 = __ldg(&D[(j1 << log2N) + i0]);
+    const float2 d11 = __ldg(&D[(j1 << log2N) + i1]);
+    const float dx = (1.0f - h) * ((1.0f - f) * d00.x + f * d01.x) + h * ((1.0f - f) * d10.x + f * d11.x);
+    const float dy = (1.0f - h) * ((1.0f - f) * d00.y + f * d01.y) + h * ((1.0f - f) * d10.y + f * d11.y);
+    z.x += dx;
+    z.y += dy;
+    if (clamp) {
+        z.x = clamp01(z.x);
+        z.y = clamp01(z.y);
+    }
+    // pixel of the moved sample for the next iteration's splat (Sec. 4.1 rule)
+    const int si = min((int)(clamp01(z.x) * fN), N - 1);
+    const int sj = min((int)(clamp01(z.y) * fN), N - 1);
+    return {z, (sj << log2N) + si};
+}
+
+// Splat one sample per lane with warp aggregation: lanes holding the same
+// pixel are merged and their leader adds the group's size.  All 32 lanes
+// must call this together; lanes with valid = false add nothing.
+__device__ __forceinline__ void splat_warp(uint32_t *__restrict__ counts, int pix, bool valid)
+{
+    const int lane = threadIdx.x & 31;
+    const int key = valid ? pix : -1 - lane;
+    const unsigned m = __match_any_sync(0xffffffffu, key);
+    if (valid && lane == __ffs(m) - 1) atomicAdd(&counts[pix], (uint32_t)__popc(m));
+}
+
+// Samples are processed in aligned pairs (one float4 = two samples), two
+// pairs per thread and loop trip, so that all eight corner gathers of a trip
+// are independent.  The loop runs warp-uniformly so that, with counts_next
+// set, the moved samples can be splatted into the next iteration's count
+// grid (which must be zero) with warp aggregation: after the reordering by
+// pixel, neighbouring lanes mostly hold samples of the same pixel.  A sample
+// before the first 16-byte boundary and one left after the last pair are
+// handled by thread 0 of block 0.
+__global__ void __launch_bounds__(kThreads) advect_kernel(float2 *__restrict__ pos, int64_t n,
+                                                          const float2 *__restrict__ D, int log2N, float off,
+                                                          int clamp, uint32_t *__restrict__ counts_next)
+{
+    const float fN = (float)(1 << log2N);
+    const int lane = threadIdx.x & 31;
+    const int64_t head = (reinterpret_cast<uintptr_t>(pos) & 15) ? 1 : 0;
+    const int64_t npairs = (n - head) / 2;
+    float4 *pp = reinterpret_cast<float4 *>(pos + head);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-        float2 z = pos[k];
-        float px = fminf(fmaxf(z.x * fN - off, -1.0f), fN);
-        float py = fminf(fmaxf(z.y * fN - off, -1.0f), fN);
-        const float fx = floorf(px), fy = floorf(py);
-        const float f = px - fx, h = py - fy;
-        const int ix = (int)fx, iy = (int)fy;
-        const int i0 = min(max(ix, 0), N - 1), i1 = min(max(ix + 1, 0), N - 1);
-        const int j0 = min(max(iy, 0), N - 1), j1 = min(max(iy + 1, 0), N - 1);
-        const float2 d00 = __ldg(&D[(j0 << log2N) + i0]);
-        const float2 d01 = __ldg(&D[(j0 << log2N) + i1]);
-        const float2 d10 = __ldg(&D[(j1 << log2N) + i0]);
-        const float2 d11 = __ldg(&D[(j1 << log2N) + i1]);
-        const float dx = (1.0f - h) * ((1.0f - f) * d00.x + f * d01.x) + h * ((1.0f - f) * d10.x + f * d11.x);
-        const float dy = (1.0f - h) * ((1.0f - f) * d00.y + f * d01.y) + h * ((1.0f - f) * d10.y + f * d11.y);
-        z.x += dx;
-        z.y += dy;
-        if (clamp) {
-            z.x = clamp01(z.x);
-            z.y = clamp01(z.y);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t qb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); qb < npairs; qb += 2 * stride) {
+        const int64_t q1 = qb + lane, q2 = q1 + stride;
+        const bool v1 = q1 < npairs, v2 = q2 < npairs;
+        const float4 a = v1 ? pp[q1] : zero4;
+        const float4 b = v2 ? pp[q2] : zero4;
+        const Moved m0 = advect_one(make_float2(a.x, a.y), D, log2N, fN, off, clamp);
+        const Moved m1 = advect_one(make_float2(a.z, a.w), D, log2N, fN, off, clamp);
+        const Moved m2 = advect_one(make_float2(b.x, b.y), D, log2N, fN, off, clamp);
+        const Moved m3 = advect_one(make_float2(b.z, b.w), D, log2N, fN, off, clamp);
+        if (v1) pp[q1] = make_float4(m0.z.x, m0.z.y, m1.z.x, m1.z.y);
+        if (v2) pp[q2] = make_float4(m2.z.x, m2.z.y, m3.z.x, m3.z.y);
+        if (counts_next) {
+            splat_warp(counts_next, m0.pix, v1);
+            splat_warp(counts_next, m1.pix, v1);
+            splat_warp(counts_next, m2.pix, v2);
+            splat_warp(counts_next, m3.pix, v2);
         }
-        pos[k] = z;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int64_t singles[2] = {head ? 0 : -1, (n - head) & 1 ? n - 1 : -1};
+        for (int s = 0; s < 2; ++s) {
+            if (singles[s] < 0) continue;
+            const Moved m = advect_one(pos[singles[s]], D, log2N, fN, off, clamp);
+            pos[singles[s]] = m.z;
+            if (counts_next) atomicAdd(&counts_next[m.pix], 1u);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// Reordering of the samples by pixel (a counting sort keyed by the splat
+// pixel), so that the iterations touch the grids with spatial locality.
+// The method itself does not depend on the order of the samples: counts are
+// integer sums and every sample moves by the same field.
+// ------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+
+__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *s_red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) s_red[w] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_red[k];
+    __syncthreads();
+    if (threadIdx.x == 0) s_red[0] = t;
+    __syncthreads();
+    return s_red[0];
+}
+
+// partials[b] = sum of counts[b * chunk, (b + 1) * chunk)
+__global__ void __launch_bounds__(kScanThreads) scan_partials_kernel(const uint32_t *__restrict__ counts, int64_t M,
+                                                                     int64_t chunk, uint32_t *__restrict__ partials)
+{
+    __shared__ uint32_t s_red[kScanThreads / 32];
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(M, beg + chunk);
+    uint32_t v = 0;
+    for (int64_t k = beg + 4 * threadIdx.x; k < end; k += 4 * kScanThreads) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(counts + k);
+        v += q.x + q.y + q.z + q.w;
+    }
+    v = block_sum_u32(v, s_red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+}
+
+// cursor[k] = sum of counts[0, k) (exclusive prefix in row-major order).
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t *__restrict__ counts, int64_t M,
+                                                                  int64_t chunk, const uint32_t *__restrict__ partials,
+                                                                  uint32_t *__restrict__ cursor)
+{
+    __shared__ uint32_t s_red[kScanThreads / 32];
+    __shared__ uint32_t s_w[kScanThreads / 32];
+    uint32_t pre = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kScanThreads) pre += partials[b];
+    uint32_t carry = block_sum_u32(pre, s_red);
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(M, beg + chunk);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t t0 = beg; t0 < end; t0 += 4 * kScanThreads) {
+        const int64_t k = t0 + 4 * threadIdx.x;
+        uint4 q = make_uint4(0, 0, 0, 0);
+        if (k < end) q = *reinterpret_cast<const uint4 *>(counts + k);
+        const uint32_t tsum = q.x + q.y + q.z + q.w;
+        uint32_t x = tsum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        __syncthreads();
+        if (lane == 31) s_w[w] = x;
+        __syncthreads();
+        uint32_t wpre = 0, tile = 0;
+        for (int k2 = 0; k2 < kScanThreads / 32; ++k2) {
+            if (k2 < w) wpre += s_w[k2];
+            tile += s_w[k2];
+        }
+        uint32_t e = carry + wpre + (x - tsum);
+        if (k < end) {
+            uint4 o;
+            o.x = e; e += q.x;
+            o.y = e; e += q.y;
+            o.z = e; e += q.z;
+            o.w = e;
+            *reinterpret_cast<uint4 *>(cursor + k) = o;
+        }
+        carry += tile;
+    }
+}
+
+__device__ __forceinline__ int sample_pixel(float2 z, int log2N, float fN)
+{
+    const int N = 1 << log2N;
+    const int i = min((int)(clamp01(z.x) * fN), N - 1);
+    const int j = min((int)(clamp01(z.y) * fN), N - 1);
+    return (j << log2N) + i;
+}
+
+// spos[slot] = pos[k], perm[slot] = k, with slot = cursor[pixel]++ (warp
+// aggregated).  Slots of pixel p are [prefix(p), prefix(p) + counts(p)), so
+// every slot < n when cursor was built from the counts of these samples; a
+// slot out of range sets DC_ERR_RANGE in the status word and is skipped.
+__global__ void __launch_bounds__(kThreads) reorder_scatter_kernel(const float2 *__restrict__ pos, int64_t n,
+                                                                   int log2N, uint32_t *__restrict__ cursor,
+                                                                   float2 *__restrict__ spos,
+                                                                   uint32_t *__restrict__ perm,
+                                                                   unsigned *__restrict__ status)
+{
+    const float fN = (float)(1 << log2N);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t k = base + lane;
+        const bool valid = k < n;
+        float2 z = make_float2(0.f, 0.f);
+        int key = -1 - lane;
+        if (valid) {
+            z = pos[k];
+            key = sample_pixel(z, log2N, fN);
+        }
+        const unsigned m = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(m) - 1;
+        uint32_t slot0 = 0;
+        if (valid && lane == leader) slot0 = atomicAdd(&cursor[key], (uint32_t)__popc(m));
+        slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+        if (valid) {
+            const uint32_t slot = slot0 + __popc(m & ((1u << lane) - 1u));
+            if ((int64_t)slot < n) {
+                spos[slot] = z;
+                perm[slot] = (uint32_t)k;
+            } else {
+                atomicOr(status, (unsigned)DC_ERR_RANGE);
+            }
+        }
+    }
+}
+
+// pos[perm[s]] = spos[s]
+__global__ void __launch_bounds__(kThreads) reorder_gather_back_kernel(const float2 *__restrict__ spos,
+                                                                       const uint32_t *__restrict__ perm, int64_t n,
+                                                                       float2 *__restrict__ pos,
+                                                                       unsigned *__restrict__ status)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += stride) {
+        const uint32_t k = perm[s];
+        if ((int64_t)k < n) pos[k] = spos[s];
+        else atomicOr(status, (unsigned)DC_ERR_RANGE);
     }
 }
 
@@ -141,11 +347,48 @@ cudaError_t launch_splat(cudaStream_t s, const float2 *pos, int64_t n, uint32_t 
 }
 
 cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *disp, int log2N,
-                          int pixel_center, int clamp)
+                          int pixel_center, int clamp, uint32_t *counts_next)
 {
     if (n <= 0) return cudaSuccess;
-    advect_kernel<<<grid_for(n, kThreads, 152 * 16), kThreads, 0, s>>>(pos, n, disp, log2N,
-                                                                         pixel_center ? 0.5f : 0.0f, clamp);
+    // two pairs (four samples) per thread and trip
+    advect_kernel<<<grid_for((n + 3) / 4, kThreads, 152 * 8), kThreads, 0, s>>>(
+        pos, n, disp, log2N, pixel_center ? 0.5f : 0.0f, clamp, counts_next);
+    return cudaGetLastError();
+}
+
+int64_t reorder_scan_chunk(int log2N)
+{
+    const int64_t M = (int64_t)1 << (2 * log2N);
+    int64_t chunk = 4096;
+    while (M / chunk > 1024) chunk *= 2;
+    return chunk;
+}
+
+cudaError_t launch_reorder_scan(cudaStream_t s, const uint32_t *counts, int log2N, uint32_t *partials,
+                                uint32_t *cursor)
+{
+    const int64_t M = (int64_t)1 << (2 * log2N);
+    const int64_t chunk = reorder_scan_chunk(log2N);
+    const int blocks = (int)((M + chunk - 1) / chunk);
+    scan_partials_kernel<<<blocks, kScanThreads, 0, s>>>(counts, M, chunk, partials);
+    scan_apply_kernel<<<blocks, kScanThreads, 0, s>>>(counts, M, chunk, partials, cursor);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n, int log2N, uint32_t *cursor,
+                                   float2 *spos, uint32_t *perm, unsigned *status)
+{
+    if (n <= 0) return cudaSuccess;
+    reorder_scatter_kernel<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, s>>>(pos, n, log2N, cursor, spos, perm,
+                                                                                status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder_back(cudaStream_t s, const float2 *spos, const uint32_t *perm, int64_t n, float2 *pos,
+                                unsigned *status)
+{
+    if (n <= 0) return cudaSuccess;
+    reorder_gather_back_kernel<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, s>>>(spos, perm, n, pos, status);
     return cudaGetLastError();
 }
 

@@ -56,7 +56,8 @@ class dc_params(ctypes.Structure):
         ("clamp_positions", ctypes.c_int32),
         ("carry_mode", ctypes.c_int32),
         ("band_rows", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("keep_order", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -91,7 +92,8 @@ _SIGS = [
     ("regularize_host", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
     ("quality_metrics", ctypes.c_int, [_P, _P]),
     ("declutter_sync", ctypes.c_int, [_P]),
-    ("declutter_profile_regularize", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]),
+    ("declutter_profile_regularize", ctypes.c_int,
+     [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     ("integral_images_u32_noalloc", ctypes.c_int, [_P, ctypes.c_uint32, _P, _P, _P]),
     ("declutter_kernel_name", ctypes.c_char_p, [ctypes.c_int32]),
     ("declutter_status_string", ctypes.c_char_p, [ctypes.c_int]),
@@ -178,7 +180,7 @@ class Context:
 
 def declutter_create(log2_res: int, kernel_r: int = -1, sigma: float = 0.0, d0: float = -1.0,
                      pixel_center: bool = False, clamp_positions: bool = True,
-                     carry_mode: int = DC_CARRY_COMPENSATED, band_rows: int = 0,
+                     carry_mode: int = DC_CARRY_COMPENSATED, band_rows: int = 0, keep_order: bool = False,
                      device: int | None = None, stream=None) -> Context:
     """Create a context.  ``stream``: a ``torch.cuda.Stream`` or None for the
     current torch stream (the library makes its own stream, ordered with the
@@ -199,6 +201,7 @@ def declutter_create(log2_res: int, kernel_r: int = -1, sigma: float = 0.0, d0: 
     p.clamp_positions = int(bool(clamp_positions))
     p.carry_mode = int(carry_mode)
     p.band_rows = int(band_rows)
+    p.keep_order = int(bool(keep_order))
     h = ctypes.c_void_p()
     _check(lib.declutter_create(ctypes.byref(p), int(device), ctypes.c_void_p(sp) if sp else None,
                                 ctypes.byref(h)), "declutter_create")
@@ -308,13 +311,25 @@ def declutter_sync(ctx: Context) -> None:
     _check(load_library().declutter_sync(ctx.handle), "declutter_sync")
 
 
-def declutter_profile_regularize(ctx: Context, pos, iters: int) -> dict:
+def declutter_profile_regularize(ctx: Context, pos, iters: int, reps: int = 10, reset_src=None) -> dict:
+    """In-graph device time of regularize(iters) and of each kernel kind in
+    it (see the C header).  Returns ``{"step_ms": t, "kernels": {name:
+    {"ms": per call, "launches": per call}}}``."""
     pp, n = _pos_args(pos)
+    src = None
+    if reset_src is not None:
+        src, n2 = _pos_args(reset_src)
+        if n2 != n:
+            raise ValueError("reset_src must have the shape of pos")
+    step = ctypes.c_float()
     ms = (ctypes.c_float * KERNEL_KINDS)()
     cnt = (ctypes.c_int32 * KERNEL_KINDS)()
-    _check(load_library().declutter_profile_regularize(ctx.handle, pp, n, int(iters), ms, cnt),
+    _check(load_library().declutter_profile_regularize(ctx.handle, pp, src, n, int(iters), int(reps),
+                                                       ctypes.byref(step), ms, cnt),
            "declutter_profile_regularize")
-    return {declutter_kernel_name(k): {"ms": float(ms[k]), "launches": int(cnt[k])} for k in range(KERNEL_KINDS)}
+    return {"step_ms": float(step.value),
+            "kernels": {declutter_kernel_name(k): {"ms": float(ms[k]), "launches": int(cnt[k])}
+                        for k in range(KERNEL_KINDS)}}
 
 
 def integral_images_u32_noalloc(grid, log2_res: int, alpha_out=None, alpha_t_out=None, stream=None) -> None:

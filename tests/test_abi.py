@@ -58,6 +58,7 @@ def _params(**kw):
     p.clamp_positions = kw.get("clamp_positions", 1)
     p.carry_mode = kw.get("carry_mode", 0)
     p.band_rows = kw.get("band_rows", 0)
+    p.keep_order = kw.get("keep_order", 0)
     return p
 
 
@@ -70,6 +71,7 @@ def _params(**kw):
     (dict(carry_mode=5), 1),
     (dict(band_rows=3), 1),
     (dict(band_rows=128), 1),
+    (dict(keep_order=2), 1),
 ])
 def test_create_rejects_bad_parameters(lib, kw, status):
     h = ctypes.c_void_p()
