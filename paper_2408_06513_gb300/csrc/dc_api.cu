@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -142,18 +143,20 @@ cudaError_t enqueue_iterations(dc_ctx *c, cudaStream_t s, float *pos, int64_t n,
             e = cudaMemsetAsync(cb[cur], 0, sizeof(uint32_t) * (size_t)c->g.N * c->g.N, s);
             if (e != cudaSuccess) return e;
             rec.count(K_SPLAT);
+            const float2 *p2 = reinterpret_cast<const float2 *>(pos);
+            e = reorder ? launch_splat_rank(s, p2, n, cb[cur], c->g.log2N, c->rank)
+                        : launch_splat(s, p2, n, cb[cur], c->g.log2N);
             // a profiling duplicate goes to the other grid, which is zeroed
             // before its next use, so that these counts stay those of pos
-            for (int t = 0; t < rec.times(K_SPLAT) && e == cudaSuccess; ++t)
-                e = launch_splat(s, reinterpret_cast<const float2 *>(pos), n, t == 0 ? cb[cur] : cb[nxt], c->g.log2N);
+            if (e == cudaSuccess && rec.times(K_SPLAT) > 1) e = launch_splat(s, p2, n, cb[nxt], c->g.log2N);
             if (e != cudaSuccess) return e;
             if (reorder) {
                 rec.count(K_REORDER);
                 for (int t = 0; t < rec.times(K_REORDER) && e == cudaSuccess; ++t) {
                     e = launch_reorder_scan(s, cb[cur], c->g.log2N, c->partials, c->cursor);
                     if (e == cudaSuccess)
-                        e = launch_reorder_scatter(s, reinterpret_cast<const float2 *>(pos), n, c->g.log2N, c->cursor,
-                                                   c->spos, c->perm, c->status);
+                        e = launch_reorder_scatter(s, p2, n, c->g.log2N, c->cursor, c->rank, c->spos, c->inv,
+                                                   c->status);
                 }
                 if (e != cudaSuccess) return e;
             }
@@ -183,7 +186,7 @@ cudaError_t enqueue_iterations(dc_ctx *c, cudaStream_t s, float *pos, int64_t n,
     }
     if (reorder && iters > 0) {
         for (int t = 0; t < rec.times(K_REORDER) && e == cudaSuccess; ++t)
-            e = launch_reorder_back(s, c->spos, c->perm, n, reinterpret_cast<float2 *>(pos), c->status);
+            e = launch_reorder_back(s, c->spos, c->inv, n, reinterpret_cast<float2 *>(pos), c->status);
     }
     return e;
 }
@@ -197,12 +200,15 @@ dc_status ensure_sort_buffers(dc_ctx *c, int64_t n)
     for (auto &ge : c->graphs) cudaGraphExecDestroy(ge.exec);
     c->graphs.clear();
     cudaFree(c->spos);
-    cudaFree(c->perm);
+    cudaFree(c->rank);
+    cudaFree(c->inv);
     c->spos = nullptr;
-    c->perm = nullptr;
+    c->rank = nullptr;
+    c->inv = nullptr;
     c->sort_cap = 0;
     if (cudaMalloc(&c->spos, sizeof(float2) * (size_t)n) != cudaSuccess ||
-        cudaMalloc(&c->perm, sizeof(uint32_t) * (size_t)n) != cudaSuccess) {
+        cudaMalloc(&c->rank, sizeof(uint32_t) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&c->inv, sizeof(uint32_t) * (size_t)n) != cudaSuccess) {
         cudaGetLastError();
         return fail(DC_ERR_OOM, "reordering buffers for %lld samples", (long long)n);
     }
@@ -289,6 +295,15 @@ const char *kKernelNames[DC_KERNEL_KINDS] = {"splat",  "smooth", "band_aggregate
 }  // namespace
 
 void dc::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+bool dc::pdl_enabled()
+{
+    static const bool on = [] {
+        const char *e = std::getenv("DECLUTTER_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 
 extern "C" {
 
@@ -431,7 +446,8 @@ dc_status declutter_destroy(dc_ctx *c)
     cudaFree(c->qacc);
     cudaFree(c->hpos);
     cudaFree(c->spos);
-    cudaFree(c->perm);
+    cudaFree(c->rank);
+    cudaFree(c->inv);
     cudaFree(c->cursor);
     cudaFree(c->partials);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

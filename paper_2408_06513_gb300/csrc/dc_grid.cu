@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(256) smooth_kernel(const uint32_t *__restrict_
     float *s_mid = s_sm + W * W; // TW x W
     const int ox = blockIdx.x * TW, oy = blockIdx.y * TW;
     const int tid = threadIdx.x;
+    pdl_wait();
     for (int idx = tid; idx < W * W; idx += blockDim.x) {
         const int yy = idx / W, xx = idx - yy * W;
         const int gy = reflect_index(oy + yy - r, N), gx = reflect_index(ox + xx - r, N);
@@ -254,6 +255,7 @@ __global__ void __launch_bounds__(CPT == 1 ? 64 : 512) band_kernel(BandArgs a, i
     __shared__ Acc s_vl[2][32];
     __shared__ Acc s_U0[64], s_VN[64], s_RT[64];
 
+    pdl_wait();
     Acc arun[CPT], Uo[CPT], Vo[CPT];
 #pragma unroll
     for (int k = 0; k < CPT; ++k) { arun[k] = Acc(0); Uo[k] = Acc(0); Vo[k] = Acc(0); }
@@ -548,6 +550,7 @@ __global__ void __launch_bounds__(1024) carry_kernel(const Acc *__restrict__ agg
     const int b_beg = g * bpg;
     const int b_end = min(nb, b_beg + bpg);
     __shared__ Sum s_sum[32][33];
+    pdl_wait();
 
     Sum s;
     s.zero();
@@ -600,21 +603,19 @@ cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, i
     const int TW = N < 32 ? N : 32;
     const int bytes = smooth_smem_bytes(w.r);
     dim3 grid(N / TW, N / TW);
-    smooth_kernel<<<grid, 256, bytes, s>>>(counts, dens, log2N, w, zero_out);
-    return cudaGetLastError();
+    return launch_kernel(smooth_kernel, grid, dim3(256), (size_t)bytes, s, counts, dens, log2N, w, zero_out);
 }
 
 template <int MODE, bool FINAL>
 static cudaError_t launch_band_mode(cudaStream_t s, const BandGeom &g, const BandArgs &a)
 {
     switch (g.CPT) {
-    case 1: band_kernel<MODE, 1, FINAL><<<g.nb, g.NT, 0, s>>>(a, g.log2N, g.T); break;
-    case 4: band_kernel<MODE, 4, FINAL><<<g.nb, g.NT, 0, s>>>(a, g.log2N, g.T); break;
-    case 8: band_kernel<MODE, 8, FINAL><<<g.nb, g.NT, 0, s>>>(a, g.log2N, g.T); break;
-    case 16: band_kernel<MODE, 16, FINAL><<<g.nb, g.NT, 0, s>>>(a, g.log2N, g.T); break;
+    case 1: return launch_kernel(band_kernel<MODE, 1, FINAL>, dim3(g.nb), dim3(g.NT), 0, s, a, g.log2N, g.T);
+    case 4: return launch_kernel(band_kernel<MODE, 4, FINAL>, dim3(g.nb), dim3(g.NT), 0, s, a, g.log2N, g.T);
+    case 8: return launch_kernel(band_kernel<MODE, 8, FINAL>, dim3(g.nb), dim3(g.NT), 0, s, a, g.log2N, g.T);
+    case 16: return launch_kernel(band_kernel<MODE, 16, FINAL>, dim3(g.nb), dim3(g.NT), 0, s, a, g.log2N, g.T);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_band_agg(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a)
@@ -639,30 +640,24 @@ cudaError_t launch_band_final(cudaStream_t s, const BandGeom &g, int mode, const
 
 cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const void *agg, void *carry)
 {
-    const int blocks = (g.lanes + 31) / 32;
+    const dim3 blocks((g.lanes + 31) / 32), threads(1024);
     switch (mode) {
     case MODE_COUNT:
-        carry_kernel<uint32_t, ScanSum<uint32_t>><<<blocks, 1024, 0, s>>>(
-            static_cast<const uint32_t *>(agg), static_cast<uint32_t *>(carry), g.log2N, g.T, g.nb, g.agg_stride);
-        break;
+        return launch_kernel(carry_kernel<uint32_t, ScanSum<uint32_t>>, blocks, threads, 0, s,
+                             static_cast<const uint32_t *>(agg), static_cast<uint32_t *>(carry), g.log2N, g.T, g.nb,
+                             g.agg_stride);
     case MODE_GRID64:
-        carry_kernel<unsigned long long, ScanSum<unsigned long long>><<<blocks, 1024, 0, s>>>(
-            static_cast<const unsigned long long *>(agg), static_cast<unsigned long long *>(carry), g.log2N, g.T,
-            g.nb, g.agg_stride);
-        break;
+        return launch_kernel(carry_kernel<unsigned long long, ScanSum<unsigned long long>>, blocks, threads, 0, s,
+                             static_cast<const unsigned long long *>(agg), static_cast<unsigned long long *>(carry),
+                             g.log2N, g.T, g.nb, g.agg_stride);
     case MODE_FLOAT:
         if (carry_mode == DC_CARRY_F64)
-            carry_kernel<float, ScanF64><<<blocks, 1024, 0, s>>>(static_cast<const float *>(agg),
-                                                                  static_cast<float *>(carry), g.log2N, g.T, g.nb,
-                                                                  g.agg_stride);
-        else
-            carry_kernel<float, ScanF2><<<blocks, 1024, 0, s>>>(static_cast<const float *>(agg),
-                                                                 static_cast<float *>(carry), g.log2N, g.T, g.nb,
-                                                                 g.agg_stride);
-        break;
+            return launch_kernel(carry_kernel<float, ScanF64>, blocks, threads, 0, s, static_cast<const float *>(agg),
+                                 static_cast<float *>(carry), g.log2N, g.T, g.nb, g.agg_stride);
+        return launch_kernel(carry_kernel<float, ScanF2>, blocks, threads, 0, s, static_cast<const float *>(agg),
+                             static_cast<float *>(carry), g.log2N, g.T, g.nb, g.agg_stride);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace dc

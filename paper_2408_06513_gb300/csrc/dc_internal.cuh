@@ -10,6 +10,33 @@
 
 namespace dc {
 
+// Programmatic dependent launch.  Every kernel is launched with programmatic
+// stream serialisation, so that its launch overlaps the tail of the kernel
+// before it; every kernel calls pdl_wait() before it touches any global
+// memory, which blocks until the preceding grid has completed and its writes
+// are visible.  pdl_trigger() lets the next kernel's CTAs be scheduled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+bool pdl_enabled();  // DECLUTTER_PDL=0 in the environment turns it off
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Kernel kinds, in the order reported by declutter_profile_regularize().
 enum KernelKind {
     K_SPLAT = 0,
@@ -80,16 +107,19 @@ cudaError_t launch_splat(cudaStream_t s, const float2 *pos, int64_t n, uint32_t 
 cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *disp, int log2N,
                           int pixel_center, int clamp, uint32_t *counts_next);
 cudaError_t launch_quality(cudaStream_t s, const uint32_t *counts, int log2N, unsigned long long *acc);
-// reordering of the samples by pixel: exclusive scan of the counts into
-// cursor (partials: at most 1024 entries), scatter into spos / perm, and back
+// reordering of the samples by pixel: the first splat also records each
+// sample's rank within its pixel; exclusive scan of the counts into cursor
+// (partials: at most 1024 entries); scatter into spos with inv[k] = slot of
+// sample k; gather back pos[k] = spos[inv[k]]
+cudaError_t launch_splat_rank(cudaStream_t s, const float2 *pos, int64_t n, uint32_t *counts, int log2N,
+                              uint32_t *rank);
 int64_t reorder_scan_chunk(int log2N);
 cudaError_t launch_reorder_scan(cudaStream_t s, const uint32_t *counts, int log2N, uint32_t *partials,
                                 uint32_t *cursor);
-cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n, int log2N, uint32_t *cursor,
-                                   float2 *spos, uint32_t *perm, unsigned *status);
-cudaError_t launch_reorder_back(cudaStream_t s, const float2 *spos, const uint32_t *perm, int64_t n, float2 *pos,
+cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n, int log2N, const uint32_t *cursor,
+                                   const uint32_t *rank, float2 *spos, uint32_t *inv, unsigned *status);
+cudaError_t launch_reorder_back(cudaStream_t s, const float2 *spos, const uint32_t *inv, int64_t n, float2 *pos,
                                 unsigned *status);
-// zero_out: if not null, the kernel also zeroes this N*N uint32 grid
 cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, int log2N, const GaussW &w,
                           uint32_t *zero_out);
 cudaError_t launch_band_agg(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a);
@@ -126,7 +156,8 @@ struct dc_ctx {
     float *hpos = nullptr;              // device staging for regularize_host
     // reordering buffers (grown on demand, outside graph capture)
     float2 *spos = nullptr;             // samples in pixel order
-    uint32_t *perm = nullptr;           // original index of each reordered sample
+    uint32_t *rank = nullptr;           // rank of each sample within its pixel
+    uint32_t *inv = nullptr;            // slot of each sample in spos
     int64_t sort_cap = 0;
     uint32_t *cursor = nullptr;         // N*N exclusive prefix of the counts
     uint32_t *partials = nullptr;       // <= 1024 chunk sums

@@ -22,6 +22,7 @@ __device__ __forceinline__ float clamp01(float v)
 __global__ void __launch_bounds__(kThreads) splat_kernel(const float2 *__restrict__ pos, int64_t n,
                                                          uint32_t *__restrict__ counts, int log2N)
 {
+    pdl_wait();
     const int N = 1 << log2N;
     const float fN = (float)N;
     const int lane = threadIdx.x & 31;
@@ -37,6 +38,36 @@ __global__ void __launch_bounds__(kThreads) splat_kernel(const float2 *__restric
         }
         const unsigned m = __match_any_sync(0xffffffffu, pix);
         if (k < n && lane == __ffs(m) - 1) atomicAdd(&counts[pix], (uint32_t)__popc(m));
+    }
+}
+
+// The same splat, also recording each sample's rank among the samples of its
+// pixel (the counter value its atomic increment returned), for the
+// reordering below.  Ranks of a pixel's samples are exactly 0 .. count - 1.
+__global__ void __launch_bounds__(kThreads) splat_rank_kernel(const float2 *__restrict__ pos, int64_t n,
+                                                              uint32_t *__restrict__ counts, int log2N,
+                                                              uint32_t *__restrict__ rank)
+{
+    pdl_wait();
+    const int N = 1 << log2N;
+    const float fN = (float)N;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t k = base + lane;
+        int pix = -1 - lane;
+        if (k < n) {
+            const float2 z = pos[k];
+            const int i = min((int)(clamp01(z.x) * fN), N - 1);
+            const int j = min((int)(clamp01(z.y) * fN), N - 1);
+            pix = (j << log2N) + i;
+        }
+        const unsigned m = __match_any_sync(0xffffffffu, pix);
+        const int leader = __ffs(m) - 1;
+        uint32_t r0 = 0;
+        if (k < n && lane == leader) r0 = atomicAdd(&counts[pix], (uint32_t)__popc(m));
+        r0 = __shfl_sync(0xffffffffu, r0, leader);
+        if (k < n) rank[k] = r0 + __popc(m & ((1u << lane) - 1u));
     }
 }
 
@@ -101,6 +132,7 @@ __global__ void __launch_bounds__(kThreads) advect_kernel(float2 *__restrict__ p
                                                           const float2 *__restrict__ D, int log2N, float off,
                                                           int clamp, uint32_t *__restrict__ counts_next)
 {
+    pdl_wait();
     const float fN = (float)(1 << log2N);
     const int lane = threadIdx.x & 31;
     const int64_t head = (reinterpret_cast<uintptr_t>(pos) & 15) ? 1 : 0;
@@ -166,6 +198,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_partials_kernel(const uint3
                                                                      int64_t chunk, uint32_t *__restrict__ partials)
 {
     __shared__ uint32_t s_red[kScanThreads / 32];
+    pdl_wait();
     const int64_t beg = (int64_t)blockIdx.x * chunk;
     const int64_t end = min(M, beg + chunk);
     uint32_t v = 0;
@@ -184,6 +217,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t
 {
     __shared__ uint32_t s_red[kScanThreads / 32];
     __shared__ uint32_t s_w[kScanThreads / 32];
+    pdl_wait();
     uint32_t pre = 0;
     for (int b = threadIdx.x; b < (int)blockIdx.x; b += kScanThreads) pre += partials[b];
     uint32_t carry = block_sum_u32(pre, s_red);
@@ -229,55 +263,45 @@ __device__ __forceinline__ int sample_pixel(float2 z, int log2N, float fN)
     return (j << log2N) + i;
 }
 
-// spos[slot] = pos[k], perm[slot] = k, with slot = cursor[pixel]++ (warp
-// aggregated).  Slots of pixel p are [prefix(p), prefix(p) + counts(p)), so
-// every slot < n when cursor was built from the counts of these samples; a
-// slot out of range sets DC_ERR_RANGE in the status word and is skipped.
+// spos[slot] = pos[k] and inv[k] = slot, with slot = cursor[pixel] + rank[k]
+// (cursor: exclusive prefix of the counts).  The slots of pixel p are
+// [prefix(p), prefix(p) + counts(p)), so every slot < n when cursor and rank
+// come from the splat of these same samples; a slot out of range sets
+// DC_ERR_RANGE in the status word and is skipped.
 __global__ void __launch_bounds__(kThreads) reorder_scatter_kernel(const float2 *__restrict__ pos, int64_t n,
-                                                                   int log2N, uint32_t *__restrict__ cursor,
+                                                                   int log2N, const uint32_t *__restrict__ cursor,
+                                                                   const uint32_t *__restrict__ rank,
                                                                    float2 *__restrict__ spos,
-                                                                   uint32_t *__restrict__ perm,
+                                                                   uint32_t *__restrict__ inv,
                                                                    unsigned *__restrict__ status)
 {
+    pdl_wait();
     const float fN = (float)(1 << log2N);
-    const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        const int64_t k = base + lane;
-        const bool valid = k < n;
-        float2 z = make_float2(0.f, 0.f);
-        int key = -1 - lane;
-        if (valid) {
-            z = pos[k];
-            key = sample_pixel(z, log2N, fN);
-        }
-        const unsigned m = __match_any_sync(0xffffffffu, key);
-        const int leader = __ffs(m) - 1;
-        uint32_t slot0 = 0;
-        if (valid && lane == leader) slot0 = atomicAdd(&cursor[key], (uint32_t)__popc(m));
-        slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-        if (valid) {
-            const uint32_t slot = slot0 + __popc(m & ((1u << lane) - 1u));
-            if ((int64_t)slot < n) {
-                spos[slot] = z;
-                perm[slot] = (uint32_t)k;
-            } else {
-                atomicOr(status, (unsigned)DC_ERR_RANGE);
-            }
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const float2 z = pos[k];
+        const uint32_t slot = __ldg(&cursor[sample_pixel(z, log2N, fN)]) + rank[k];
+        if ((int64_t)slot < n) {
+            spos[slot] = z;
+            inv[k] = slot;
+        } else {
+            inv[k] = 0xffffffffu;
+            atomicOr(status, (unsigned)DC_ERR_RANGE);
         }
     }
 }
 
-// pos[perm[s]] = spos[s]
+// pos[k] = spos[inv[k]]
 __global__ void __launch_bounds__(kThreads) reorder_gather_back_kernel(const float2 *__restrict__ spos,
-                                                                       const uint32_t *__restrict__ perm, int64_t n,
+                                                                       const uint32_t *__restrict__ inv, int64_t n,
                                                                        float2 *__restrict__ pos,
                                                                        unsigned *__restrict__ status)
 {
+    pdl_wait();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += stride) {
-        const uint32_t k = perm[s];
-        if ((int64_t)k < n) pos[k] = spos[s];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const uint32_t s = inv[k];
+        if ((int64_t)s < n) pos[k] = spos[s];
         else atomicOr(status, (unsigned)DC_ERR_RANGE);
     }
 }
@@ -287,6 +311,7 @@ __global__ void __launch_bounds__(kThreads) reorder_gather_back_kernel(const flo
 __global__ void __launch_bounds__(kThreads) quality_kernel(const uint32_t *__restrict__ counts, int log2N,
                                                            unsigned long long *__restrict__ acc)
 {
+    pdl_wait();
     const int N = 1 << log2N;
     const int B = N >> 2;
     const int nbins = B * B;
@@ -342,8 +367,8 @@ int grid_for(int64_t n, int per_block, int max_blocks)
 cudaError_t launch_splat(cudaStream_t s, const float2 *pos, int64_t n, uint32_t *counts, int log2N)
 {
     if (n <= 0) return cudaSuccess;
-    splat_kernel<<<grid_for(n, kThreads, 152 * 16), kThreads, 0, s>>>(pos, n, counts, log2N);
-    return cudaGetLastError();
+    return launch_kernel(splat_kernel, dim3(grid_for(n, kThreads, 152 * 16)), dim3(kThreads), 0, s, pos, n, counts,
+                         log2N);
 }
 
 cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *disp, int log2N,
@@ -351,9 +376,8 @@ cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *
 {
     if (n <= 0) return cudaSuccess;
     // two pairs (four samples) per thread and trip
-    advect_kernel<<<grid_for((n + 3) / 4, kThreads, 152 * 8), kThreads, 0, s>>>(
-        pos, n, disp, log2N, pixel_center ? 0.5f : 0.0f, clamp, counts_next);
-    return cudaGetLastError();
+    return launch_kernel(advect_kernel, dim3(grid_for((n + 3) / 4, kThreads, 152 * 8)), dim3(kThreads), 0, s, pos, n,
+                         disp, log2N, pixel_center ? 0.5f : 0.0f, clamp, counts_next);
 }
 
 int64_t reorder_scan_chunk(int log2N)
@@ -370,33 +394,42 @@ cudaError_t launch_reorder_scan(cudaStream_t s, const uint32_t *counts, int log2
     const int64_t M = (int64_t)1 << (2 * log2N);
     const int64_t chunk = reorder_scan_chunk(log2N);
     const int blocks = (int)((M + chunk - 1) / chunk);
-    scan_partials_kernel<<<blocks, kScanThreads, 0, s>>>(counts, M, chunk, partials);
-    scan_apply_kernel<<<blocks, kScanThreads, 0, s>>>(counts, M, chunk, partials, cursor);
-    return cudaGetLastError();
+    cudaError_t e = launch_kernel(scan_partials_kernel, dim3(blocks), dim3(kScanThreads), 0, s, counts, M, chunk,
+                                  partials);
+    if (e != cudaSuccess) return e;
+    return launch_kernel(scan_apply_kernel, dim3(blocks), dim3(kScanThreads), 0, s, counts, M, chunk,
+                         (const uint32_t *)partials, cursor);
 }
 
-cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n, int log2N, uint32_t *cursor,
-                                   float2 *spos, uint32_t *perm, unsigned *status)
+cudaError_t launch_splat_rank(cudaStream_t s, const float2 *pos, int64_t n, uint32_t *counts, int log2N,
+                              uint32_t *rank)
 {
     if (n <= 0) return cudaSuccess;
-    reorder_scatter_kernel<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, s>>>(pos, n, log2N, cursor, spos, perm,
-                                                                                status);
-    return cudaGetLastError();
+    return launch_kernel(splat_rank_kernel, dim3(grid_for(n, kThreads, 152 * 16)), dim3(kThreads), 0, s, pos, n,
+                         counts, log2N, rank);
 }
 
-cudaError_t launch_reorder_back(cudaStream_t s, const float2 *spos, const uint32_t *perm, int64_t n, float2 *pos,
+cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n, int log2N, const uint32_t *cursor,
+                                   const uint32_t *rank, float2 *spos, uint32_t *inv, unsigned *status)
+{
+    if (n <= 0) return cudaSuccess;
+    return launch_kernel(reorder_scatter_kernel, dim3(grid_for(n, kThreads, 152 * 8)), dim3(kThreads), 0, s, pos, n,
+                         log2N, cursor, rank, spos, inv, status);
+}
+
+cudaError_t launch_reorder_back(cudaStream_t s, const float2 *spos, const uint32_t *inv, int64_t n, float2 *pos,
                                 unsigned *status)
 {
     if (n <= 0) return cudaSuccess;
-    reorder_gather_back_kernel<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, s>>>(spos, perm, n, pos, status);
-    return cudaGetLastError();
+    return launch_kernel(reorder_gather_back_kernel, dim3(grid_for(n, kThreads, 152 * 8)), dim3(kThreads), 0, s,
+                         spos, inv, n, pos, status);
 }
 
 cudaError_t launch_quality(cudaStream_t s, const uint32_t *counts, int log2N, unsigned long long *acc)
 {
     const int B = (1 << log2N) >> 2;
-    quality_kernel<<<grid_for((int64_t)B * B, kThreads, 152 * 4), kThreads, 0, s>>>(counts, log2N, acc);
-    return cudaGetLastError();
+    return launch_kernel(quality_kernel, dim3(grid_for((int64_t)B * B, kThreads, 152 * 4)), dim3(kThreads), 0, s,
+                         counts, log2N, acc);
 }
 
 }  // namespace dc
