@@ -209,6 +209,52 @@ const char *declutter_kernel_name(int32_t k);
 const char *declutter_status_string(dc_status s);
 const char *declutter_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Batched regularisation of many independent scatterplots, e.g. all
+ * dimension-pair panels of a scatterplot matrix, with per-panel resolution
+ * and sample count (not in the paper; the paper regularises one plot).
+ * Every panel is an independent problem with its own context; one call runs
+ * all panels' iterations as the independent branches of one CUDA graph
+ * (captured on the first call for the given sample pointers, sizes,
+ * iterations and metrics flag, replayed afterwards).
+ * ------------------------------------------------------------------------ */
+typedef struct dc_batch dc_batch;
+
+/* base: shared parameters (its log2_res is ignored); log2_res[p] and
+ * max_samples[p] (host arrays of n_panels entries): each panel's resolution
+ * and the largest sample count it will be given.  Panels run on cuda_stream
+ * (or a library stream when NULL). */
+dc_status declutter_batch_create(const dc_params *base, const uint32_t *log2_res, const int64_t *max_samples,
+                                 int32_t n_panels, int device, void *cuda_stream, dc_batch **out);
+dc_status declutter_batch_destroy(dc_batch *batch);
+
+/* pos_xy: host array of n_panels device pointers (float[2 n[p]] each, moved in
+ * place); n: host array of sample counts (<= max_samples).  uniformity_out:
+ * host double[n_panels * iters] (panel-major) of the Sec. 6.2 bin std after
+ * each iteration, or NULL (then the call is asynchronous).  Results are
+ * identical to regularize() on each panel alone. */
+dc_status declutter_batch_regularize(dc_batch *batch, float *const *pos_xy, const int64_t *n, int32_t iters,
+                                     double *uniformity_out);
+
+/* Wait for the batch's stream; returns the first CUDA error or device status. */
+dc_status declutter_batch_sync(dc_batch *batch);
+
+/* Autotuner of the integral-image band height (rows per band): times
+ * regularize(iters) on a copy of the given samples for every band height
+ * 1, 2, 4, ... 64 with at most 1024 bands, and returns the fastest in
+ * *best_out (its median time in *best_ms_out, or -1 when the answer came
+ * from the cache).  Answers are cached per (device, resolution, radius, carry
+ * mode, floor(log2 n)) for the life of the process.  The samples are not
+ * modified.  Synchronises. */
+dc_status declutter_autotune_band_rows(const dc_params *params, int device, void *cuda_stream, const float *pos_xy,
+                                       int64_t n, int32_t iters, int32_t *best_out, float *best_ms_out);
+
+/* Autotunes every resolution of a batch on its largest panel and rebuilds the
+ * panels' contexts with the chosen band heights (band_rows_out: host
+ * int32[n_panels] or NULL). */
+dc_status declutter_batch_autotune(dc_batch *batch, float *const *pos_xy, const int64_t *n, int32_t iters,
+                                   int32_t *band_rows_out);
+
 /* No-allocation variant of integral_images_u32(), for callers that cannot
  * allocate device memory when they need the result: code running while a
  * stream is captured into a CUDA graph (where cudaMalloc and cudaFree are not

@@ -296,6 +296,29 @@ const char *kKernelNames[DC_KERNEL_KINDS] = {"splat",  "smooth", "band_aggregate
 
 void dc::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
 
+dc_status dc::prepare_regularize(dc_ctx *c, int64_t n, int iters, int metrics)
+{
+    if (dc_status st = check_samples(c, reinterpret_cast<const void *>(16), n)) return st;
+    if (metrics)
+        if (dc_status st = ensure_qslots(c, iters)) return st;
+    return ensure_sort_buffers(c, n);
+}
+
+cudaError_t dc::enqueue_regularize(dc_ctx *c, cudaStream_t s, float *pos, int64_t n, int iters, int metrics)
+{
+    Recorder rec;
+    return enqueue_iterations(c, s, pos, n, iters, metrics, rec);
+}
+
+void dc::finish_regularize(dc_ctx *c, int64_t n, int iters, int metrics)
+{
+    c->n_last = n;
+    c->have_disp = true;
+    c->cur_counts = metrics ? (iters & 1) : ((iters - 1) & 1);
+}
+
+void dc::read_metrics(const dc_ctx *c, const unsigned long long *acc, double *out3) { metrics_from_acc(c, acc, out3); }
+
 bool dc::pdl_enabled()
 {
     static const bool on = [] {

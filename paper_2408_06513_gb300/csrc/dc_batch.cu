@@ -1,0 +1,358 @@
+// Batched regularisation of many independent scatterplots (the panels of a
+// scatterplot matrix) and the band-height autotuner.
+//
+// Each panel has its own context (resolution, buffers).  All panels' iteration
+// sequences are captured into one CUDA graph as independent branches (a fork
+// from the capture stream to one stream per panel and a join back), so one
+// graph launch runs every panel, and panels of different sizes overlap on the
+// GPU.  The graph is cached per (sample pointers, sizes, iterations, metrics).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "dc_internal.cuh"
+
+using namespace dc;
+
+struct dc_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    dc_params base{};
+    std::vector<dc_ctx *> ctx;
+    std::vector<uint32_t> log2;
+    std::vector<int64_t> cap;
+    std::vector<cudaStream_t> branch;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    struct Entry {
+        std::vector<const void *> pos;
+        std::vector<int64_t> n;
+        int iters = 0;
+        int metrics = 0;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<Entry> graphs;
+};
+
+namespace {
+
+dc_status bfail(dc_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    set_last_error(buf);
+    return st;
+}
+
+#define DC_BCUDA(call)                                                                            \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return bfail(DC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+struct Guard {
+    int prev = -1;
+    bool changed = false;
+    explicit Guard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~Guard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+// autotuned band heights: (device, log2 N, radius, carry mode, log2 of n) -> rows
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;
+
+int n_bucket(int64_t n) { return n > 0 ? (int)std::floor(std::log2((double)n)) : 0; }
+
+void drop_graphs(dc_batch *b)
+{
+    for (auto &e : b->graphs)
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+    b->graphs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+dc_status declutter_autotune_band_rows(const dc_params *params, int device, void *cuda_stream, const float *pos_xy,
+                                       int64_t n, int32_t iters, int32_t *best_out, float *best_ms_out)
+{
+    if (!params || !best_out) return bfail(DC_ERR_INVALID_ARG, "null params or best_out");
+    if (n <= 0 || !pos_xy || (reinterpret_cast<uintptr_t>(pos_xy) & 7)) return bfail(DC_ERR_INVALID_ARG, "samples");
+    if (iters < 1) return bfail(DC_ERR_INVALID_ARG, "iters = %d", iters);
+    if (params->log2_res < 4 || params->log2_res > 13) return bfail(DC_ERR_NOT_POW2, "log2_res");
+    const int N = 1 << params->log2_res;
+    const int r = params->kernel_r < 0 ? (N / 128 < 2 ? 2 : N / 128) : params->kernel_r;
+    const auto key = std::make_tuple(device, (int)params->log2_res, r, (int)params->carry_mode, n_bucket(n));
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *best_out = it->second;
+            if (best_ms_out) *best_ms_out = -1.f;
+            return DC_OK;
+        }
+    }
+    Guard guard(device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    float *tmp = nullptr;
+    if (cudaMalloc(&tmp, sizeof(float) * 2 * (size_t)n) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(DC_ERR_OOM, "autotune staging");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = 0.f;
+    dc_status st = DC_OK;
+    for (int T = 1; T <= 64 && st == DC_OK; T *= 2) {
+        if (T > N || N / T > 1024) continue;
+        dc_params p = *params;
+        p.band_rows = T;
+        dc_ctx *c = nullptr;
+        if ((st = declutter_create(&p, device, cuda_stream, &c)) != DC_OK) break;
+        float ms[5];
+        for (int rep = -2; rep < 5 && st == DC_OK; ++rep) {
+            if (cudaMemcpyAsync(tmp, pos_xy, sizeof(float) * 2 * (size_t)n, cudaMemcpyDeviceToDevice, c->stream) !=
+                cudaSuccess) {
+                st = bfail(DC_ERR_CUDA, "autotune copy");
+                break;
+            }
+            cudaEventRecord(e0, c->stream);
+            st = regularize(c, tmp, n, iters, nullptr);
+            cudaEventRecord(e1, c->stream);
+            if (st == DC_OK && cudaEventSynchronize(e1) != cudaSuccess) st = bfail(DC_ERR_CUDA, "autotune sync");
+            if (st == DC_OK && rep >= 0) cudaEventElapsedTime(&ms[rep], e0, e1);
+        }
+        declutter_destroy(c);
+        if (st != DC_OK) break;
+        std::sort(ms, ms + 5);
+        if (!best || ms[2] < best_ms) {
+            best = T;
+            best_ms = ms[2];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(tmp);
+    (void)s;
+    if (st != DC_OK) return st;
+    if (!best) return bfail(DC_ERR_INVALID_ARG, "no band height fits");
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    *best_out = best;
+    if (best_ms_out) *best_ms_out = best_ms;
+    return DC_OK;
+}
+
+dc_status declutter_batch_create(const dc_params *base, const uint32_t *log2_res, const int64_t *max_samples,
+                                 int32_t n_panels, int device, void *cuda_stream, dc_batch **out)
+{
+    if (!base || !log2_res || !max_samples || !out) return bfail(DC_ERR_INVALID_ARG, "null argument");
+    if (n_panels < 1 || n_panels > 4096) return bfail(DC_ERR_INVALID_ARG, "n_panels = %d", n_panels);
+    *out = nullptr;
+    Guard guard(device);
+    dc_batch *b = new dc_batch();
+    b->device = device;
+    b->base = *base;
+    auto bail = [&](dc_status st) {
+        declutter_batch_destroy(b);
+        return st;
+    };
+    if (cuda_stream) {
+        b->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreate(&b->stream) != cudaSuccess) return bail(bfail(DC_ERR_CUDA, "cudaStreamCreate"));
+        b->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        return bail(bfail(DC_ERR_CUDA, "stream or event creation"));
+    for (int p = 0; p < n_panels; ++p) {
+        if (max_samples[p] < 0 || max_samples[p] >= (int64_t(1) << 32))
+            return bail(bfail(DC_ERR_INVALID_ARG, "max_samples[%d]", p));
+        dc_params pp = *base;
+        pp.log2_res = log2_res[p];
+        dc_ctx *c = nullptr;
+        if (dc_status st = declutter_create(&pp, device, b->stream, &c)) return bail(st);
+        b->ctx.push_back(c);
+        b->log2.push_back(log2_res[p]);
+        b->cap.push_back(max_samples[p]);
+        cudaStream_t br = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&br, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            return bail(bfail(DC_ERR_CUDA, "branch stream"));
+        b->branch.push_back(br);
+        b->join.push_back(ev);
+        if (dc_status st = prepare_regularize(c, max_samples[p], 1, 0)) return bail(st);
+    }
+    *out = b;
+    return DC_OK;
+}
+
+dc_status declutter_batch_destroy(dc_batch *b)
+{
+    if (!b) return DC_OK;
+    Guard guard(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    for (auto *c : b->ctx) declutter_destroy(c);
+    for (auto s : b->branch) cudaStreamDestroy(s);
+    for (auto e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return DC_OK;
+}
+
+dc_status declutter_batch_autotune(dc_batch *b, float *const *pos_xy, const int64_t *n, int32_t iters,
+                                   int32_t *band_rows_out)
+{
+    if (!b || !pos_xy || !n) return bfail(DC_ERR_INVALID_ARG, "null argument");
+    Guard guard(b->device);
+    const int P = (int)b->ctx.size();
+    // one representative per resolution: the panel with the most samples
+    std::map<uint32_t, int> rep;
+    for (int p = 0; p < P; ++p) {
+        auto it = rep.find(b->log2[p]);
+        if (it == rep.end() || n[p] > n[it->second]) rep[b->log2[p]] = p;
+    }
+    std::map<uint32_t, int> best;
+    for (auto &kv : rep) {
+        dc_params pp = b->base;
+        pp.log2_res = kv.first;
+        int32_t T = 0;
+        if (dc_status st = declutter_autotune_band_rows(&pp, b->device, b->stream, pos_xy[kv.second], n[kv.second],
+                                                        iters, &T, nullptr))
+            return st;
+        best[kv.first] = T;
+    }
+    drop_graphs(b);
+    for (int p = 0; p < P; ++p) {
+        const int T = best[b->log2[p]];
+        if (b->ctx[p]->g.T != T) {
+            dc_params pp = b->base;
+            pp.log2_res = b->log2[p];
+            pp.band_rows = T;
+            dc_ctx *c = nullptr;
+            if (dc_status st = declutter_create(&pp, b->device, b->stream, &c)) return st;
+            if (dc_status st = prepare_regularize(c, b->cap[p], 1, 0)) {
+                declutter_destroy(c);
+                return st;
+            }
+            declutter_destroy(b->ctx[p]);
+            b->ctx[p] = c;
+        }
+        if (band_rows_out) band_rows_out[p] = T;
+    }
+    return DC_OK;
+}
+
+dc_status declutter_batch_regularize(dc_batch *b, float *const *pos_xy, const int64_t *n, int32_t iters,
+                                     double *uniformity_out)
+{
+    if (!b || !pos_xy || !n) return bfail(DC_ERR_INVALID_ARG, "null argument");
+    if (iters < 0) return bfail(DC_ERR_INVALID_ARG, "iters = %d", iters);
+    if (iters == 0) return DC_OK;
+    Guard guard(b->device);
+    const int P = (int)b->ctx.size();
+    const int metrics = uniformity_out ? 1 : 0;
+    bool moved = false;
+    for (int p = 0; p < P; ++p) {
+        if (n[p] < 0 || n[p] > b->cap[p]) return bfail(DC_ERR_INVALID_ARG, "n[%d] = %lld", p, (long long)n[p]);
+        if (n[p] > 0 && (!pos_xy[p] || (reinterpret_cast<uintptr_t>(pos_xy[p]) & 7)))
+            return bfail(DC_ERR_INVALID_ARG, "pos_xy[%d]", p);
+        const void *q0 = b->ctx[p]->qacc, *s0 = b->ctx[p]->spos;
+        if (dc_status st = prepare_regularize(b->ctx[p], n[p], iters, metrics)) return st;
+        moved |= q0 != b->ctx[p]->qacc || s0 != b->ctx[p]->spos;
+    }
+    if (moved) drop_graphs(b);  // cached graphs hold the old buffer addresses
+    cudaGraphExec_t exec = nullptr;
+    for (auto &e : b->graphs) {
+        if (e.iters != iters || e.metrics != metrics) continue;
+        bool same = true;
+        for (int p = 0; p < P && same; ++p) same = e.pos[p] == pos_xy[p] && e.n[p] == n[p];
+        if (same) exec = e.exec;
+    }
+    if (!exec) {
+        if (b->graphs.size() >= 8) {
+            cudaGraphExecDestroy(b->graphs.front().exec);
+            b->graphs.erase(b->graphs.begin());
+        }
+        cudaGraph_t graph = nullptr;
+        DC_BCUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaEventRecord(b->fork, b->cap_stream);
+        for (int p = 0; p < P && e == cudaSuccess; ++p) {
+            e = cudaStreamWaitEvent(b->branch[p], b->fork, 0);
+            if (e == cudaSuccess) e = enqueue_regularize(b->ctx[p], b->branch[p], pos_xy[p], n[p], iters, metrics);
+            if (e == cudaSuccess) e = cudaEventRecord(b->join[p], b->branch[p]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap_stream, b->join[p], 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return bfail(DC_ERR_CUDA, "batch capture: %s / %s", cudaGetErrorString(e), cudaGetErrorString(e2));
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return bfail(DC_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        dc_batch::Entry en;
+        en.pos.assign(pos_xy, pos_xy + P);
+        en.n.assign(n, n + P);
+        en.iters = iters;
+        en.metrics = metrics;
+        en.exec = exec;
+        b->graphs.push_back(en);
+    }
+    DC_BCUDA(cudaGraphLaunch(exec, b->stream));
+    for (int p = 0; p < P; ++p) finish_regularize(b->ctx[p], n[p], iters, metrics);
+    if (metrics) {
+        std::vector<unsigned long long> acc(3 * (size_t)iters * P);
+        for (int p = 0; p < P; ++p)
+            DC_BCUDA(cudaMemcpyAsync(acc.data() + 3 * (size_t)iters * p, b->ctx[p]->qacc,
+                                     3 * (size_t)iters * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                     b->stream));
+        DC_BCUDA(cudaStreamSynchronize(b->stream));
+        for (int p = 0; p < P; ++p)
+            for (int it = 0; it < iters; ++it) {
+                double m[3];
+                read_metrics(b->ctx[p], &acc[3 * ((size_t)iters * p + it)], m);
+                uniformity_out[(size_t)iters * p + it] = m[0];
+            }
+    }
+    return DC_OK;
+}
+
+dc_status declutter_batch_sync(dc_batch *b)
+{
+    if (!b) return bfail(DC_ERR_INVALID_ARG, "null batch");
+    Guard guard(b->device);
+    DC_BCUDA(cudaStreamSynchronize(b->stream));
+    for (auto *c : b->ctx)
+        if (dc_status st = declutter_sync(c)) return st;
+    return DC_OK;
+}
+
+}  // extern "C"

@@ -129,6 +129,13 @@ cudaError_t launch_band_final(cudaStream_t s, const BandGeom &g, int mode, const
 int smooth_smem_bytes(int r);
 cudaError_t prepare_kernels();  // per-device kernel attributes; call with the device current
 void set_last_error(const char *msg);  // message returned by declutter_last_error()
+// regularize() building blocks for the batched runtime: buffers for n samples
+// (outside any capture), the iteration sequence on stream s, and the
+// context's state after it; Sec. 6.2 measures from quality accumulators
+dc_status prepare_regularize(dc_ctx *c, int64_t n, int iters, int metrics);
+cudaError_t enqueue_regularize(dc_ctx *c, cudaStream_t s, float *pos, int64_t n, int iters, int metrics);
+void finish_regularize(dc_ctx *c, int64_t n, int iters, int metrics);
+void read_metrics(const dc_ctx *c, const unsigned long long *acc, double *out3);
 
 }  // namespace dc
 

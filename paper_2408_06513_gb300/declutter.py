@@ -28,7 +28,9 @@ __all__ = [
     "integral_images_u32", "displacement_field", "advect_samples", "regularize", "regularize_host",
     "quality_metrics", "declutter_sync", "declutter_profile_regularize", "declutter_kernel_name",
     "declutter_status_string", "declutter_last_error", "DC_CARRY_COMPENSATED", "DC_CARRY_F64",
-    "integral_images_u32_noalloc", "DC_NOALLOC_MAX_LOG2_RES",
+    "integral_images_u32_noalloc", "DC_NOALLOC_MAX_LOG2_RES", "Batch", "declutter_batch_create",
+    "declutter_batch_destroy", "declutter_batch_regularize", "declutter_batch_sync",
+    "declutter_autotune_band_rows", "declutter_batch_autotune",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -95,6 +97,14 @@ _SIGS = [
     ("declutter_profile_regularize", ctypes.c_int,
      [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     ("integral_images_u32_noalloc", ctypes.c_int, [_P, ctypes.c_uint32, _P, _P, _P]),
+    ("declutter_batch_create", ctypes.c_int,
+     [ctypes.POINTER(dc_params), _P, _P, ctypes.c_int32, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    ("declutter_batch_destroy", ctypes.c_int, [_P]),
+    ("declutter_batch_regularize", ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P]),
+    ("declutter_batch_sync", ctypes.c_int, [_P]),
+    ("declutter_autotune_band_rows", ctypes.c_int,
+     [ctypes.POINTER(dc_params), ctypes.c_int, _P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]),
+    ("declutter_batch_autotune", ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P]),
     ("declutter_kernel_name", ctypes.c_char_p, [ctypes.c_int32]),
     ("declutter_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("declutter_last_error", ctypes.c_char_p, []),
@@ -178,6 +188,30 @@ class Context:
         declutter_destroy(self)
 
 
+def make_params(log2_res: int, kernel_r: int = -1, sigma: float = 0.0, d0: float = -1.0,
+                pixel_center: bool = False, clamp_positions: bool = True,
+                carry_mode: int = DC_CARRY_COMPENSATED, band_rows: int = 0, keep_order: bool = False) -> dc_params:
+    p = dc_params()
+    p.log2_res = int(log2_res)
+    p.kernel_r = int(kernel_r)
+    p.sigma = float(sigma)
+    p.d0 = float(d0)
+    p.pixel_center = int(bool(pixel_center))
+    p.clamp_positions = int(bool(clamp_positions))
+    p.carry_mode = int(carry_mode)
+    p.band_rows = int(band_rows)
+    p.keep_order = int(bool(keep_order))
+    return p
+
+
+def _stream_ptr(stream, device):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    sp = getattr(stream, "cuda_stream", stream) or 0
+    return ctypes.c_void_p(sp) if sp else None
+
+
 def declutter_create(log2_res: int, kernel_r: int = -1, sigma: float = 0.0, d0: float = -1.0,
                      pixel_center: bool = False, clamp_positions: bool = True,
                      carry_mode: int = DC_CARRY_COMPENSATED, band_rows: int = 0, keep_order: bool = False,
@@ -192,16 +226,7 @@ def declutter_create(log2_res: int, kernel_r: int = -1, sigma: float = 0.0, d0: 
     if stream is None:
         stream = torch.cuda.current_stream(device)
     sp = getattr(stream, "cuda_stream", stream) or 0
-    p = dc_params()
-    p.log2_res = int(log2_res)
-    p.kernel_r = int(kernel_r)
-    p.sigma = float(sigma)
-    p.d0 = float(d0)
-    p.pixel_center = int(bool(pixel_center))
-    p.clamp_positions = int(bool(clamp_positions))
-    p.carry_mode = int(carry_mode)
-    p.band_rows = int(band_rows)
-    p.keep_order = int(bool(keep_order))
+    p = make_params(log2_res, kernel_r, sigma, d0, pixel_center, clamp_positions, carry_mode, band_rows, keep_order)
     h = ctypes.c_void_p()
     _check(lib.declutter_create(ctypes.byref(p), int(device), ctypes.c_void_p(sp) if sp else None,
                                 ctypes.byref(h)), "declutter_create")
@@ -347,3 +372,96 @@ def integral_images_u32_noalloc(grid, log2_res: int, alpha_out=None, alpha_t_out
                                                       _u64(alpha_t_out, NN, "alpha_t_out"),
                                                       ctypes.c_void_p(sp) if sp else None),
            "integral_images_u32_noalloc")
+
+
+@dataclass
+class Batch:
+    """Owner of a ``dc_batch*`` (panels of a scatterplot matrix)."""
+    handle: ctypes.c_void_p
+    log2_res: list
+    max_samples: list
+    device: int
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        declutter_batch_destroy(self)
+
+
+def declutter_batch_create(log2_res, max_samples, device: int | None = None, stream=None, **params) -> Batch:
+    """``log2_res``, ``max_samples``: per-panel lists; ``params``: as for
+    :func:`declutter_create` (its log2_res is per panel here)."""
+    import torch
+    if device is None:
+        device = torch.cuda.current_device()
+    P = len(log2_res)
+    if len(max_samples) != P:
+        raise ValueError("log2_res and max_samples differ in length")
+    p = make_params(0, **params)
+    l2 = (ctypes.c_uint32 * P)(*[int(x) for x in log2_res])
+    ms = (ctypes.c_int64 * P)(*[int(x) for x in max_samples])
+    h = ctypes.c_void_p()
+    _check(load_library().declutter_batch_create(ctypes.byref(p), l2, ms, P, int(device),
+                                                 _stream_ptr(stream, device), ctypes.byref(h)),
+           "declutter_batch_create")
+    return Batch(h, list(log2_res), list(max_samples), int(device))
+
+
+def declutter_batch_destroy(batch: Batch) -> None:
+    if batch.handle:
+        _check(load_library().declutter_batch_destroy(batch.handle), "declutter_batch_destroy")
+        batch.handle = ctypes.c_void_p()
+
+
+def _batch_arrays(positions):
+    P = len(positions)
+    ptrs = (ctypes.c_void_p * P)()
+    ns = (ctypes.c_int64 * P)()
+    for k, t in enumerate(positions):
+        pp, n = _pos_args(t)
+        ptrs[k] = pp
+        ns[k] = n
+    return ptrs, ns
+
+
+def declutter_batch_regularize(batch: Batch, positions, iters: int, uniformity: bool = False):
+    """``positions``: list of CUDA float32 [n_p, 2] tensors, one per panel."""
+    P = len(positions)
+    ptrs, ns = _batch_arrays(positions)
+    out = (ctypes.c_double * max(P * int(iters), 1))() if uniformity else None
+    _check(load_library().declutter_batch_regularize(batch.handle, ptrs, ns, int(iters), out),
+           "declutter_batch_regularize")
+    if not uniformity:
+        return None
+    return [list(out[p * iters:(p + 1) * iters]) for p in range(P)]
+
+
+def declutter_batch_sync(batch: Batch) -> None:
+    _check(load_library().declutter_batch_sync(batch.handle), "declutter_batch_sync")
+
+
+def declutter_autotune_band_rows(pos, iters: int, log2_res: int, device: int | None = None, stream=None,
+                                 **params):
+    """Fastest band height for ``regularize(iters)`` on these samples:
+    returns ``(band_rows, median_ms or -1 if cached)``."""
+    import torch
+    if device is None:
+        device = torch.cuda.current_device()
+    p = make_params(log2_res, **params)
+    pp, n = _pos_args(pos)
+    best = ctypes.c_int32()
+    ms = ctypes.c_float()
+    _check(load_library().declutter_autotune_band_rows(ctypes.byref(p), int(device), _stream_ptr(stream, device), pp,
+                                                       n, int(iters), ctypes.byref(best), ctypes.byref(ms)),
+           "declutter_autotune_band_rows")
+    return int(best.value), float(ms.value)
+
+
+def declutter_batch_autotune(batch: Batch, positions, iters: int):
+    P = len(positions)
+    ptrs, ns = _batch_arrays(positions)
+    out = (ctypes.c_int32 * P)()
+    _check(load_library().declutter_batch_autotune(batch.handle, ptrs, ns, int(iters), out),
+           "declutter_batch_autotune")
+    return list(out)

@@ -19,6 +19,12 @@ Workloads (sizes follow the configurations the method is measured on):
                    U[0.03, 0.08]); used on a 2048x2048 grid.
 * ``sat_grid``  -- uint32 grids with values U{0..255} for the standalone
                    integral-image sweep (256^2 .. 8192^2).
+* ``splom``     -- scatterplot matrix: 200,000 rows of a 16-dimensional
+                   12-component correlated Gaussian mixture (means U[-3,3]^16,
+                   covariances A A^T with A ~ N(0, 0.3^2)); all 120 dimension
+                   pairs, each min-max normalised; panel p keeps a seeded
+                   fraction U[0.25, 1] of the rows and uses a grid of
+                   256^2 / 512^2 / 1024^2 for p mod 3 = 0 / 1 / 2.
 
 Samples drawn outside the unit square are rejected and redrawn; the reject
 fraction is returned with the samples.  The paper's own statistics use random
@@ -41,6 +47,7 @@ __all__ = [
     "four_clusters",
     "WORKLOADS",
     "workload",
+    "splom",
 ]
 
 
@@ -194,3 +201,28 @@ def workload(name: str, n: int | None = None):
     z, _ = spec["gen"](nn)
     spec["n"] = nn
     return z, spec
+
+
+def splom(rows: int = 200_000, dims: int = 16, comps: int = 12, seed: int = 4):
+    """Panels of a scatterplot matrix: list of ``(samples float32 [n_p, 2],
+    log2_res)`` for every pair i < j of the ``dims`` dimensions."""
+    rng = np.random.default_rng(seed)
+    means = rng.uniform(-3.0, 3.0, size=(comps, dims))
+    A = rng.normal(0.0, 0.3, size=(comps, dims, dims))
+    w = rng.uniform(0.5, 1.5, size=comps)
+    w = w / w.sum()
+    comp = rng.choice(comps, size=rows, p=w)
+    e = rng.standard_normal((rows, dims))
+    X = np.einsum("rij,rj->ri", A[comp], e) + means[comp]
+    panels = []
+    p = 0
+    for i in range(dims):
+        for j in range(i + 1, dims):
+            frac = rng.uniform(0.25, 1.0)
+            keep = rng.random(rows) < frac
+            z = X[keep][:, [i, j]]
+            lo, hi = z.min(axis=0), z.max(axis=0)
+            z = (z - lo) / np.where(hi > lo, hi - lo, 1.0)
+            panels.append((np.ascontiguousarray(z.astype(np.float32)), (8, 9, 10)[p % 3]))
+            p += 1
+    return panels
