@@ -401,6 +401,7 @@ def run_gpu(args, world, rank, local, pg):
     e2e_value = world * n * iters / e2e_s / 1e6
 
     batched = None if args.no_batched else run_batched(args, dc, dev, stream, flush, seed_offset=rank)
+    surrogate = None if args.surrogate_budget <= 0 else run_surrogate(args, dc, dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -421,6 +422,7 @@ def run_gpu(args, world, rank, local, pg):
             "kernels": kernels,
             "cpu_baseline": cpu,
             "batched": batched,
+            "surrogate": surrogate,
             "clocks": clocks.summary(),
         }
         print(json.dumps(line), flush=True)
@@ -503,6 +505,79 @@ def run_batched(args, dc, dev, stream, flush, seed_offset=0):
         dc.declutter_batch_destroy(batch)
 
 
+def run_surrogate(args, dc, dev):
+    """Learned surrogate at 256^2: train the 4-level network (32..256 channels)
+    on pairs the plain method generates, within a time budget, then compare
+    one surrogate pass (+ plain iterations as fallback) with the plain
+    iterations on held-out mixtures of 2M samples, at equal uniformity
+    (Sec. 6.2 bin std / mean)."""
+    import torch
+
+    from paper_2408_06513_gb300 import surrogate as SG
+
+    rng = np.random.default_rng(5)
+    gen = SG.PairGenerator(log2_res=8, iters=8, kernel_r=2, device=dev.index)
+    t0 = time.perf_counter()
+    dens, scales, target = gen.make(args.surrogate_pairs, rng)
+    held = gen.make(32, np.random.default_rng(99))
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    gen.close()
+    sg = dc.surrogate_create(8, 4, 32, max_batch=16, seed=1, device=dev.index)
+    ctx = dc.declutter_create(8, kernel_r=2, device=dev.index)
+    try:
+        t0 = time.perf_counter()
+        losses = SG.train(sg, dens, scales, target, steps=1_000_000, batch=16, lr=1e-3, rng=rng,
+                          time_budget_s=args.surrogate_budget, log_every=100)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        err = SG.field_error(sg, *held)
+
+        def wall(fn):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            return (time.perf_counter() - a) * 1e3, r
+
+        rows = []
+        n = 2_000_000
+        mean = n / (256 // 4) ** 2
+        for t in range(4):
+            r2 = np.random.default_rng(700 + t)
+            z = SG.gmm_samples(n, int(r2.integers(2, 31)), r2, dev)
+            u = dc.regularize(ctx, z.clone(), 8, uniformity=True)
+            cv_plain = [x / mean for x in u]
+            target_cv = 1.05 * cv_plain[-1]
+            for _ in range(2):  # warm-up: graph capture of every iteration count used below
+                dc.regularize(ctx, z.clone(), 8)
+                dc.regularize(ctx, z.clone(), 1)
+                dc.surrogate_apply(ctx, sg, z.clone(), 0.0, 0)
+            ms_sg, (used0, cv_sg) = wall(lambda: dc.surrogate_apply(ctx, sg, z.clone(), 0.0, 0))
+            worth = sum(1 for c in cv_plain if c >= cv_sg)
+            ms_plain_eq = wall(lambda: dc.regularize(ctx, z.clone(), max(worth, 1)))[0] if worth else 0.0
+            ms_plain8 = wall(lambda: dc.regularize(ctx, z.clone(), 8))[0]
+            ms_fb, (used, cv_fb) = wall(lambda: dc.surrogate_apply(ctx, sg, z.clone(), target_cv, 16))
+            rows.append({"cv0_plain": cv_plain[0], "cv_plain8": cv_plain[-1], "cv_surrogate": cv_sg,
+                         "worth_plain_iters": worth, "ms_surrogate_pass": ms_sg, "ms_plain_equal_quality": ms_plain_eq,
+                         "ms_plain8": ms_plain8, "ms_surrogate_to_plain8_quality": ms_fb, "fallback_plain_iters": used,
+                         "cv_after_fallback": cv_fb})
+        avg = lambda k: float(np.mean([r[k] for r in rows]))  # noqa: E731
+        return {"model": "conv encoder-decoder, 4 levels, 32/64/128/256 channels, 3x3, bf16 weights, fp32 accumulation",
+                "grid": 256, "target_iterations": 8, "pairs": int(dens.shape[0]), "pair_generation_s": t_gen,
+                "train_s": t_train, "train_steps": losses[-1][0] + 1 if losses else 0, "batch": 16,
+                "loss_first": losses[0][1] if losses else None, "loss_last": losses[-1][1] if losses else None,
+                "field_rms_px": err["rms_px"], "field_target_rms_px": err["target_rms_px"],
+                "eval_samples": n, "worth_plain_iters_mean": avg("worth_plain_iters"),
+                "ms_surrogate_pass": avg("ms_surrogate_pass"), "ms_plain_equal_quality": avg("ms_plain_equal_quality"),
+                "ms_plain8": avg("ms_plain8"), "ms_surrogate_to_plain8_quality": avg("ms_surrogate_to_plain8_quality"),
+                "fallback_plain_iters_mean": avg("fallback_plain_iters"),
+                "fixed_error": "bin std/mean within 1.05x of 8 plain iterations", "cases": rows}
+    finally:
+        dc.declutter_destroy(ctx)
+        dc.surrogate_destroy(sg)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -515,6 +590,9 @@ def main():
     ap.add_argument("--keep-order", action="store_true", help="iterate in the caller's sample order")
     ap.add_argument("--workload", default="gmm20_512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-batched", action="store_true", help="skip the scatterplot-matrix measurement")
+    ap.add_argument("--surrogate-budget", type=float, default=60.0,
+                    help="seconds of surrogate training before its comparison (0 skips it)")
+    ap.add_argument("--surrogate-pairs", type=int, default=1500)
     ap.add_argument("--ncu-run", action="store_true",
                     help="only warm-up and timed steps (for profiler captures); prints no bench line")
     args = ap.parse_args()

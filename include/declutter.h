@@ -168,6 +168,14 @@ dc_status advect_samples(dc_ctx *ctx, float *pos_xy, int64_t n);
  *   status; otherwise the call is asynchronous. */
 dc_status regularize(dc_ctx *ctx, float *pos_xy, int64_t n, int32_t iters, double *uniformity_out);
 
+/* regularize() that also moves n_tracers massless tracers (device
+ * float[2 n_tracers]) by each iteration's field without splatting them, e.g.
+ * the pixel nodes, whose final minus initial positions are the displacement
+ * field composed over the iterations (the deformed grid of Sec. 5).
+ * Asynchronous; not captured into a graph. */
+dc_status regularize_tracers(dc_ctx *ctx, float *pos_xy, int64_t n, float *tracer_xy, int64_t n_tracers,
+                             int32_t iters);
+
 /* regularize() on HOST samples: copies host float[2n] to a context-owned
  * device buffer, runs the iterations, copies the result back into the same
  * host array and synchronises.  Pinned host memory gives asynchronous
@@ -254,6 +262,57 @@ dc_status declutter_autotune_band_rows(const dc_params *params, int device, void
  * int32[n_panels] or NULL). */
 dc_status declutter_batch_autotune(dc_batch *batch, float *const *pos_xy, const int64_t *n, int32_t iters,
                                    int32_t *band_rows_out);
+
+/* ------------------------------------------------------------------------
+ * Learned surrogate (not in the paper): a convolutional encoder-decoder that
+ * maps a density grid to the displacement field composed over several plain
+ * iterations, trained on pairs the plain method generates.  BF16 weights and
+ * activations, FP32 accumulation on tensor cores (mma.sync BF16), FP32
+ * master weights and Adam.  Layers, in order: enc{l}a, enc{l}b for
+ * l = 0..L-1 (widths c_l = base_channels * 2^l), dec{l}up, dec{l}c for
+ * l = L-2..0, head (2 outputs); 3x3 convolutions with zero padding, ReLU
+ * after every layer but the head, 2x2 average pooling down, nearest
+ * upsampling and additive skips up.  Tensors are [batch][y][x][channel].
+ * ------------------------------------------------------------------------ */
+typedef struct dc_surrogate dc_surrogate;
+
+/* Input and output grids are 2^log2_res square; levels 1..6 with
+ * log2_res >= levels + 2; base_channels a multiple of 8 (<= 256); batches of
+ * at most max_batch; He-normal initial weights from seed. */
+dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channels, int32_t max_batch,
+                           uint64_t seed, int device, void *cuda_stream, dc_surrogate **out);
+dc_status surrogate_destroy(dc_surrogate *sg);
+
+/* Parameter counts in the unpadded layout used by get/set: for every layer
+ * in order, weights [out][3][3][in] (all layers' weights concatenated) and
+ * biases [out] (all layers' biases concatenated). */
+dc_status surrogate_num_params(const dc_surrogate *sg, int64_t *weights, int64_t *biases);
+dc_status surrogate_get_params(dc_surrogate *sg, float *w_host, float *b_host);
+/* Sets the FP32 master weights (BF16 copies follow) and resets Adam. */
+dc_status surrogate_set_params(dc_surrogate *sg, const float *w_host, const float *b_host);
+/* Weight and bias gradients of the last surrogate_loss_grad / train_step. */
+dc_status surrogate_get_grads(dc_surrogate *sg, float *gw_host, float *gb_host);
+
+/* density: device float[batch][H][W], multiplied on input by scales[b]
+ * (device float[batch], e.g. N^2 / n so that the even layout reads 1; NULL
+ * means 1); out: device float[batch][H][W][2] (pixels), or NULL. */
+dc_status surrogate_forward(dc_surrogate *sg, const float *density, const float *scales, int32_t batch,
+                            float *out);
+/* Forward + backward for 0.5 * mean((out - target)^2), target device
+ * float[batch][H][W][2]; *loss_out (host) after synchronising, if given. */
+dc_status surrogate_loss_grad(dc_surrogate *sg, const float *density, const float *scales, const float *target,
+                              int32_t batch, float *loss_out);
+/* surrogate_loss_grad followed by one Adam step (beta 0.9 / 0.999). */
+dc_status surrogate_train_step(dc_surrogate *sg, const float *density, const float *scales, const float *target,
+                               int32_t batch, float lr, float *loss_out);
+/* One-shot regularisation of device samples with the surrogate (context in
+ * float mode at the surrogate's resolution): predict the composed field from
+ * the samples' density, move every sample once by it, then run plain
+ * iterations while the Sec. 6.2 bin std / mean exceeds target_cv (at most
+ * max_plain_iters).  Returns the plain iterations used and the final ratio.
+ * Synchronises. */
+dc_status surrogate_apply(dc_ctx *ctx, dc_surrogate *sg, float *pos_xy, int64_t n, float target_cv,
+                          int32_t max_plain_iters, int32_t *plain_iters_out, double *cv_out);
 
 /* No-allocation variant of integral_images_u32(), for callers that cannot
  * allocate device memory when they need the result: code running while a

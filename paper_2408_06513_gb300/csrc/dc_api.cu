@@ -124,7 +124,7 @@ cudaError_t enqueue_inims(dc_ctx *c, cudaStream_t s, const BandArgs &a, int mode
 // own memset and splat.  With metrics, the quality of the counts after
 // iteration it goes to accumulator slot it.
 cudaError_t enqueue_iterations(dc_ctx *c, cudaStream_t s, float *pos, int64_t n, int iters, int metrics,
-                               Recorder &rec)
+                               Recorder &rec, float *tracers = nullptr, int64_t n_tracers = 0)
 {
     cudaError_t e = cudaSuccess;
     uint32_t *cb[2] = {c->counts_buf[0], c->counts_buf[1]};
@@ -177,6 +177,12 @@ cudaError_t enqueue_iterations(dc_ctx *c, cudaStream_t s, float *pos, int64_t n,
             e = launch_advect(s, reinterpret_cast<float2 *>(ipos), n, c->disp, c->g.log2N, c->p.pixel_center,
                               c->p.clamp_positions, need_next ? cb[nxt] : nullptr);
         if (e != cudaSuccess) return e;
+        if (n_tracers > 0) {
+            // massless tracers: moved by the same field, not splatted
+            e = launch_advect(s, reinterpret_cast<float2 *>(tracers), n_tracers, c->disp, c->g.log2N,
+                              c->p.pixel_center, c->p.clamp_positions, nullptr);
+            if (e != cudaSuccess) return e;
+        }
         if (metrics) {
             rec.count(K_QUALITY);
             e = launch_quality(s, cb[nxt], c->g.log2N, c->qacc + 3 * it);
@@ -628,6 +634,23 @@ dc_status regularize(dc_ctx *c, float *pos, int64_t n, int32_t iters, double *un
             uniformity_out[it] = m[0];
         }
     }
+    return DC_OK;
+}
+
+dc_status regularize_tracers(dc_ctx *c, float *pos, int64_t n, float *tracer_xy, int64_t n_tracers, int32_t iters)
+{
+    if (dc_status st = check_ctx(c)) return st;
+    if (dc_status st = check_samples(c, pos, n)) return st;
+    if (dc_status st = check_samples(c, tracer_xy, n_tracers)) return st;
+    if (iters < 0) return fail(DC_ERR_INVALID_ARG, "iters = %d", iters);
+    if (iters == 0) return DC_OK;
+    DeviceGuard guard(c->device);
+    if (dc_status st = ensure_sort_buffers(c, n)) return st;
+    Recorder rec;
+    DC_CUDA(enqueue_iterations(c, c->stream, pos, n, iters, 0, rec, tracer_xy, n_tracers));
+    c->n_last = n;
+    c->have_disp = true;
+    c->cur_counts = (iters - 1) & 1;
     return DC_OK;
 }
 

@@ -30,7 +30,9 @@ __all__ = [
     "declutter_status_string", "declutter_last_error", "DC_CARRY_COMPENSATED", "DC_CARRY_F64",
     "integral_images_u32_noalloc", "DC_NOALLOC_MAX_LOG2_RES", "Batch", "declutter_batch_create",
     "declutter_batch_destroy", "declutter_batch_regularize", "declutter_batch_sync",
-    "declutter_autotune_band_rows", "declutter_batch_autotune",
+    "declutter_autotune_band_rows", "declutter_batch_autotune", "regularize_tracers", "Surrogate",
+    "surrogate_create", "surrogate_destroy", "surrogate_num_params", "surrogate_get_params", "surrogate_set_params",
+    "surrogate_get_grads", "surrogate_forward", "surrogate_loss_grad", "surrogate_train_step", "surrogate_apply",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -105,6 +107,18 @@ _SIGS = [
     ("declutter_autotune_band_rows", ctypes.c_int,
      [ctypes.POINTER(dc_params), ctypes.c_int, _P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]),
     ("declutter_batch_autotune", ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P]),
+    ("regularize_tracers", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32]),
+    ("surrogate_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_uint64, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    ("surrogate_destroy", ctypes.c_int, [_P]),
+    ("surrogate_num_params", ctypes.c_int, [_P, _P, _P]),
+    ("surrogate_get_params", ctypes.c_int, [_P, _P, _P]),
+    ("surrogate_set_params", ctypes.c_int, [_P, _P, _P]),
+    ("surrogate_get_grads", ctypes.c_int, [_P, _P, _P]),
+    ("surrogate_forward", ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P]),
+    ("surrogate_loss_grad", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, _P]),
+    ("surrogate_train_step", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_float, _P]),
+    ("surrogate_apply", ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_int32, _P, _P]),
     ("declutter_kernel_name", ctypes.c_char_p, [ctypes.c_int32]),
     ("declutter_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("declutter_last_error", ctypes.c_char_p, []),
@@ -465,3 +479,128 @@ def declutter_batch_autotune(batch: Batch, positions, iters: int):
     _check(load_library().declutter_batch_autotune(batch.handle, ptrs, ns, int(iters), out),
            "declutter_batch_autotune")
     return list(out)
+
+
+def regularize_tracers(ctx: Context, pos, tracers, iters: int) -> None:
+    """``regularize`` that also moves ``tracers`` (CUDA float32 [m, 2]) by each
+    iteration's field without splatting them."""
+    pp, n = _pos_args(pos)
+    tp, nt = _pos_args(tracers)
+    _check(load_library().regularize_tracers(ctx.handle, pp, n, tp, nt, int(iters)), "regularize_tracers")
+
+
+@dataclass
+class Surrogate:
+    """Owner of a ``dc_surrogate*``."""
+    handle: ctypes.c_void_p
+    log2_res: int
+    levels: int
+    base_channels: int
+    max_batch: int
+    device: int
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        surrogate_destroy(self)
+
+
+def surrogate_create(log2_res: int, levels: int = 4, base_channels: int = 32, max_batch: int = 16, seed: int = 0,
+                     device: int | None = None, stream=None) -> Surrogate:
+    import torch
+    if device is None:
+        device = torch.cuda.current_device()
+    h = ctypes.c_void_p()
+    _check(load_library().surrogate_create(int(log2_res), int(levels), int(base_channels), int(max_batch), int(seed),
+                                           int(device), _stream_ptr(stream, device), ctypes.byref(h)),
+           "surrogate_create")
+    return Surrogate(h, int(log2_res), int(levels), int(base_channels), int(max_batch), int(device))
+
+
+def surrogate_destroy(sg: Surrogate) -> None:
+    if sg.handle:
+        _check(load_library().surrogate_destroy(sg.handle), "surrogate_destroy")
+        sg.handle = ctypes.c_void_p()
+
+
+def surrogate_num_params(sg: Surrogate):
+    nw, nb = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().surrogate_num_params(sg.handle, ctypes.byref(nw), ctypes.byref(nb)), "surrogate_num_params")
+    return int(nw.value), int(nb.value)
+
+
+def surrogate_get_params(sg: Surrogate):
+    nw, nb = surrogate_num_params(sg)
+    w = np.empty(nw, np.float32)
+    b = np.empty(nb, np.float32)
+    _check(load_library().surrogate_get_params(sg.handle, w.ctypes.data, b.ctypes.data), "surrogate_get_params")
+    return w, b
+
+
+def surrogate_set_params(sg: Surrogate, w, b) -> None:
+    w = np.ascontiguousarray(w, np.float32)
+    b = np.ascontiguousarray(b, np.float32)
+    nw, nb = surrogate_num_params(sg)
+    if w.size != nw or b.size != nb:
+        raise ValueError("parameter sizes")
+    _check(load_library().surrogate_set_params(sg.handle, w.ctypes.data, b.ctypes.data), "surrogate_set_params")
+
+
+def surrogate_get_grads(sg: Surrogate):
+    nw, nb = surrogate_num_params(sg)
+    w = np.empty(nw, np.float32)
+    b = np.empty(nb, np.float32)
+    _check(load_library().surrogate_get_grads(sg.handle, w.ctypes.data, b.ctypes.data), "surrogate_get_grads")
+    return w, b
+
+
+def _grid_arg(t, batch, H, ch, name):
+    import torch
+    return _ptr(t, torch.float32, batch * H * H * ch, name)
+
+
+def _scales_arg(scales, batch):
+    import torch
+    if scales is None:
+        return None
+    return _ptr(scales, torch.float32, batch, "scales")
+
+
+def surrogate_forward(sg: Surrogate, density, scales=None, out=None) -> None:
+    """``density``: CUDA float32 [B, H, W]; ``scales``: CUDA float32 [B] or None."""
+    B = density.shape[0]
+    H = 1 << sg.log2_res
+    _check(load_library().surrogate_forward(sg.handle, _grid_arg(density, B, H, 1, "density"), _scales_arg(scales, B),
+                                            B, _grid_arg(out, B, H, 2, "out") if out is not None else None),
+           "surrogate_forward")
+
+
+def surrogate_loss_grad(sg: Surrogate, density, scales, target) -> float:
+    B = density.shape[0]
+    H = 1 << sg.log2_res
+    loss = ctypes.c_float()
+    _check(load_library().surrogate_loss_grad(sg.handle, _grid_arg(density, B, H, 1, "density"),
+                                              _scales_arg(scales, B), _grid_arg(target, B, H, 2, "target"), B,
+                                              ctypes.byref(loss)), "surrogate_loss_grad")
+    return float(loss.value)
+
+
+def surrogate_train_step(sg: Surrogate, density, scales, target, lr: float, want_loss: bool = True):
+    B = density.shape[0]
+    H = 1 << sg.log2_res
+    loss = ctypes.c_float()
+    _check(load_library().surrogate_train_step(sg.handle, _grid_arg(density, B, H, 1, "density"),
+                                               _scales_arg(scales, B), _grid_arg(target, B, H, 2, "target"), B,
+                                               float(lr), ctypes.byref(loss) if want_loss else None),
+           "surrogate_train_step")
+    return float(loss.value) if want_loss else None
+
+
+def surrogate_apply(ctx: Context, sg: Surrogate, pos, target_cv: float, max_plain_iters: int):
+    pp, n = _pos_args(pos)
+    used = ctypes.c_int32()
+    cv = ctypes.c_double()
+    _check(load_library().surrogate_apply(ctx.handle, sg.handle, pp, n, float(target_cv), int(max_plain_iters),
+                                          ctypes.byref(used), ctypes.byref(cv)), "surrogate_apply")
+    return int(used.value), float(cv.value)

@@ -1,0 +1,145 @@
+"""The surrogate network's forward and backward passes on the GPU (BF16 tensor
+cores, FP32 accumulation) against the FP64 network oracle on the same
+bfloat16-rounded tensors, at small shapes.  Bounds: the output within 2 % of
+its largest magnitude; every layer's gradients within 1 % relative RMS and
+their largest error within 2 % of the largest gradient, or within twice the
+oracle's own bfloat16-versus-FP64 difference when that is larger (two
+bfloat16 pipelines that sum in different orders can flip a rounding, each
+sits that far from the exact gradient, and the deepest layers of the 4-level
+network sit at that noise floor).  Then a short
+training run on pairs generated by the plain method shows what the network
+gains."""
+
+import numpy as np
+import pytest
+
+from oracle import surrogate as S
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu]
+
+
+@pytest.fixture(scope="module")
+def dc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_06513_gb300 import build as dc_build
+    dc_build.build()
+    from paper_2408_06513_gb300 import declutter
+    declutter.load_library()
+    return declutter
+
+
+def flat_params(P, levels, c0):
+    ws, bs = [], []
+    for name, co, ci in S.layer_shapes(levels, c0):
+        ws.append(P[name + ".w"].reshape(-1))
+        bs.append(P[name + ".b"].reshape(-1))
+    return np.concatenate(ws), np.concatenate(bs)
+
+
+def split_params(w, b, levels, c0):
+    out = {}
+    ow = ob = 0
+    for name, co, ci in S.layer_shapes(levels, c0):
+        n = co * 9 * ci
+        out[name + ".w"] = w[ow:ow + n].reshape(co, 3, 3, ci)
+        out[name + ".b"] = b[ob:ob + co]
+        ow += n
+        ob += co
+    return out
+
+
+@pytest.mark.parametrize("levels,c0,log2,batch", [(2, 8, 4, 2), (3, 8, 5, 2), (2, 16, 4, 3), (4, 32, 6, 1)])
+def test_forward_and_gradients_match_oracle(dc, levels, c0, log2, batch):
+    H = 1 << log2
+    rng = np.random.default_rng(levels * 10 + c0)
+    P = S.init_params(levels, c0, seed=levels + c0)
+    for k in P:
+        if k.endswith(".b"):
+            P[k] = rng.normal(0, 0.05, size=P[k].shape)
+    x = rng.random((batch, H, H)) * 3.0
+    t = rng.normal(size=(batch, H, H, 2))
+    sg = dc.surrogate_create(log2, levels, c0, max_batch=batch, seed=0)
+    try:
+        w, b = flat_params(P, levels, c0)
+        dc.surrogate_set_params(sg, w, b)
+        w2, b2 = dc.surrogate_get_params(sg)
+        assert np.array_equal(w2, w.astype(np.float32)) and np.array_equal(b2, b.astype(np.float32))
+        xd = torch.from_numpy(x.astype(np.float32)).cuda()
+        td = torch.from_numpy(t.astype(np.float32)).cuda()
+        out = torch.empty(batch, H, H, 2, device="cuda")
+        dc.surrogate_forward(sg, xd, None, out)
+        loss = dc.surrogate_loss_grad(sg, xd, None, td)
+        gw, gb = dc.surrogate_get_grads(sg)
+    finally:
+        dc.surrogate_destroy(sg)
+    Pf = {k: v.astype(np.float32).astype(np.float64) for k, v in P.items()}
+    x64 = x.astype(np.float32).astype(np.float64)[..., None]
+    t64 = t.astype(np.float32).astype(np.float64)
+    ref_out, cache = S.forward(Pf, x64, levels)
+    ref_loss, dout = S.mse_loss(ref_out, t64)
+    G = S.backward(cache, dout, levels)
+    # the size of bfloat16 rounding noise itself: the oracle with and without it
+    out64, cache64 = S.forward(Pf, x64, levels, round_bf16=False)
+    G64 = S.backward(cache64, S.mse_loss(out64, t64)[1], levels, round_bf16=False)
+    o = out.cpu().numpy().astype(np.float64)
+    scale = np.max(np.abs(ref_out))
+    # both sides round the same tensors to bfloat16; FP32 vs FP64 sums can flip
+    # a rounding decision, and ten layers of such flips stay within 2 %
+    assert np.max(np.abs(o - ref_out)) <= 2e-2 * scale, (np.max(np.abs(o - ref_out)), scale)
+    assert abs(loss - ref_loss) <= 2e-2 * abs(ref_loss)
+    g = split_params(gw.astype(np.float64), gb.astype(np.float64), levels, c0)
+    for name, _, _ in S.layer_shapes(levels, c0):
+        for kind in (".w", ".b"):
+            ref = G[name + kind]
+            got = g[name + kind]
+            m = np.max(np.abs(ref))
+            err = np.max(np.abs(got - ref))
+            noise = np.max(np.abs(G64[name + kind] - ref))
+            den = max(np.sum(ref ** 2), 1e-300)
+            rel_rms = np.sqrt(np.sum((got - ref) ** 2) / den)
+            noise_rms = np.sqrt(np.sum((G64[name + kind] - ref) ** 2) / den)
+            # |got - ref| <= |got - exact| + |exact - ref|: when the GPU's own
+            # bfloat16 noise is as large as the oracle's, the bound is twice it
+            assert rel_rms <= max(1e-2, 2.0 * noise_rms), (name + kind, rel_rms, noise_rms)
+            assert err <= max(2e-2 * m, 2.0 * noise) + 1e-9, (name + kind, err, m, noise)
+
+
+def test_training_gains_over_untrained_and_over_no_iteration(dc):
+    """Train the 4-level network briefly at 128^2 on pairs from the plain
+    method, then: the loss falls, the predicted composed field beats the
+    untrained one on held-out mixtures, and one surrogate pass is worth at
+    least one plain iteration of uniformity (Sec. 6.2 bin std / mean)."""
+    import math
+    from paper_2408_06513_gb300 import surrogate as SG
+    rng = np.random.default_rng(7)
+    gen = SG.PairGenerator(log2_res=7, iters=4, kernel_r=2)
+    try:
+        dens, scales, target = gen.make(160, rng, n_range=(20_000, 300_000))
+        held = gen.make(16, np.random.default_rng(70), n_range=(20_000, 300_000))
+    finally:
+        gen.close()
+    sg = dc.surrogate_create(7, 4, 32, max_batch=8, seed=3)
+    ctx = dc.declutter_create(7, kernel_r=2)
+    try:
+        before = SG.field_error(sg, *held)
+        losses = SG.train(sg, dens, scales, target, steps=400, batch=8, lr=2e-3, rng=rng, log_every=50)
+        after = SG.field_error(sg, *held)
+        assert losses[-1][1] < 0.6 * losses[0][1], losses
+        assert after["rms_px"] < 0.85 * before["rms_px"], (before, after)
+        worth = []
+        for t in range(3):
+            r2 = np.random.default_rng(900 + t)
+            z = SG.gmm_samples(200_000, int(r2.integers(2, 12)), r2, 0)
+            mean = 200_000 / (128 // 4) ** 2
+            u = dc.regularize(ctx, z.clone(), 4, uniformity=True)
+            cv_plain = [x / mean for x in u]
+            used, cv = dc.surrogate_apply(ctx, sg, z.clone(), 0.0, 0)
+            assert used == 0
+            worth.append(sum(1 for c in cv_plain if c >= cv))
+        print("surrogate pass worth (plain iterations):", worth, "field rms px:", before, after)
+        assert min(worth) >= 1, worth
+    finally:
+        dc.declutter_destroy(ctx)
+        dc.surrogate_destroy(sg)
