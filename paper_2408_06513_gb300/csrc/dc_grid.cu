@@ -43,7 +43,7 @@ BandGeom make_band_geom(int log2N, int band_rows)
     g.CPT = g.N >= 128 ? (g.N / 512 > 4 ? g.N / 512 : 4) : 1;
     g.NT = g.N / g.CPT;
     if (g.NT < 32) g.NT = 32;
-    g.agg_stride = (3 * g.N + 2 * T + 1 + 3) & ~3;
+    g.agg_stride = (3 * g.N + 2 * T + 2 + 3) & ~3;  // + the 64-bit-band flag
     g.lanes = 5 * g.N;
     return g;
 }
@@ -208,6 +208,9 @@ __device__ __forceinline__ float exact_component(long long A1, long long A0, int
     return (float)((neg ? -dm : dm) * inv_den);
 }
 
+__device__ __forceinline__ unsigned bits32(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ unsigned bits32(uint32_t x) { return x; }
+
 template <typename T, int CPT>
 __device__ __forceinline__ void store_row(T *dst, const T (&v)[CPT], int c0, int N)
 {
@@ -216,16 +219,13 @@ __device__ __forceinline__ void store_row(T *dst, const T (&v)[CPT], int c0, int
 #pragma unroll
         for (int q = 0; q < CPT / per; ++q) {
             if constexpr (sizeof(T) == 4) {
-                float4 f;
-                f.x = __int_as_float(*(const int *)&v[per * q]);
-                f.y = __int_as_float(*(const int *)&v[per * q + 1]);
-                f.z = __int_as_float(*(const int *)&v[per * q + 2]);
-                f.w = __int_as_float(*(const int *)&v[per * q + 3]);
-                *reinterpret_cast<float4 *>(dst + c0 + per * q) = f;
+                const uint4 f = make_uint4(bits32(v[per * q]), bits32(v[per * q + 1]), bits32(v[per * q + 2]),
+                                           bits32(v[per * q + 3]));
+                *reinterpret_cast<uint4 *>(dst + c0 + per * q) = f;
             } else {
                 ulonglong2 f;
-                f.x = *(const unsigned long long *)&v[per * q];
-                f.y = *(const unsigned long long *)&v[per * q + 1];
+                f.x = (unsigned long long)v[per * q];
+                f.y = (unsigned long long)v[per * q + 1];
                 *reinterpret_cast<ulonglong2 *>(dst + c0 + per * q) = f;
             }
         }
@@ -236,10 +236,14 @@ __device__ __forceinline__ void store_row(T *dst, const T (&v)[CPT], int c0, int
     }
 }
 
-// One band per CTA.  FINAL = false: write the band's compact aggregate.
-// FINAL = true: combine with the carries and evaluate the outputs.
+// One band per CTA, thread t owning the CPT contiguous columns
+// [t CPT, t CPT + CPT), state in MODE's accumulator type (uint64 for
+// MODE_GRID64).  Used for grids below 128 x 128 and, for MODE_GRID64, for
+// bands whose sums may reach 2^32 (the interleaved kernels below keep
+// band-local sums in 32 bits).  FINAL = false: write the band's compact
+// aggregate.  FINAL = true: combine with the carries and evaluate the outputs.
 template <int MODE, int CPT, bool FINAL>
-__global__ void __launch_bounds__(CPT == 1 ? 64 : 512) band_kernel(BandArgs a, int log2N, int T)
+__device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
 {
     using Acc = typename ModeT<MODE>::Acc;
     const int N = 1 << log2N;
@@ -480,6 +484,420 @@ __global__ void __launch_bounds__(CPT == 1 ? 64 : 512) band_kernel(BandArgs a, i
     }
 }
 
+template <int MODE, int CPT, bool FINAL>
+__global__ void __launch_bounds__(CPT == 1 ? 64 : 512) band_kernel(BandArgs a, int log2N, int T)
+{
+    band_body<MODE, CPT, FINAL>(a, log2N, T);
+}
+
+// out-of-line copy for the 64-bit fallback of the interleaved kernels
+template <int MODE, int CPT, bool FINAL>
+__device__ __noinline__ void band_body_wide(BandArgs a, int log2N, int T)
+{
+    band_body<MODE, CPT, FINAL>(a, log2N, T);
+}
+
+// ------------------------------------------------------------------------
+// Band kernels for N >= 128, interleaved column layout.
+//
+// Thread t of NT = min(512, N / 4) owns G = N / (4 NT) chunks of four
+// columns: chunk q covers columns 4 (q NT + t) .. 4 (q NT + t) + 3, so the
+// 32 lanes of a warp load and store one chunk's row segment as one
+// contiguous run (128- or 256-bit accesses).  The row prefix is a scan of G
+// values per thread (one warp scan each, one block barrier per row).
+// Rows are prefetched PD rows ahead into registers.
+//
+// The final pass stages, once per band, every carry and marginal lane the
+// band touches into shared memory: the vertical lines [0, N) and the
+// anti-diagonal / diagonal windows of N + T - 1 lines.  A window element
+// i sits at (i & 3) * L4 + (i >> 2), so that the 32 lanes reading one
+// (chunk, column) slot at any row shift hit 32 consecutive words.
+//
+// MODE_GRID64 keeps its band-local sums in 32 bits: every band-local
+// quantity (row prefix, vertical, anti-diagonal and diagonal sums) is at
+// most the band total, which is below 2^32 whenever max(grid) T N < 2^32.
+// The aggregate pass checks that bound per band and runs the 64-bit body
+// for a band that fails it, flagging it in its aggregate record; the final
+// pass sends flagged bands to the 64-bit body too.  Carries are 64-bit.
+// ------------------------------------------------------------------------
+template <int MODE> struct Band2T;
+template <> struct Band2T<MODE_COUNT> { using S = uint32_t; using C = uint32_t; };
+template <> struct Band2T<MODE_FLOAT> { using S = float; using C = float; };
+template <> struct Band2T<MODE_GRID64> { using S = uint32_t; using C = unsigned long long; };
+
+__device__ __forceinline__ int wpos(int i, int L4) { return (i & 3) * L4 + (i >> 2); }
+
+__device__ __forceinline__ uint4 ld_stream_v4(const void *p)
+{
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+__device__ __forceinline__ void st_v4_u64(void *p, unsigned long long a, unsigned long long b, unsigned long long c,
+                                          unsigned long long d)
+{
+    asm volatile("st.global.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
+}
+__device__ __forceinline__ void st_v8_f32(void *p, const float (&v)[8])
+{
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+                 "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+}
+// four consecutive uint64 at p (16-byte aligned; one 256-bit store when
+// 32-byte aligned)
+__device__ __forceinline__ void store4_u64(unsigned long long *p, unsigned long long a, unsigned long long b,
+                                           unsigned long long c, unsigned long long d, bool al32)
+{
+    if (al32) {
+        st_v4_u64(p, a, b, c, d);
+    } else {
+        reinterpret_cast<ulonglong2 *>(p)[0] = make_ulonglong2(a, b);
+        reinterpret_cast<ulonglong2 *>(p)[1] = make_ulonglong2(c, d);
+    }
+}
+
+template <int MODE, int G, bool FINAL>
+__global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T)
+{
+    using S = typename Band2T<MODE>::S;
+    using C = typename Band2T<MODE>::C;
+    constexpr int PD = G >= 4 ? 1 : 2;  // rows prefetched ahead
+    const int N = 1 << log2N;
+    const int NT = blockDim.x, nw = NT >> 5;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int b = blockIdx.x;
+    const int j0 = b * T;
+    const int lanes = 5 * N;
+
+    __shared__ S s_wt[2][G][16];
+    __shared__ S s_uf[2][G][16];
+    __shared__ S s_vl[2][G][16];
+    __shared__ S s_U0[64], s_VN[64], s_RT[64];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+
+    pdl_wait();
+    if constexpr (MODE == MODE_GRID64 && FINAL) {
+        const unsigned long long *ag = static_cast<const unsigned long long *>(a.agg) + (size_t)b * a.agg_stride;
+        if (ag[3 * N + 2 * T + 1]) {
+            band_body_wide<MODE_GRID64, 4 * G, true>(a, log2N, T);
+            return;
+        }
+    }
+
+    // ---- final pass: stage the band's carry and marginal windows
+    const int L4a = ((((N + 3) >> 2) + 23) >> 5 << 5) + 8;
+    const int L4w = ((((N + T - 1 + 3) >> 2) + 23) >> 5 << 5) + 8;
+    C *sA = nullptr, *sU = nullptr, *sV = nullptr, *sR = nullptr, *sAm = nullptr, *sBm = nullptr;
+    C Ctot = C(0), CVbN = C(0);
+    float kappa = 0.f, scale = 0.f;
+    if constexpr (FINAL) {
+        C *p = reinterpret_cast<C *>(s_dyn);
+        sA = p; p += 4 * L4a;
+        sU = p; p += 4 * L4w;
+        sV = p; p += 4 * L4w;
+        if constexpr (MODE != MODE_GRID64) {
+            sR = p; p += 4 * L4a;
+            sAm = p; p += 4 * L4w;
+            sBm = p;
+        }
+        const C *cb = static_cast<const C *>(a.carry) + (size_t)b * lanes;
+        const C *ce = static_cast<const C *>(a.carry) + (size_t)(N / T) * lanes;
+        const int ubase = N + j0;              // lane of window element 0: u = j0
+        const int vbase = 3 * N + N - j0 - T;  // lane of window element 0: v = -(j0 + T - 1)
+        for (int i = t; i < N; i += NT) {
+            sA[wpos(i, L4a)] = cb[i];
+            if constexpr (MODE != MODE_GRID64) sR[wpos(i, L4a)] = ce[i];
+        }
+        for (int i = t; i < N + T - 1; i += NT) {
+            sU[wpos(i, L4w)] = cb[ubase + i];
+            sV[wpos(i, L4w)] = cb[vbase + i];
+            if constexpr (MODE != MODE_GRID64) {
+                sAm[wpos(i, L4w)] = ce[ubase + i];
+                sBm[wpos(i, L4w)] = ce[vbase + i];
+            }
+        }
+        Ctot = ce[N - 1];
+        CVbN = cb[N - 1];
+        if constexpr (MODE == MODE_FLOAT) {
+            const float NN = (float)N * (float)N;
+            kappa = Ctot / NN;
+            const float Sg = a.pixel_center ? 2.0f * N : (float)N;
+            const float Call = Ctot + a.mu * NN + a.d0 * NN;
+            scale = Call > 0.0f ? 1.0f / (2.0f * Sg * Call) : 0.0f;
+        }
+        // the first row's barrier orders these writes before any read
+    }
+
+    S arun[G][4], Uo[G][4], Vo[G][4];
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { arun[q][e] = S(0); Uo[q][e] = S(0); Vo[q][e] = S(0); }
+    S RTcum = S(0);
+    uint32_t vmax = 0u;
+
+    const unsigned char *src = static_cast<const unsigned char *>(a.src);
+    auto load = [&](int j, uint4 (&dst)[G]) {
+#pragma unroll
+        for (int q = 0; q < G; ++q)
+            dst[q] = ld_stream_v4(src + 4 * (((size_t)j << log2N) + 4 * (q * NT + t)));
+    };
+    uint4 buf[PD][G];
+#pragma unroll
+    for (int d = 0; d < PD; ++d)
+        if (d < T) load(j0 + d, buf[d]);
+
+    const bool out32 = ((reinterpret_cast<uintptr_t>(a.alpha_out) | reinterpret_cast<uintptr_t>(a.alpha_t_out)) & 31) == 0;
+
+    for (int r = 0; r < T; ++r) {
+        const int j = j0 + r;
+        const int par = r & 1;
+        uint4 cur[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) cur[q] = buf[0][q];
+#pragma unroll
+        for (int d = 0; d + 1 < PD; ++d)
+#pragma unroll
+            for (int q = 0; q < G; ++q) buf[d][q] = buf[d + 1][q];
+        if (r + PD < T) load(j + PD, buf[PD - 1]);
+
+        if constexpr (!FINAL) {
+            if (a.zero_out) {
+#pragma unroll
+                for (int q = 0; q < G; ++q)
+                    *reinterpret_cast<uint4 *>(a.zero_out + ((size_t)j << log2N) + 4 * (q * NT + t)) =
+                        make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+
+        // row values and the in-chunk prefix
+        S p[G][4];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const uint32_t x[4] = {cur[q].x, cur[q].y, cur[q].z, cur[q].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if constexpr (MODE == MODE_FLOAT) p[q][e] = __uint_as_float(x[e]) - a.mu;
+                else p[q][e] = x[e];
+                if constexpr (MODE == MODE_GRID64 && !FINAL) vmax = max(vmax, x[e]);
+            }
+#pragma unroll
+            for (int e = 1; e < 4; ++e) p[q][e] = p[q][e] + p[q][e - 1];
+        }
+
+        // neighbour state of the previous row (before this row's barrier)
+        S u_next[G], v_prev[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            u_next[q] = __shfl_down_sync(kFull, Uo[q][0], 1);
+            v_prev[q] = __shfl_up_sync(kFull, Vo[q][3], 1);
+            if (lane == 0) s_uf[par][q][warp] = Uo[q][0];
+            if (lane == 31) s_vl[par][q][warp] = Vo[q][3];
+        }
+
+        // warp scans of the chunk sums
+        S incl[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            S x = p[q][3];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const S y = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x = x + y;
+            }
+            incl[q] = x;
+            if (lane == 31) s_wt[par][q][warp] = x;
+        }
+        __syncthreads();
+
+        // scan over warps, then over chunk groups
+        S off[G];
+        S gp = S(0);
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            S wv = lane < nw ? s_wt[par][q][lane] : S(0);
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                const S y = __shfl_up_sync(kFull, wv, o);
+                if (lane >= o) wv = wv + y;
+            }
+            const S wex = __shfl_sync(kFull, wv, (warp + 31) & 31);
+            const S tot = __shfl_sync(kFull, wv, nw - 1);
+            off[q] = gp + (warp > 0 ? wex : S(0)) + (incl[q] - p[q][3]);
+            gp = gp + tot;
+        }
+        const S total = gp;
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) p[q][e] = p[q][e] + off[q];
+            if (lane == 31) u_next[q] = warp + 1 < nw ? s_uf[par][q][warp + 1] : (q + 1 < G ? s_uf[par][q + 1][0] : S(0));
+            if (lane == 0) v_prev[q] = warp > 0 ? s_vl[par][q][warp - 1] : (q > 0 ? s_vl[par][q - 1][nw - 1] : S(0));
+        }
+
+        // the three recurrences, in place: U ascending, V descending
+        const S RTprev = RTcum;
+        RTcum = RTcum + total;
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int cq = 4 * (q * NT + t);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                S ur = e < 3 ? Uo[q][e + 1] : u_next[q];
+                if (cq + e == N - 1) ur = RTprev;  // U(N, j-1): row totals only
+                Uo[q][e] = ur + p[q][e];
+                arun[q][e] = arun[q][e] + p[q][e];
+            }
+#pragma unroll
+            for (int e = 3; e >= 0; --e) {
+                S vl = e > 0 ? Vo[q][e - 1] : v_prev[q];
+                if (cq + e == 0) vl = S(0);       // V(-1, j-1) = 0
+                const S pm1 = e > 0 ? p[q][e - 1] : off[q];  // P(j, c-1)
+                Vo[q][e] = vl + pm1;
+            }
+        }
+
+        if constexpr (!FINAL) {
+            if (t == 0) {
+                s_U0[r] = Uo[0][0];
+                s_RT[r] = total;
+            }
+            if (t == NT - 1) s_VN[r] = Vo[G - 1][3];
+        } else {
+            const size_t rowoff = (size_t)j << log2N;
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const int cq = 4 * (q * NT + t);
+                if constexpr (MODE == MODE_GRID64) {
+                    unsigned long long oal[4], oat[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = cq + e;
+                        oal[e] = sA[wpos(c, L4a)] + (unsigned long long)arun[q][e];
+                        oat[e] = (sU[wpos(c + r, L4w)] + (unsigned long long)Uo[q][e]) -
+                                 (sV[wpos(c - r + T - 1, L4w)] + (unsigned long long)Vo[q][e]);
+                    }
+                    if (a.alpha_out)
+                        store4_u64(static_cast<unsigned long long *>(a.alpha_out) + rowoff + cq, oal[0], oal[1],
+                                   oal[2], oal[3], out32);
+                    if (a.alpha_t_out)
+                        store4_u64(static_cast<unsigned long long *>(a.alpha_t_out) + rowoff + cq, oat[0], oat[1],
+                                   oat[2], oat[3], out32);
+                } else {
+                    const C Ccj = CVbN + RTcum;
+                    float dxy[8];
+                    C oal[4], oat[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = cq + e;
+                        const int iu = wpos(c + r, L4w), iv = wpos(c - r + T - 1, L4w);
+                        const C al = sA[wpos(c, L4a)] + arun[q][e];
+                        const C at = (sU[iu] + Uo[q][e]) - (sV[iv] + Vo[q][e]);
+                        const C A = sAm[iu];
+                        const C Bv = Ctot - sBm[iv];
+                        const C R = sR[wpos(c, L4a)];
+                        C w[8];
+                        w[0] = al;
+                        w[1] = R - al;
+                        w[2] = Ctot - R - Ccj + al;
+                        w[3] = Ccj - al;
+                        w[4] = at;
+                        w[5] = A - at;
+                        w[6] = Ctot - A - Bv + at;
+                        w[7] = Bv - at;
+                        oal[e] = al;
+                        oat[e] = at;
+                        const int Sg = a.pixel_center ? 2 * N : N;
+                        const int ai = a.pixel_center ? 2 * c + 1 : c;
+                        const int bj = a.pixel_center ? 2 * j + 1 : j;
+                        int qx[8], qy[8], w0[8];
+                        anchors(ai, bj, Sg, qx, qy);
+                        lattice_counts(c, j, N, w0);
+                        if constexpr (MODE == MODE_FLOAT) {
+                            float nx = 0.f, ny = 0.f, nx0 = 0.f, ny0 = 0.f;
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                nx = fmaf(w[k], (float)qx[k], nx);
+                                ny = fmaf(w[k], (float)qy[k], ny);
+                                nx0 = fmaf((float)w0[k], (float)qx[k], nx0);
+                                ny0 = fmaf((float)w0[k], (float)qy[k], ny0);
+                            }
+                            dxy[2 * e] = fmaf(-kappa, nx0, nx) * scale;
+                            dxy[2 * e + 1] = fmaf(-kappa, ny0, ny) * scale;
+                            oal[e] = al + a.mu * (float)w0[0];
+                            oat[e] = at + a.mu * (float)w0[4];
+                        } else {
+                            long long A1x = 0, A1y = 0, A0x = 0, A0y = 0;
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const long long wq = (long long)(uint32_t)w[k];
+                                A1x += wq * qx[k];
+                                A1y += wq * qy[k];
+                                A0x += (long long)w0[k] * qx[k];
+                                A0y += (long long)w0[k] * qy[k];
+                            }
+                            const long long Cn = (long long)(uint32_t)Ctot;
+                            dxy[2 * e] = exact_component(A1x, A0x, 2 * log2N, Cn, a.inv_den_exact);
+                            dxy[2 * e + 1] = exact_component(A1y, A0y, 2 * log2N, Cn, a.inv_den_exact);
+                        }
+                    }
+                    if (a.disp) st_v8_f32(reinterpret_cast<float *>(a.disp) + 2 * (rowoff + cq), dxy);
+                    if constexpr (MODE == MODE_FLOAT) {
+                        if (a.alpha_out)
+                            *reinterpret_cast<float4 *>(static_cast<float *>(a.alpha_out) + rowoff + cq) =
+                                make_float4(oal[0], oal[1], oal[2], oal[3]);
+                        if (a.alpha_t_out)
+                            *reinterpret_cast<float4 *>(static_cast<float *>(a.alpha_t_out) + rowoff + cq) =
+                                make_float4(oat[0], oat[1], oat[2], oat[3]);
+                    } else {
+                        if (a.alpha_out)
+                            store4_u64(static_cast<unsigned long long *>(a.alpha_out) + rowoff + cq, oal[0], oal[1],
+                                       oal[2], oal[3], out32);
+                        if (a.alpha_t_out)
+                            store4_u64(static_cast<unsigned long long *>(a.alpha_t_out) + rowoff + cq, oat[0], oat[1],
+                                       oat[2], oat[3], out32);
+                    }
+                }
+            }
+        }
+    }
+
+    if constexpr (!FINAL) {
+        // compact aggregate [alpha N][U N][V N][U0 T][E T][S][flag], as in band_body
+        __syncthreads();
+        C *ag = static_cast<C *>(a.agg) + (size_t)b * a.agg_stride;
+        if constexpr (MODE == MODE_GRID64) {
+            const uint32_t lim = 0xffffffffu / (uint32_t)(T << log2N);
+            if (__syncthreads_or(vmax > lim)) {
+                band_body_wide<MODE_GRID64, 4 * G, false>(a, log2N, T);
+                if (t == 0) ag[3 * N + 2 * T + 1] = 1ull;
+                return;
+            }
+            if (t == 0) ag[3 * N + 2 * T + 1] = 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int cq = 4 * (q * NT + t);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                ag[cq + e] = C(arun[q][e]);
+                ag[N + cq + e] = C(Uo[q][e]);
+                ag[2 * N + cq + e] = C(Vo[q][e]);
+            }
+        }
+        for (int rr = t; rr < T; rr += NT) {
+            S below = S(0);
+            for (int q = rr + 1; q < T; ++q) below = below + s_RT[q];
+            ag[3 * N + rr] = C(s_U0[rr]);
+            ag[3 * N + T + rr] = C(s_VN[rr] + below);
+        }
+        if (t == 0) ag[3 * N + 2 * T] = C(RTcum);
+    }
+}
+
 // ------------------------------------------------------------------------
 // Carries: exclusive scan over bands of every absolute line.
 // Lanes [0, N): vertical line i.  [N, 3N): anti-diagonal u = lane - N.
@@ -590,10 +1008,38 @@ int smooth_smem_bytes(int r)
     return (W * W + TW * W) * (int)sizeof(float);
 }
 
+// dynamic shared memory of the interleaved final kernel: the carry windows
+// (and, outside MODE_GRID64, the marginal windows)
+static size_t band2_smem_bytes(int mode, int N, int T)
+{
+    auto l4 = [](int len) { return ((((len + 3) >> 2) + 23) >> 5 << 5) + 8; };
+    const size_t per = 4 * (size_t)l4(N) + 8 * (size_t)l4(N + T - 1);
+    return mode == MODE_GRID64 ? per * 8 : 2 * per * 4;
+}
+
+template <int MODE, int G>
+static cudaError_t allow_band2_smem()
+{
+    // largest grid of each G: N = 2048 G (G = 1: up to 2048), band height <= 64
+    return cudaFuncSetAttribute(band2_kernel<MODE, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)band2_smem_bytes(MODE, 2048 * G, 64));
+}
+
 cudaError_t prepare_kernels()
 {
     // dynamic shared memory of the smoothing tile for the largest radius
-    return cudaFuncSetAttribute(smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smooth_smem_bytes(64));
+    cudaError_t e = cudaFuncSetAttribute(smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smooth_smem_bytes(64));
+    if (e == cudaSuccess) e = allow_band2_smem<MODE_COUNT, 1>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE_COUNT, 2>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE_COUNT, 4>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE_FLOAT, 1>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE_FLOAT, 2>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE_FLOAT, 4>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE_GRID64, 1>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE_GRID64, 2>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE_GRID64, 4>();
+    return e;
 }
 
 cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, int log2N, const GaussW &w,
@@ -606,9 +1052,24 @@ cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, i
     return launch_kernel(smooth_kernel, grid, dim3(256), (size_t)bytes, s, counts, dens, log2N, w, zero_out);
 }
 
+template <int MODE, bool FINAL, int G>
+static cudaError_t launch_band2(cudaStream_t s, const BandGeom &g, const BandArgs &a)
+{
+    const size_t smem = FINAL ? band2_smem_bytes(MODE, g.N, g.T) : 0;
+    return launch_kernel(band2_kernel<MODE, G, FINAL>, dim3(g.nb), dim3(g.NT), smem, s, a, g.log2N, g.T);
+}
+
 template <int MODE, bool FINAL>
 static cudaError_t launch_band_mode(cudaStream_t s, const BandGeom &g, const BandArgs &a)
 {
+    if (g.N >= 128) {
+        switch (g.CPT) {
+        case 4: return launch_band2<MODE, FINAL, 1>(s, g, a);
+        case 8: return launch_band2<MODE, FINAL, 2>(s, g, a);
+        case 16: return launch_band2<MODE, FINAL, 4>(s, g, a);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (g.CPT) {
     case 1: return launch_kernel(band_kernel<MODE, 1, FINAL>, dim3(g.nb), dim3(g.NT), 0, s, a, g.log2N, g.T);
     case 4: return launch_kernel(band_kernel<MODE, 4, FINAL>, dim3(g.nb), dim3(g.NT), 0, s, a, g.log2N, g.T);

@@ -192,6 +192,60 @@ def test_integral_images_u32_large_exact(dc, k):
         dc.declutter_destroy(ctx)
 
 
+@pytest.mark.parametrize("k,T", [(7, 1), (7, 64), (8, 2), (11, 64), (12, 1), (12, 16), (13, 8)])
+def test_integral_images_u32_band_heights(dc, k, T):
+    # every column layout of the band kernels (4, 8 and 16 columns a thread)
+    # and band heights from one row to 64
+    N = 1 << k
+    grid = synth.sat_grid(k, seed=T)
+    a_ref, at_ref = oracle.sat_u64(grid)
+    ctx = dc.declutter_create(k, kernel_r=0, band_rows=T)
+    try:
+        g = torch.from_numpy(grid.view(np.int32)).to(DEV)
+        a = torch.empty(N * N, dtype=torch.int64, device=DEV)
+        at = torch.empty(N * N, dtype=torch.int64, device=DEV)
+        dc.integral_images_u32(ctx, g, a, at)
+        dc.declutter_sync(ctx)
+        assert np.array_equal(u64(a, N), a_ref)
+        assert np.array_equal(u64(at, N), at_ref)
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+@pytest.mark.parametrize("k,T", [(7, 4), (9, 64), (12, 32), (13, 64)])
+def test_integral_images_u32_wide_bands(dc, k, T):
+    # Bands whose sums reach 2^32 take the 64-bit path; the others keep
+    # band-local sums in 32 bits while max(grid) * T * N < 2^32.  Bands cycle
+    # through: values in [2^31, 2^32); every value at that bound (32-bit path,
+    # sums up to 2^32 - 1); the bound plus one pixel one above it (64-bit path).
+    N = 1 << k
+    rng = np.random.default_rng(100 * k + T)
+    grid = synth.sat_grid(k).copy()
+    lim = (2**32 - 1) // (T * N)
+    for band in range(N // T):
+        rows = slice(band * T, (band + 1) * T)
+        kind = band % 3
+        if kind == 0:
+            grid[rows] = rng.integers(2**31, 2**32, size=(T, N), dtype=np.uint64).astype(np.uint32)
+        elif kind == 1:
+            grid[rows] = lim
+        else:
+            grid[rows] = lim
+            grid[band * T + int(rng.integers(T)), int(rng.integers(N))] = lim + 1
+    a_ref, at_ref = oracle.sat_u64(grid)
+    ctx = dc.declutter_create(k, kernel_r=0, band_rows=T)
+    try:
+        g = torch.from_numpy(grid.view(np.int32)).to(DEV)
+        a = torch.empty(N * N, dtype=torch.int64, device=DEV)
+        at = torch.empty(N * N, dtype=torch.int64, device=DEV)
+        dc.integral_images_u32(ctx, g, a, at)
+        dc.declutter_sync(ctx)
+        assert np.array_equal(u64(a, N), a_ref)
+        assert np.array_equal(u64(at, N), at_ref)
+    finally:
+        dc.declutter_destroy(ctx)
+
+
 # --------------------------------------------------------------------------
 # Options and edge cases
 # --------------------------------------------------------------------------
