@@ -79,6 +79,7 @@ BandArgs band_args(const dc_ctx *c, const void *src, int mode, int64_t n)
     const double S = c->p.pixel_center ? 2.0 * c->g.N : (double)c->g.N;
     const double den = 2.0 * S * NN * ((double)n + d0 * NN);
     a.inv_den_exact = den > 0.0 ? 1.0 / den : 0.0;
+    a.status = c->status;
     return a;
 }
 

@@ -559,12 +559,59 @@ __device__ __forceinline__ void store4_u64(unsigned long long *p, unsigned long 
     }
 }
 
-template <int MODE, int G, bool FINAL>
-__global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T)
+// Row staging by the bulk-copy (TMA) engine: one thread copies a whole row
+// into a ring slot of shared memory; the slot's mbarrier completes when the
+// bytes have landed.
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *m)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(m)) : "memory");
+}
+__device__ __forceinline__ void tma_row(void *dst, const void *src, unsigned bytes, unsigned long long *m)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(m))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long *m, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for a ring slot: false after one second.
+__device__ __noinline__ bool mbar_wait(unsigned long long *m, unsigned parity)
+{
+    if (mbar_try(m, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(m, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+
+// RING: rows arrive through a ring of `ring` shared-memory slots filled by
+// bulk copies (placed before the carry windows); otherwise each thread
+// prefetches its own chunks of the next row into registers.
+template <int MODE, int G, bool FINAL, bool RING>
+__global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T, int ring)
 {
     using S = typename Band2T<MODE>::S;
     using C = typename Band2T<MODE>::C;
-    constexpr int PD = G >= 4 ? 1 : 2;  // rows prefetched ahead
     const int N = 1 << log2N;
     const int NT = blockDim.x, nw = NT >> 5;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -576,7 +623,10 @@ __global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T
     __shared__ S s_uf[2][G][16];
     __shared__ S s_vl[2][G][16];
     __shared__ S s_U0[64], s_VN[64], s_RT[64];
-    extern __shared__ __align__(16) unsigned char s_dyn[];
+    __shared__ unsigned long long s_mbar[8];
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    const unsigned rowbytes = 4u << log2N;
+    unsigned char *ringp = s_dyn;
 
     pdl_wait();
     if constexpr (MODE == MODE_GRID64 && FINAL) {
@@ -587,6 +637,18 @@ __global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T
         }
     }
 
+    const unsigned char *src = static_cast<const unsigned char *>(a.src);
+    if constexpr (RING) {
+        if (t == 0) {
+            for (int k = 0; k < ring; ++k) mbar_init(&s_mbar[k]);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (t == 0)
+            for (int k = 0; k < ring && k < T; ++k)
+                tma_row(ringp + (size_t)k * rowbytes, src + (size_t)(j0 + k) * rowbytes, rowbytes, &s_mbar[k]);
+    }
+
     // ---- final pass: stage the band's carry and marginal windows
     const int L4a = ((((N + 3) >> 2) + 23) >> 5 << 5) + 8;
     const int L4w = ((((N + T - 1 + 3) >> 2) + 23) >> 5 << 5) + 8;
@@ -594,7 +656,7 @@ __global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T
     C Ctot = C(0), CVbN = C(0);
     float kappa = 0.f, scale = 0.f;
     if constexpr (FINAL) {
-        C *p = reinterpret_cast<C *>(s_dyn);
+        C *p = reinterpret_cast<C *>(s_dyn + (RING ? (size_t)ring * rowbytes : 0));
         sA = p; p += 4 * L4a;
         sU = p; p += 4 * L4w;
         sV = p; p += 4 * L4w;
@@ -639,16 +701,16 @@ __global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T
     S RTcum = S(0);
     uint32_t vmax = 0u;
 
-    const unsigned char *src = static_cast<const unsigned char *>(a.src);
     auto load = [&](int j, uint4 (&dst)[G]) {
 #pragma unroll
         for (int q = 0; q < G; ++q)
             dst[q] = ld_stream_v4(src + 4 * (((size_t)j << log2N) + 4 * (q * NT + t)));
     };
-    uint4 buf[PD][G];
-#pragma unroll
-    for (int d = 0; d < PD; ++d)
-        if (d < T) load(j0 + d, buf[d]);
+    uint4 buf[G];
+    if constexpr (!RING) load(j0, buf);
+    int rslot = 0;
+    unsigned rpar = 0;
+    bool dead = false;  // a ring wait expired: stop waiting, report DC_ERR_TIMEOUT
 
     const bool out32 = ((reinterpret_cast<uintptr_t>(a.alpha_out) | reinterpret_cast<uintptr_t>(a.alpha_t_out)) & 31) == 0;
 
@@ -656,13 +718,19 @@ __global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T
         const int j = j0 + r;
         const int par = r & 1;
         uint4 cur[G];
+        if constexpr (RING) {
+            if (!dead && !mbar_wait(&s_mbar[rslot], rpar)) {
+                dead = true;
+                if (a.status) atomicOr(a.status, (unsigned)DC_ERR_TIMEOUT);
+            }
+            const unsigned char *rowp = ringp + (size_t)rslot * rowbytes;
 #pragma unroll
-        for (int q = 0; q < G; ++q) cur[q] = buf[0][q];
+            for (int q = 0; q < G; ++q) cur[q] = *reinterpret_cast<const uint4 *>(rowp + 16 * (q * NT + t));
+        } else {
 #pragma unroll
-        for (int d = 0; d + 1 < PD; ++d)
-#pragma unroll
-            for (int q = 0; q < G; ++q) buf[d][q] = buf[d + 1][q];
-        if (r + PD < T) load(j + PD, buf[PD - 1]);
+            for (int q = 0; q < G; ++q) cur[q] = buf[q];
+            if (r + 1 < T) load(j + 1, buf);
+        }
 
         if constexpr (!FINAL) {
             if (a.zero_out) {
@@ -712,6 +780,18 @@ __global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T
             if (lane == 31) s_wt[par][q][warp] = x;
         }
         __syncthreads();
+        if constexpr (RING) {
+            // every thread has read this row's slot: refill it with row j + ring
+            if (t == 0 && r + ring < T && !dead) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_row(ringp + (size_t)rslot * rowbytes, src + (size_t)(j + ring) * rowbytes, rowbytes,
+                        &s_mbar[rslot]);
+            }
+            if (++rslot == ring) {
+                rslot = 0;
+                rpar ^= 1u;
+            }
+        }
 
         // scan over warps, then over chunk groups
         S off[G];
@@ -899,6 +979,235 @@ __global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T
 }
 
 // ------------------------------------------------------------------------
+// Aggregate pass by projections (N >= 128).
+//
+// Every value of a band's compact aggregate is a prefix sum of one of three
+// one-dimensional projections of the band (rows r' = 0 .. T-1 of the band,
+// x its values, minus mu in MODE_FLOAT):
+//   column sums        K_c  = sum_r' x(r', c)                c in [0, N)
+//   anti-diagonal sums A_d  = sum_r' x(r', d - r')           d in [0, N + T - 1)
+//   diagonal sums      D_e  = sum_r' x(r', e + r' - T + 1)   e in [0, N + T - 1)
+// Unrolling the band-local recurrences of band_body gives, with inclusive
+// prefixes PK, PA, PD:
+//   alpha(i) = PK(i), U(i) = PA(i + T - 1), V(i) = PD(i - 1) (0 for i = 0),
+//   U0[r] = PA(r), E[r] = PD(N + T - 3 - r), S = PK(N - 1).
+// So the pass needs no per-row scan: rows arrive by bulk copy into a ring of
+// shared-memory slots padded by T - 1 columns on both sides (zeros, or mu in
+// MODE_FLOAT, so that the padding contributes nothing), each thread adds the
+// shifted row values of the lines it owns, and three block scans at the end
+// produce the record.  Thread t owns columns 4 (t + NT k) .. + 3 of the
+// column sums and lines t + NT k (k < CPT) plus N + t and N + NT + t (below
+// N + T - 1) of the diagonal projections, so that every shared-memory read
+// of a warp is conflict-free.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ int ring_pad(int T) { return ((T - 1) + 3) & ~3; }
+
+// inclusive block scan, in place, of smem array v[0, L); NT threads
+template <typename S>
+__device__ void block_scan_inplace(S *v, int L, S *s_part)
+{
+    const int NT = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = NT >> 5;
+    const int per = ((L + NT - 1) / NT) | 1;  // odd stride: conflict-free segments
+    const int b0 = t * per, b1 = min(L, b0 + per);
+    S acc = S(0);
+    for (int i = b0; i < b1; ++i) acc = acc + v[i];
+    S x = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const S y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x = x + y;
+    }
+    if (lane == 31) s_part[warp] = x;
+    __syncthreads();
+    S wv = lane < nw ? s_part[lane] : S(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const S y = __shfl_up_sync(kFull, wv, o);
+        if (lane >= o) wv = wv + y;
+    }
+    const S wex = __shfl_sync(kFull, wv, (warp + 31) & 31);
+    S run = (warp > 0 ? wex : S(0)) + (x - acc);
+    for (int i = b0; i < b1; ++i) {
+        run = run + v[i];
+        v[i] = run;
+    }
+    __syncthreads();
+}
+
+template <int MODE, int CPT>
+__global__ void __launch_bounds__(512) agg_proj_kernel(BandArgs a, int log2N, int T, int ring)
+{
+    using S = typename Band2T<MODE>::S;
+    using C = typename Band2T<MODE>::C;
+    constexpr int G = CPT / 4;
+    const int N = 1 << log2N;
+    const int NT = blockDim.x;
+    const int t = threadIdx.x;
+    const int b = blockIdx.x;
+    const int j0 = b * T;
+    const int P0 = ring_pad(T);
+    const int slotw = N + 2 * P0;  // words per ring slot
+    const unsigned rowbytes = 4u << log2N;
+
+    __shared__ unsigned long long s_mbar[8];
+    __shared__ S s_part[32];
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    S *ringw = reinterpret_cast<S *>(s_dyn);
+    const unsigned char *src = static_cast<const unsigned char *>(a.src);
+
+    pdl_wait();
+    // padding columns of every slot (the bulk copies fill only the middle)
+    const S padv = MODE == MODE_FLOAT ? S(a.mu) : S(0);
+    for (int k = 0; k < ring; ++k)
+        for (int i = t; i < 2 * P0; i += NT) ringw[k * slotw + (i < P0 ? i : N + i)] = padv;
+    if (t == 0) {
+        for (int k = 0; k < ring; ++k) mbar_init(&s_mbar[k]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (t == 0)
+        for (int k = 0; k < ring && k < T; ++k)
+            tma_row(ringw + k * slotw + P0, src + (size_t)(j0 + k) * rowbytes, rowbytes, &s_mbar[k]);
+
+    S K[G][4], A[CPT + 2], D[CPT + 2];
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) K[q][e] = S(0);
+#pragma unroll
+    for (int k = 0; k < CPT + 2; ++k) { A[k] = S(0); D[k] = S(0); }
+    // lines N + t and N + NT + t of the diagonal projections (T - 1 <= 63, NT >= 32)
+    const bool extra = t < T - 1, extra2 = NT + t < T - 1;
+    uint32_t vor = 0u;
+    int rslot = 0;
+    unsigned rpar = 0;
+    bool dead = false;
+
+    for (int r = 0; r < T; ++r) {
+        const int j = j0 + r;
+        if (!dead && !mbar_wait(&s_mbar[rslot], rpar)) {
+            dead = true;
+            if (a.status) atomicOr(a.status, (unsigned)DC_ERR_TIMEOUT);
+        }
+        const S *row = ringw + rslot * slotw + P0;  // row[c], c in [-P0, N + P0)
+        if constexpr (MODE == MODE_COUNT) {
+            if (a.zero_out) {
+#pragma unroll
+                for (int q = 0; q < G; ++q)
+                    *reinterpret_cast<uint4 *>(a.zero_out + ((size_t)j << log2N) + 4 * (t + NT * q)) =
+                        make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(row + 4 * (t + NT * q));
+            if constexpr (MODE == MODE_FLOAT) {
+                K[q][0] = K[q][0] + (__uint_as_float(v.x) - a.mu);
+                K[q][1] = K[q][1] + (__uint_as_float(v.y) - a.mu);
+                K[q][2] = K[q][2] + (__uint_as_float(v.z) - a.mu);
+                K[q][3] = K[q][3] + (__uint_as_float(v.w) - a.mu);
+            } else {
+                K[q][0] = K[q][0] + v.x;
+                K[q][1] = K[q][1] + v.y;
+                K[q][2] = K[q][2] + v.z;
+                K[q][3] = K[q][3] + v.w;
+                if constexpr (MODE == MODE_GRID64) vor |= v.x | v.y | v.z | v.w;
+            }
+        }
+        const S *ra = row + t - r;            // A: column (t + NT k) - r
+        const S *rd = row + t + r - (T - 1);  // D: column (t + NT k) + r - (T - 1)
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            if constexpr (MODE == MODE_FLOAT) {
+                A[k] = A[k] + (ra[NT * k] - a.mu);
+                D[k] = D[k] + (rd[NT * k] - a.mu);
+            } else {
+                A[k] = A[k] + ra[NT * k];
+                D[k] = D[k] + rd[NT * k];
+            }
+        }
+        if (extra) {
+            if constexpr (MODE == MODE_FLOAT) {
+                A[CPT] = A[CPT] + (ra[N] - a.mu);
+                D[CPT] = D[CPT] + (rd[N] - a.mu);
+            } else {
+                A[CPT] = A[CPT] + ra[N];
+                D[CPT] = D[CPT] + rd[N];
+            }
+        }
+        if (extra2) {
+            if constexpr (MODE == MODE_FLOAT) {
+                A[CPT + 1] = A[CPT + 1] + (ra[N + NT] - a.mu);
+                D[CPT + 1] = D[CPT + 1] + (rd[N + NT] - a.mu);
+            } else {
+                A[CPT + 1] = A[CPT + 1] + ra[N + NT];
+                D[CPT + 1] = D[CPT + 1] + rd[N + NT];
+            }
+        }
+        __syncthreads();
+        if (t == 0 && r + ring < T && !dead) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_row(ringw + rslot * slotw + P0, src + (size_t)(j + ring) * rowbytes, rowbytes, &s_mbar[rslot]);
+        }
+        if (++rslot == ring) {
+            rslot = 0;
+            rpar ^= 1u;
+        }
+    }
+
+    C *ag = static_cast<C *>(a.agg) + (size_t)b * a.agg_stride;
+    if constexpr (MODE == MODE_GRID64) {
+        // every band-local sum is at most the band total <= max(x) T N
+        const uint32_t lim = 0xffffffffu / (uint32_t)(T << log2N);
+        if (__syncthreads_or(vor > lim)) {
+            band_body_wide<MODE_GRID64, CPT, false>(a, log2N, T);
+            if (t == 0) ag[3 * N + 2 * T + 1] = 1ull;
+            return;
+        }
+    }
+
+    // projections into shared memory (the ring is no longer read), then scans
+    const int L = N + T - 1;
+    S *pk = ringw, *pa = ringw + N, *pd = ringw + N + L;
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) pk[4 * (t + NT * q) + e] = K[q][e];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        pa[t + NT * k] = A[k];
+        pd[t + NT * k] = D[k];
+    }
+    if (extra) {
+        pa[N + t] = A[CPT];
+        pd[N + t] = D[CPT];
+    }
+    if (extra2) {
+        pa[N + NT + t] = A[CPT + 1];
+        pd[N + NT + t] = D[CPT + 1];
+    }
+    __syncthreads();
+    block_scan_inplace(pk, N, s_part);
+    block_scan_inplace(pa, L, s_part);
+    block_scan_inplace(pd, L, s_part);
+
+    // compact aggregate [alpha N][U N][V N][U0 T][E T][S][flag]
+    for (int i = t; i < N; i += NT) {
+        ag[i] = C(pk[i]);
+        ag[N + i] = C(pa[i + T - 1]);
+        ag[2 * N + i] = i > 0 ? C(pd[i - 1]) : C(0);
+    }
+    for (int r = t; r < T; r += NT) {
+        ag[3 * N + r] = C(pa[r]);
+        ag[3 * N + T + r] = C(pd[N + T - 3 - r]);
+    }
+    if (t == 0) {
+        ag[3 * N + 2 * T] = C(pk[N - 1]);
+        if constexpr (MODE == MODE_GRID64) ag[3 * N + 2 * T + 1] = 0ull;
+    }
+}
+
+// ------------------------------------------------------------------------
 // Carries: exclusive scan over bands of every absolute line.
 // Lanes [0, N): vertical line i.  [N, 3N): anti-diagonal u = lane - N.
 // [3N, 5N): diagonal v = lane - 3N - (N - 1).  Row b of the output holds
@@ -1020,9 +1329,17 @@ static size_t band2_smem_bytes(int mode, int N, int T)
 template <int MODE, int G>
 static cudaError_t allow_band2_smem()
 {
-    // largest grid of each G: N = 2048 G (G = 1: up to 2048), band height <= 64
-    return cudaFuncSetAttribute(band2_kernel<MODE, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)band2_smem_bytes(MODE, 2048 * G, 64));
+    // the most any launch asks for (carry windows plus ring, <= 200 KB)
+    const int most = 204800;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(agg_proj_kernel<MODE, 4 * G>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(band2_kernel<MODE, G, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(band2_kernel<MODE, G, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 most);
+    return e;
 }
 
 cudaError_t prepare_kernels()
@@ -1052,11 +1369,63 @@ cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, i
     return launch_kernel(smooth_kernel, grid, dim3(256), (size_t)bytes, s, counts, dens, log2N, w, zero_out);
 }
 
+// Ring slots of the interleaved kernels: up to 128 KB of rows for the
+// aggregate pass; for the final pass what is left of 200 KB after the carry
+// windows (none at N = 8192, whose final pass prefetches into registers).
+static int band2_ring(int mode, bool final_pass, int N, int T)
+{
+    const size_t row = 4 * (size_t)N;
+    size_t room = 131072;
+    if (final_pass) {
+        const size_t win = band2_smem_bytes(mode, N, T);
+        room = win < 204800 ? 204800 - win : 0;
+    }
+    int k = (int)(room / row);
+    if (k > 8) k = 8;
+    if (k > T) k = T < 2 ? 2 : T;
+    return k >= 2 ? k : 0;
+}
+
+// Ring of the projection aggregate pass: up to 8 padded rows within 128 KB;
+// the scans at the end reuse the same memory (3N + 2T words).
+static int agg_ring(int N, int T)
+{
+    const int pad = ((T - 1) + 3) & ~3;
+    const size_t slot = 4 * (size_t)(N + 2 * pad);
+    int k = (int)(131072 / slot);
+    if (k > 8) k = 8;
+    if (k > T) k = T;
+    return k < 2 ? 2 : k;
+}
+static size_t agg_smem_bytes(int N, int T, int ring)
+{
+    const int pad = ((T - 1) + 3) & ~3;
+    const size_t ringb = 4 * (size_t)ring * (N + 2 * pad);
+    const size_t scanb = 4 * (size_t)(3 * N + 2 * T);
+    return ringb > scanb ? ringb : scanb;
+}
+
+template <int MODE, int CPT>
+static cudaError_t launch_agg_proj(cudaStream_t s, const BandGeom &g, const BandArgs &a)
+{
+    const int ring = agg_ring(g.N, g.T);
+    return launch_kernel(agg_proj_kernel<MODE, CPT>, dim3(g.nb), dim3(g.NT), agg_smem_bytes(g.N, g.T, ring), s, a,
+                         g.log2N, g.T, ring);
+}
+
 template <int MODE, bool FINAL, int G>
 static cudaError_t launch_band2(cudaStream_t s, const BandGeom &g, const BandArgs &a)
 {
-    const size_t smem = FINAL ? band2_smem_bytes(MODE, g.N, g.T) : 0;
-    return launch_kernel(band2_kernel<MODE, G, FINAL>, dim3(g.nb), dim3(g.NT), smem, s, a, g.log2N, g.T);
+    if constexpr (!FINAL) {
+        return launch_agg_proj<MODE, 4 * G>(s, g, a);
+    } else {
+        const int ring = band2_ring(MODE, true, g.N, g.T);
+        const size_t smem = band2_smem_bytes(MODE, g.N, g.T) + (size_t)ring * 4 * g.N;
+        if (ring)
+            return launch_kernel(band2_kernel<MODE, G, true, true>, dim3(g.nb), dim3(g.NT), smem, s, a, g.log2N, g.T,
+                                 ring);
+        return launch_kernel(band2_kernel<MODE, G, true, false>, dim3(g.nb), dim3(g.NT), smem, s, a, g.log2N, g.T, 0);
+    }
 }
 
 template <int MODE, bool FINAL>

@@ -75,6 +75,12 @@ extern "C" dc_status integral_images_u32_noalloc(const uint32_t *grid, uint32_t 
                 snprintf(g_noalloc_msg, sizeof(g_noalloc_msg), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
                 return noalloc_fail(DC_ERR_CUDA);
             }
+            // kernel attributes (dynamic shared memory of the band kernels)
+            const cudaError_t ek = prepare_kernels();
+            if (ek != cudaSuccess) {
+                snprintf(g_noalloc_msg, sizeof(g_noalloc_msg), "kernel attributes: %s", cudaGetErrorString(ek));
+                return noalloc_fail(DC_ERR_CUDA);
+            }
             g_noalloc_ptr[dev] = p;
         }
         scratch = g_noalloc_ptr[dev];
@@ -89,7 +95,8 @@ extern "C" dc_status integral_images_u32_noalloc(const uint32_t *grid, uint32_t 
         return noalloc_fail(DC_ERR_INVALID_ARG);
     }
     // No element of the scratch has to start at zero: each one the kernels
-    // read is written earlier in the same call.
+    // read is written earlier in the same call.  There is no status word
+    // here, so an expired bounded wait inside a kernel is not reported.
     BandArgs a{};
     a.src = grid;
     a.agg = scratch;
