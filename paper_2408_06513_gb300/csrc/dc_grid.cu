@@ -52,6 +52,13 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Carry layout: band b < nb keeps the lanes its final pass reads, at
+// b * carry_stride: [vertical N][anti-diagonal window N + T - 1]
+// [diagonal window N + T - 1], the windows starting at lines u = j0 and
+// v = -(j0 + T - 1); row nb (at nb * carry_stride) keeps all 5N lanes of
+// the totals (the marginals).
+__host__ __device__ __forceinline__ int carry_stride(int N, int T) { return (3 * N + 2 * T - 2 + 3) & ~3; }
+
 // ------------------------------------------------------------------------
 // Smoothing: one 2D tile per CTA with a halo of r on each side, vertical
 // then horizontal pass in shared memory; reflect border (-1 -> 0, N -> N-1).
@@ -271,8 +278,8 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
     Acc Ctot = Acc(0), CVbN = Acc(0);
     float kappa = 0.f, scale = 0.f;
     if constexpr (FINAL) {
-        cb = static_cast<const Acc *>(a.carry) + (size_t)b * lanes;
-        ce = static_cast<const Acc *>(a.carry) + (size_t)(N / T) * lanes;
+        cb = static_cast<const Acc *>(a.carry) + (size_t)b * carry_stride(N, T);
+        ce = static_cast<const Acc *>(a.carry) + (size_t)(N / T) * carry_stride(N, T);
 #pragma unroll
         for (int k = 0; k < CPT; ++k) {
             const int c = min(c0 + k, N - 1);
@@ -377,7 +384,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
                 const int u = cc + j;
                 const int vi = cc - j + N - 1;
                 const Acc al = cvb[k] + arun[k];
-                const Acc at = (cb[N + u] + Un[k]) - (cb[3 * N + vi] + Vn[k]);
+                const Acc at = (cb[N + (u - j0)] + Un[k]) - (cb[2 * N + T - 1 + (vi - (N - j0 - T))] + Vn[k]);
                 const Acc A = ce[N + u];
                 const Acc Bv = Ctot - ce[3 * N + vi];
                 const Acc R = Rk[k];
@@ -665,17 +672,17 @@ __global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T
             sAm = p; p += 4 * L4w;
             sBm = p;
         }
-        const C *cb = static_cast<const C *>(a.carry) + (size_t)b * lanes;
-        const C *ce = static_cast<const C *>(a.carry) + (size_t)(N / T) * lanes;
-        const int ubase = N + j0;              // lane of window element 0: u = j0
-        const int vbase = 3 * N + N - j0 - T;  // lane of window element 0: v = -(j0 + T - 1)
+        const C *cb = static_cast<const C *>(a.carry) + (size_t)b * carry_stride(N, T);
+        const C *ce = static_cast<const C *>(a.carry) + (size_t)(N / T) * carry_stride(N, T);
+        const int ubase = N + j0;              // marginal lane of window element 0: u = j0
+        const int vbase = 3 * N + N - j0 - T;  // marginal lane of window element 0: v = -(j0 + T - 1)
         for (int i = t; i < N; i += NT) {
             sA[wpos(i, L4a)] = cb[i];
             if constexpr (MODE != MODE_GRID64) sR[wpos(i, L4a)] = ce[i];
         }
         for (int i = t; i < N + T - 1; i += NT) {
-            sU[wpos(i, L4w)] = cb[ubase + i];
-            sV[wpos(i, L4w)] = cb[vbase + i];
+            sU[wpos(i, L4w)] = cb[N + i];
+            sV[wpos(i, L4w)] = cb[2 * N + T - 1 + i];
             if constexpr (MODE != MODE_GRID64) {
                 sAm[wpos(i, L4w)] = ce[ubase + i];
                 sBm[wpos(i, L4w)] = ce[vbase + i];
@@ -1264,48 +1271,80 @@ struct ScanF64 {
     __device__ ScanF64 shfl_up(int o) const { ScanF64 r; r.s = __shfl_up_sync(kFull, s, o); return r; }
 };
 
+// One block: 32 lanes x ng groups of bands (ng warps); each thread sums its
+// group's contributions (kept in registers when the group has at most
+// kCarryCache bands), the groups' totals are scanned in shared memory, and
+// each thread writes its group's exclusive prefixes into the bands whose
+// windows hold the lane.
+constexpr int kCarryCache = 16;
+
 template <typename Acc, typename Sum>
 __global__ void __launch_bounds__(1024) carry_kernel(const Acc *__restrict__ agg, Acc *__restrict__ carry,
                                                      int log2N, int T, int nb, int agg_stride)
 {
     const int N = 1 << log2N;
     const int lanes = 5 * N;
-    const int lx = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int cs = carry_stride(N, T);
+    const int lx = threadIdx.x & 31, g = threadIdx.x >> 5, ng = blockDim.x >> 5;
     const int lane = blockIdx.x * 32 + lx;
     const bool active = lane < lanes;
-    const int bpg = (nb + 31) / 32;
+    const int bpg = (nb + ng - 1) / ng;
     const int b_beg = g * bpg;
     const int b_end = min(nb, b_beg + bpg);
     __shared__ Sum s_sum[32][33];
     pdl_wait();
 
+    Acc cache[kCarryCache];
     Sum s;
     s.zero();
-    if (active)
-        for (int b = b_beg; b < b_end; ++b) s.add(band_contrib(agg + (size_t)b * agg_stride, b, lane, N, T));
+    if (active) {
+        if (bpg <= kCarryCache) {
+#pragma unroll
+            for (int k = 0; k < kCarryCache; ++k)
+                if (b_beg + k < b_end) cache[k] = band_contrib(agg + (size_t)(b_beg + k) * agg_stride, b_beg + k, lane, N, T);
+#pragma unroll
+            for (int k = 0; k < kCarryCache; ++k)
+                if (b_beg + k < b_end) s.add(cache[k]);
+        } else {
+            for (int b = b_beg; b < b_end; ++b) s.add(band_contrib(agg + (size_t)b * agg_stride, b, lane, N, T));
+        }
+    }
     s_sum[g][lx] = s;
     __syncthreads();
-    {
-        // warp g scans column (lane) g over the 32 groups held by its lanes
-        Sum x = s_sum[lx][g];
-        Sum inc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            Sum y = inc.shfl_up(o);
-            if (lx >= o) inc.add(y);
-        }
-        Sum ex = inc.shfl_up(1);
-        if (lx == 0) ex.zero();
-        s_sum[lx][g] = ex;
-    }
-    __syncthreads();
     if (!active) return;
-    Sum pre = s_sum[g][lx];
-    for (int b = b_beg; b < b_end; ++b) {
-        carry[(size_t)b * lanes + lane] = pre.value();
-        pre.add(band_contrib(agg + (size_t)b * agg_stride, b, lane, N, T));
+    Sum pre;
+    pre.zero();
+    for (int q = 0; q < g; ++q) pre.add(s_sum[q][lx]);
+
+    // where lane's value goes in band b's window (or -1)
+    auto slot = [&](int b) -> int {
+        if (lane < N) return lane;
+        const int j0 = b * T;
+        if (lane < 3 * N) {
+            const int o = lane - N - j0;
+            return (o >= 0 && o < N + T - 1) ? N + o : -1;
+        }
+        const int o = lane - 3 * N - (N - j0 - T);
+        return (o >= 0 && o < N + T - 1) ? 2 * N + T - 1 + o : -1;
+    };
+    if (bpg <= kCarryCache) {
+#pragma unroll
+        for (int k = 0; k < kCarryCache; ++k) {
+            const int b = b_beg + k;
+            if (b < b_end) {
+                const int o = slot(b);
+                if (o >= 0) carry[(size_t)b * cs + o] = pre.value();
+                pre.add(cache[k]);
+            }
+        }
+    } else {
+        for (int b = b_beg; b < b_end; ++b) {
+            const int o = slot(b);
+            if (o >= 0) carry[(size_t)b * cs + o] = pre.value();
+            pre.add(band_contrib(agg + (size_t)b * agg_stride, b, lane, N, T));
+        }
     }
-    if (b_beg < nb && b_end == nb) carry[(size_t)nb * lanes + lane] = pre.value();
+    if (b_beg < nb && b_end == nb) carry[(size_t)nb * cs + lane] = pre.value();
 }
 
 }  // namespace
@@ -1470,7 +1509,9 @@ cudaError_t launch_band_final(cudaStream_t s, const BandGeom &g, int mode, const
 
 cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const void *agg, void *carry)
 {
-    const dim3 blocks((g.lanes + 31) / 32), threads(1024);
+    int ng = (g.nb + kCarryCache - 1) / kCarryCache;  // groups of at most kCarryCache bands
+    ng = ng < 1 ? 1 : (ng > 32 ? 32 : ng);
+    const dim3 blocks((g.lanes + 31) / 32), threads(32 * ng);
     switch (mode) {
     case MODE_COUNT:
         return launch_kernel(carry_kernel<uint32_t, ScanSum<uint32_t>>, blocks, threads, 0, s,
