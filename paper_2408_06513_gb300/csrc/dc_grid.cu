@@ -602,25 +602,28 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 // Bounded wait for a ring slot: false after one second.
-__device__ __noinline__ bool mbar_wait(unsigned long long *m, unsigned parity)
+__device__ __noinline__ bool mbar_wait_slow(unsigned long long *m, unsigned parity)
 {
-    if (mbar_try(m, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try(m, parity))
         if (global_ns() - t0 > 1000000000ull) return false;
     return true;
 }
+__device__ __forceinline__ bool mbar_wait(unsigned long long *m, unsigned parity)
+{
+    return mbar_try(m, parity) || mbar_wait_slow(m, parity);
+}
 
 // RING: rows arrive through a ring of `ring` shared-memory slots filled by
 // bulk copies (placed before the carry windows); otherwise each thread
 // prefetches its own chunks of the next row into registers.
-template <int MODE, int G, bool FINAL, bool RING>
-__global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T, int ring)
+template <int MODE, int NT, int G, bool FINAL, bool RING>
+__global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T, int ring)
 {
     using S = typename Band2T<MODE>::S;
     using C = typename Band2T<MODE>::C;
-    const int N = 1 << log2N;
-    const int NT = blockDim.x, nw = NT >> 5;
+    constexpr int nw = NT / 32;
+    const int N = 4 * NT * G;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int b = blockIdx.x;
     const int j0 = b * T;
@@ -821,27 +824,31 @@ __global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T
         for (int q = 0; q < G; ++q) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) p[q][e] = p[q][e] + off[q];
-            if (lane == 31) u_next[q] = warp + 1 < nw ? s_uf[par][q][warp + 1] : (q + 1 < G ? s_uf[par][q + 1][0] : S(0));
-            if (lane == 0) v_prev[q] = warp > 0 ? s_vl[par][q][warp - 1] : (q > 0 ? s_vl[par][q - 1][nw - 1] : S(0));
         }
-
-        // the three recurrences, in place: U ascending, V descending
+        // the grid's edges: U(N, j-1) is the row totals above (column N - 1
+        // is element 3 of thread NT - 1's last chunk); V(-1, j-1) = 0
+        // (column 0 is element 0 of thread 0's first chunk)
         const S RTprev = RTcum;
         RTcum = RTcum + total;
 #pragma unroll
         for (int q = 0; q < G; ++q) {
-            const int cq = 4 * (q * NT + t);
+            if (lane == 31)
+                u_next[q] = warp + 1 < nw ? s_uf[par][q][warp + 1] : (q + 1 < G ? s_uf[par][q + 1][0] : RTprev);
+            if (lane == 0) v_prev[q] = warp > 0 ? s_vl[par][q][warp - 1] : (q > 0 ? s_vl[par][q - 1][nw - 1] : S(0));
+        }
+
+        // the three recurrences, in place: U ascending, V descending
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                S ur = e < 3 ? Uo[q][e + 1] : u_next[q];
-                if (cq + e == N - 1) ur = RTprev;  // U(N, j-1): row totals only
+                const S ur = e < 3 ? Uo[q][e + 1] : u_next[q];
                 Uo[q][e] = ur + p[q][e];
                 arun[q][e] = arun[q][e] + p[q][e];
             }
 #pragma unroll
             for (int e = 3; e >= 0; --e) {
-                S vl = e > 0 ? Vo[q][e - 1] : v_prev[q];
-                if (cq + e == 0) vl = S(0);       // V(-1, j-1) = 0
+                const S vl = e > 0 ? Vo[q][e - 1] : v_prev[q];
                 const S pm1 = e > 0 ? p[q][e - 1] : off[q];  // P(j, c-1)
                 Vo[q][e] = vl + pm1;
             }
@@ -855,12 +862,23 @@ __global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T
             if (t == NT - 1) s_VN[r] = Vo[G - 1][3];
         } else {
             const size_t rowoff = (size_t)j << log2N;
+            // window element of column 4 m + e at this row: wpos(4 m + e + r)
+            // = offU[e] + m, wpos(4 m + e - r + T - 1) = offV[e] + m
+            int offU[4], offV[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int iu = e + r, iv = e - r + T - 1;
+                offU[e] = (iu & 3) * L4w + (iu >> 2) + t;
+                offV[e] = (iv & 3) * L4w + (iv >> 2) + t;
+            }
 #pragma unroll
             for (int q = 0; q < G; ++q) {
                 const int cq = 4 * (q * NT + t);
                 if constexpr (MODE == MODE_GRID64) {
                     unsigned long long oal[4], oat[4];
 #pragma unroll
+                    // (window positions recomputed per column: fewer live
+                    // registers than the per-row offsets, faster at G = 4)
                     for (int e = 0; e < 4; ++e) {
                         const int c = cq + e;
                         oal[e] = sA[wpos(c, L4a)] + (unsigned long long)arun[q][e];
@@ -880,12 +898,12 @@ __global__ void __launch_bounds__(512) band2_kernel(BandArgs a, int log2N, int T
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int c = cq + e;
-                        const int iu = wpos(c + r, L4w), iv = wpos(c - r + T - 1, L4w);
-                        const C al = sA[wpos(c, L4a)] + arun[q][e];
+                        const int iu = offU[e] + q * NT, iv = offV[e] + q * NT, ia = e * L4a + q * NT + t;
+                        const C al = sA[ia] + arun[q][e];
                         const C at = (sU[iu] + Uo[q][e]) - (sV[iv] + Vo[q][e]);
                         const C A = sAm[iu];
                         const C Bv = Ctot - sBm[iv];
-                        const C R = sR[wpos(c, L4a)];
+                        const C R = sR[ia];
                         C w[8];
                         w[0] = al;
                         w[1] = R - al;
@@ -1041,14 +1059,13 @@ __device__ void block_scan_inplace(S *v, int L, S *s_part)
     __syncthreads();
 }
 
-template <int MODE, int CPT>
-__global__ void __launch_bounds__(512) agg_proj_kernel(BandArgs a, int log2N, int T, int ring)
+template <int MODE, int NT, int CPT>
+__global__ void __launch_bounds__(NT) agg_proj_kernel(BandArgs a, int log2N, int T, int ring)
 {
     using S = typename Band2T<MODE>::S;
     using C = typename Band2T<MODE>::C;
     constexpr int G = CPT / 4;
-    const int N = 1 << log2N;
-    const int NT = blockDim.x;
+    const int N = NT * CPT;
     const int t = threadIdx.x;
     const int b = blockIdx.x;
     const int j0 = b * T;
@@ -1365,19 +1382,28 @@ static size_t band2_smem_bytes(int mode, int N, int T)
     return mode == MODE_GRID64 ? per * 8 : 2 * per * 4;
 }
 
-template <int MODE, int G>
+template <int MODE, int NT, int G>
 static cudaError_t allow_band2_smem()
 {
     // the most any launch asks for (carry windows plus ring, <= 200 KB)
     const int most = 204800;
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(agg_proj_kernel<MODE, NT, 4 * G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         most);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(agg_proj_kernel<MODE, 4 * G>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(band2_kernel<MODE, G, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(band2_kernel<MODE, G, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(band2_kernel<MODE, NT, G, true, (G < 4)>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  most);
+    return e;
+}
+template <int MODE>
+static cudaError_t allow_band2_smem_all()
+{
+    cudaError_t e = allow_band2_smem<MODE, 32, 1>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE, 64, 1>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE, 128, 1>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE, 256, 1>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE, 512, 1>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE, 512, 2>();
+    if (e == cudaSuccess) e = allow_band2_smem<MODE, 512, 4>();
     return e;
 }
 
@@ -1386,15 +1412,9 @@ cudaError_t prepare_kernels()
     // dynamic shared memory of the smoothing tile for the largest radius
     cudaError_t e = cudaFuncSetAttribute(smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smooth_smem_bytes(64));
-    if (e == cudaSuccess) e = allow_band2_smem<MODE_COUNT, 1>();
-    if (e == cudaSuccess) e = allow_band2_smem<MODE_COUNT, 2>();
-    if (e == cudaSuccess) e = allow_band2_smem<MODE_COUNT, 4>();
-    if (e == cudaSuccess) e = allow_band2_smem<MODE_FLOAT, 1>();
-    if (e == cudaSuccess) e = allow_band2_smem<MODE_FLOAT, 2>();
-    if (e == cudaSuccess) e = allow_band2_smem<MODE_FLOAT, 4>();
-    if (e == cudaSuccess) e = allow_band2_smem<MODE_GRID64, 1>();
-    if (e == cudaSuccess) e = allow_band2_smem<MODE_GRID64, 2>();
-    if (e == cudaSuccess) e = allow_band2_smem<MODE_GRID64, 4>();
+    if (e == cudaSuccess) e = allow_band2_smem_all<MODE_COUNT>();
+    if (e == cudaSuccess) e = allow_band2_smem_all<MODE_FLOAT>();
+    if (e == cudaSuccess) e = allow_band2_smem_all<MODE_GRID64>();
     return e;
 }
 
@@ -1444,40 +1464,46 @@ static size_t agg_smem_bytes(int N, int T, int ring)
     return ringb > scanb ? ringb : scanb;
 }
 
-template <int MODE, int CPT>
-static cudaError_t launch_agg_proj(cudaStream_t s, const BandGeom &g, const BandArgs &a)
+template <int MODE, int NT, int G>
+static cudaError_t launch_band2(cudaStream_t s, const BandGeom &g, const BandArgs &a, bool final_pass)
 {
-    const int ring = agg_ring(g.N, g.T);
-    return launch_kernel(agg_proj_kernel<MODE, CPT>, dim3(g.nb), dim3(g.NT), agg_smem_bytes(g.N, g.T, ring), s, a,
-                         g.log2N, g.T, ring);
+    if (!final_pass) {
+        const int ring = agg_ring(g.N, g.T);
+        return launch_kernel(agg_proj_kernel<MODE, NT, 4 * G>, dim3(g.nb), dim3(NT), agg_smem_bytes(g.N, g.T, ring),
+                             s, a, g.log2N, g.T, ring);
+    }
+    const int ring = band2_ring(MODE, true, g.N, g.T);
+    const size_t smem = band2_smem_bytes(MODE, g.N, g.T) + (size_t)ring * 4 * g.N;
+    if constexpr (G < 4) {  // N <= 4096: rows through the bulk-copy ring
+        if (ring)
+            return launch_kernel(band2_kernel<MODE, NT, G, true, true>, dim3(g.nb), dim3(NT), smem, s, a, g.log2N,
+                                 g.T, ring);
+        return cudaErrorInvalidValue;
+    } else {  // N = 8192: the carry windows fill shared memory
+        return launch_kernel(band2_kernel<MODE, NT, G, true, false>, dim3(g.nb), dim3(NT), smem, s, a, g.log2N, g.T,
+                             0);
+    }
 }
 
-template <int MODE, bool FINAL, int G>
-static cudaError_t launch_band2(cudaStream_t s, const BandGeom &g, const BandArgs &a)
+template <int MODE>
+static cudaError_t launch_band2_n(cudaStream_t s, const BandGeom &g, const BandArgs &a, bool final_pass)
 {
-    if constexpr (!FINAL) {
-        return launch_agg_proj<MODE, 4 * G>(s, g, a);
-    } else {
-        const int ring = band2_ring(MODE, true, g.N, g.T);
-        const size_t smem = band2_smem_bytes(MODE, g.N, g.T) + (size_t)ring * 4 * g.N;
-        if (ring)
-            return launch_kernel(band2_kernel<MODE, G, true, true>, dim3(g.nb), dim3(g.NT), smem, s, a, g.log2N, g.T,
-                                 ring);
-        return launch_kernel(band2_kernel<MODE, G, true, false>, dim3(g.nb), dim3(g.NT), smem, s, a, g.log2N, g.T, 0);
+    switch (g.log2N) {  // NT = min(512, N / 4) threads, G = N / (4 NT) chunks a thread
+    case 7: return launch_band2<MODE, 32, 1>(s, g, a, final_pass);
+    case 8: return launch_band2<MODE, 64, 1>(s, g, a, final_pass);
+    case 9: return launch_band2<MODE, 128, 1>(s, g, a, final_pass);
+    case 10: return launch_band2<MODE, 256, 1>(s, g, a, final_pass);
+    case 11: return launch_band2<MODE, 512, 1>(s, g, a, final_pass);
+    case 12: return launch_band2<MODE, 512, 2>(s, g, a, final_pass);
+    case 13: return launch_band2<MODE, 512, 4>(s, g, a, final_pass);
+    default: return cudaErrorInvalidValue;
     }
 }
 
 template <int MODE, bool FINAL>
 static cudaError_t launch_band_mode(cudaStream_t s, const BandGeom &g, const BandArgs &a)
 {
-    if (g.N >= 128) {
-        switch (g.CPT) {
-        case 4: return launch_band2<MODE, FINAL, 1>(s, g, a);
-        case 8: return launch_band2<MODE, FINAL, 2>(s, g, a);
-        case 16: return launch_band2<MODE, FINAL, 4>(s, g, a);
-        default: return cudaErrorInvalidValue;
-        }
-    }
+    if (g.N >= 128) return launch_band2_n<MODE>(s, g, a, FINAL);
     switch (g.CPT) {
     case 1: return launch_kernel(band_kernel<MODE, 1, FINAL>, dim3(g.nb), dim3(g.NT), 0, s, a, g.log2N, g.T);
     case 4: return launch_kernel(band_kernel<MODE, 4, FINAL>, dim3(g.nb), dim3(g.NT), 0, s, a, g.log2N, g.T);
