@@ -168,22 +168,39 @@ class ClockSampler:
 # algorithmic bytes per launch (see the design notes for the derivation)
 # ---------------------------------------------------------------------------
 
+def band_record_bytes(N: int, T: int, elem: int = 4):
+    """(aggregate bytes, carry bytes) of the band decomposition: nb compact
+    aggregates of 3N + 2T + 2 values; carries of nb windows of 3N + 2T - 2
+    values (rounded to 4) plus the 5N marginals."""
+    nb = N // T
+    agg = nb * (3 * N + 2 * T + 2) * elem
+    carry = (nb * ((3 * N + 2 * T - 2 + 3) // 4 * 4) + 5 * N) * elem
+    return agg, carry
+
+
 def algorithmic_bytes(kind: str, n: int, N: int, info) -> float:
     NN = N * N
-    T, nb = info.band_rows, info.n_bands
-    agg = nb * (3 * N + 2 * T + 1) * 4
-    carry = (nb + 1) * 5 * N * 4
+    agg, carry = band_record_bytes(N, info.band_rows)
     table = {
         "splat": 8.0 * n,                       # read the samples (atomics are the bound)
         "smooth": 8.0 * NN,                     # read counts, write d_r
         "band_aggregate": 4.0 * NN + agg,       # read d_r, write the compact aggregates
         "band_carry": agg + carry,              # read aggregates, write carries
-        "band_final": 12.0 * NN,                # read d_r, write the float2 displacement
+        "band_final": 12.0 * NN + 2 * carry,    # read d_r and the carry/marginal windows, write the field
         "advect": 16.0 * n,                     # read + write the samples
         "quality": 4.0 * NN,
         "reorder": 4.0 * NN * 3 + 8.0 * n * 2 + 4.0 * n * 2 + 8.0 * n,  # scan, scatter, way back
     }
     return table[kind]
+
+
+def combine_ranks(pg, world: int, n: int, iters: int, ms_local: float, e2e_s_local: float, device=None):
+    """Whole-job numbers from every rank's own timings: the slowest rank's
+    step time (max over ranks) and the units all ranks processed over it."""
+    ms = max_over_ranks(pg, ms_local, device)
+    e2e_s = max_over_ranks(pg, e2e_s_local, device)
+    return {"ms_per_step": ms, "value": world * n * iters / (ms * 1e-3) / 1e6,
+            "e2e_value": world * n * iters / e2e_s / 1e6}
 
 
 def csrc_digest() -> str:
@@ -264,7 +281,8 @@ def run_reference(args, world, rank):
     z_full = gen_samples(0)
     iters = WORKLOAD["iters"]
     total_steps = args.steps + args.warmup
-    n_s = oracle_sample_size(z_full, iters, target_step_s=max(0.5, 150.0 / max(total_steps, 1)))
+    # each step a bounded sample: the whole run stays within a few minutes
+    n_s = oracle_sample_size(z_full, iters, target_step_s=max(0.2, min(args.cpu_budget, 150.0 / max(total_steps, 1))))
     z = np.ascontiguousarray(z_full[:n_s])
     import oracle
     p = oracle.Params(log2_res=WORKLOAD["log2_res"], kernel_r=WORKLOAD["kernel_r"])
@@ -346,7 +364,8 @@ def run_gpu(args, world, rank, local, pg):
     barrier(pg)
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     ms = sum(step_ms) / len(step_ms)
-    ms_max = max_over_ranks(pg, ms, dev if pg is not None and torch.distributed.get_backend() == "nccl" else None)
+    red_dev = dev if pg is not None and torch.distributed.get_backend() == "nccl" else None
+    ms_max = max_over_ranks(pg, ms, red_dev)
     dc.declutter_sync(ctx)
 
     if args.ncu_run:
@@ -371,8 +390,7 @@ def run_gpu(args, world, rank, local, pg):
         if s >= args.warmup:
             e2e_times.append(t1 - t0)
     clocks.stop()
-    e2e_s = max_over_ranks(pg, sum(e2e_times) / len(e2e_times),
-                           dev if pg is not None and torch.distributed.get_backend() == "nccl" else None)
+    job = combine_ranks(pg, world, n, iters, ms, sum(e2e_times) / len(e2e_times), red_dev)
 
     # per-kernel device times inside the graph: the step is captured as in
     # regularize(); each kernel kind's time is the growth of the step when
@@ -397,9 +415,9 @@ def run_gpu(args, world, rank, local, pg):
                 "algorithmic_bytes_per_launch": algorithmic_bytes(dominant, n, N, info)}
 
     launches_per_step = sum(v["launches"] for v in prof["kernels"].values())
-    value = world * n * iters / (ms_max * 1e-3) / 1e6
-    e2e_value = world * n * iters / e2e_s / 1e6
+    ms_max, value, e2e_value = job["ms_per_step"], job["value"], job["e2e_value"]
 
+    inim = None if args.no_inim_sweep else run_inim_sweep(args, dc, dev, stream, flush)
     batched = None if args.no_batched else run_batched(args, dc, dev, stream, flush, seed_offset=rank)
     surrogate = None if args.surrogate_budget <= 0 else run_surrogate(args, dc, dev)
 
@@ -421,11 +439,80 @@ def run_gpu(args, world, rank, local, pg):
             "roofline": roofline,
             "kernels": kernels,
             "cpu_baseline": cpu,
+            "inim_sweep": inim,
             "batched": batched,
             "surrogate": surrogate,
             "clocks": clocks.summary(),
         }
         print(json.dumps(line), flush=True)
+
+
+def run_inim_sweep(args, dc, dev, stream, flush, reps: int = 15):
+    """Standalone integral images (Sec. 3.1) of uint32 grids of values
+    U{0..255}, 256^2 .. 8192^2: exact uint64 alpha and alpha_t through
+    integral_images_u32 (band aggregates, carries, final pass).  Algorithmic
+    bytes: 4 read + 2 x 8 written per pixel.  L2 flushed before every launch;
+    CUDA events on the context's stream; median of ``reps``."""
+    import torch
+
+    import synth
+    peaks, src = measured_peaks()
+    rows = []
+    for k in range(8, 14):
+        N = 1 << k
+        g = torch.from_numpy(synth.sat_grid(k).view(np.int32)).to(dev)
+        a = torch.empty(N * N, dtype=torch.int64, device=dev)
+        at = torch.empty(N * N, dtype=torch.int64, device=dev)
+        ctx = dc.declutter_create(k, kernel_r=0, device=dev.index, stream=stream)
+        info = dc.declutter_get_info(ctx)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                dc.integral_images_u32(ctx, g, a, at)
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                dc.integral_images_u32(ctx, g, a, at)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        dc.declutter_sync(ctx)
+        dc.declutter_destroy(ctx)
+        us = statistics.median(ts) * 1e3
+        gbs = 20.0 * N * N / (us * 1e-6) / 1e9
+        agg, carry = band_record_bytes(N, info.band_rows, 8)
+        rows.append({"grid": N, "band_rows": info.band_rows, "us": us, "GBps": gbs, "frac": gbs / peaks["hbm_gbs"],
+                     "launches": 3, "record_bytes": 2 * agg + 2 * carry})
+        del g, a, at
+    best = max(rows, key=lambda r: r["frac"])
+    return {"unit": "GB/s", "bytes_per_pixel": 20, "peak": peaks["hbm_gbs"], "peak_source": src,
+            "best_frac": best["frac"], "best_grid": best["grid"], "sizes": rows,
+            "note": "exact uint64 alpha and alpha_t of uint32 grids; L2 flushed before each launch"}
+
+
+def run_ncu_inim(args):
+    """Minimal run for profiler captures of the integral-image kernels."""
+    import torch
+
+    import synth
+    from paper_2408_06513_gb300 import build as dc_build
+    from paper_2408_06513_gb300 import declutter as dc
+    dc_build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    k = args.ncu_inim
+    N = 1 << k
+    g = torch.from_numpy(synth.sat_grid(k).view(np.int32)).to(dev)
+    a = torch.empty(N * N, dtype=torch.int64, device=dev)
+    at = torch.empty(N * N, dtype=torch.int64, device=dev)
+    ctx = dc.declutter_create(k, kernel_r=0, device=0, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup + args.steps):
+            dc.integral_images_u32(ctx, g, a, at)
+    dc.declutter_sync(ctx)
+    dc.declutter_destroy(ctx)
 
 
 def run_batched(args, dc, dev, stream, flush, seed_offset=0):
@@ -590,9 +677,13 @@ def main():
     ap.add_argument("--keep-order", action="store_true", help="iterate in the caller's sample order")
     ap.add_argument("--workload", default="gmm20_512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-batched", action="store_true", help="skip the scatterplot-matrix measurement")
+    ap.add_argument("--no-inim-sweep", action="store_true", help="skip the standalone integral-image sweep")
     ap.add_argument("--surrogate-budget", type=float, default=60.0,
                     help="seconds of surrogate training before its comparison (0 skips it)")
     ap.add_argument("--surrogate-pairs", type=int, default=1500)
+    ap.add_argument("--ncu-inim", type=int, default=0, metavar="LOG2",
+                    help="profiler capture of the standalone integral images of a 2^LOG2 grid: "
+                         "warm-up plus --steps launches, no bench line")
     ap.add_argument("--ncu-run", action="store_true",
                     help="only warm-up and timed steps (for profiler captures); prints no bench line")
     args = ap.parse_args()
@@ -602,7 +693,9 @@ def main():
         args.warmup = 3
     world, rank, local, pg = dist_init()
     try:
-        if args.impl == "reference":
+        if args.ncu_inim:
+            run_ncu_inim(args)
+        elif args.impl == "reference":
             run_reference(args, world, rank)
         else:
             run_gpu(args, world, rank, local, pg)

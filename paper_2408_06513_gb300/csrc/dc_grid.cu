@@ -1328,10 +1328,25 @@ __global__ void __launch_bounds__(1024) carry_kernel(const Acc *__restrict__ agg
     }
     s_sum[g][lx] = s;
     __syncthreads();
+    // exclusive scan over the ng groups of each of the 32 lanes: warp w
+    // scans lanes w, w + ng, ... (one group per warp lane)
+    for (int col = g; col < 32; col += ng) {
+        Sum x;
+        if (lx < ng) x = s_sum[lx][col];
+        else x.zero();
+        Sum inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            Sum y = inc.shfl_up(o);
+            if (lx >= o) inc.add(y);
+        }
+        Sum ex = inc.shfl_up(1);
+        if (lx == 0) ex.zero();
+        if (lx < ng) s_sum[lx][col] = ex;
+    }
+    __syncthreads();
     if (!active) return;
-    Sum pre;
-    pre.zero();
-    for (int q = 0; q < g; ++q) pre.add(s_sum[q][lx]);
+    Sum pre = s_sum[g][lx];
 
     // where lane's value goes in band b's window (or -1)
     auto slot = [&](int b) -> int {
@@ -1373,6 +1388,12 @@ int smooth_smem_bytes(int r)
     return (W * W + TW * W) * (int)sizeof(float);
 }
 
+// Grids from 2048 x 2048 (1024 x 1024 for the exact 64-bit images) use the
+// interleaved kernels; smaller ones (few rows per band, latency-bound) the
+// per-thread-contiguous band_kernel, which measured faster there (512^2
+// float mode: 3.5 vs 4.9 us aggregate, 5.3 vs 5.9 us final pass).
+constexpr int interleaved_min_log2(int mode) { return mode == MODE_GRID64 ? 10 : 11; }
+
 // dynamic shared memory of the interleaved final kernel: the carry windows
 // (and, outside MODE_GRID64, the marginal windows)
 static size_t band2_smem_bytes(int mode, int N, int T)
@@ -1397,11 +1418,9 @@ static cudaError_t allow_band2_smem()
 template <int MODE>
 static cudaError_t allow_band2_smem_all()
 {
-    cudaError_t e = allow_band2_smem<MODE, 32, 1>();
-    if (e == cudaSuccess) e = allow_band2_smem<MODE, 64, 1>();
-    if (e == cudaSuccess) e = allow_band2_smem<MODE, 128, 1>();
-    if (e == cudaSuccess) e = allow_band2_smem<MODE, 256, 1>();
-    if (e == cudaSuccess) e = allow_band2_smem<MODE, 512, 1>();
+    cudaError_t e = allow_band2_smem<MODE, 512, 1>();
+    if constexpr (MODE == MODE_GRID64)
+        if (e == cudaSuccess) e = allow_band2_smem<MODE, 256, 1>();
     if (e == cudaSuccess) e = allow_band2_smem<MODE, 512, 2>();
     if (e == cudaSuccess) e = allow_band2_smem<MODE, 512, 4>();
     return e;
@@ -1489,10 +1508,9 @@ template <int MODE>
 static cudaError_t launch_band2_n(cudaStream_t s, const BandGeom &g, const BandArgs &a, bool final_pass)
 {
     switch (g.log2N) {  // NT = min(512, N / 4) threads, G = N / (4 NT) chunks a thread
-    case 7: return launch_band2<MODE, 32, 1>(s, g, a, final_pass);
-    case 8: return launch_band2<MODE, 64, 1>(s, g, a, final_pass);
-    case 9: return launch_band2<MODE, 128, 1>(s, g, a, final_pass);
-    case 10: return launch_band2<MODE, 256, 1>(s, g, a, final_pass);
+    case 10:
+        if constexpr (MODE == MODE_GRID64) return launch_band2<MODE, 256, 1>(s, g, a, final_pass);
+        return cudaErrorInvalidValue;
     case 11: return launch_band2<MODE, 512, 1>(s, g, a, final_pass);
     case 12: return launch_band2<MODE, 512, 2>(s, g, a, final_pass);
     case 13: return launch_band2<MODE, 512, 4>(s, g, a, final_pass);
@@ -1503,7 +1521,7 @@ static cudaError_t launch_band2_n(cudaStream_t s, const BandGeom &g, const BandA
 template <int MODE, bool FINAL>
 static cudaError_t launch_band_mode(cudaStream_t s, const BandGeom &g, const BandArgs &a)
 {
-    if (g.N >= 128) return launch_band2_n<MODE>(s, g, a, FINAL);
+    if (g.log2N >= interleaved_min_log2(MODE)) return launch_band2_n<MODE>(s, g, a, FINAL);
     switch (g.CPT) {
     case 1: return launch_kernel(band_kernel<MODE, 1, FINAL>, dim3(g.nb), dim3(g.NT), 0, s, a, g.log2N, g.T);
     case 4: return launch_kernel(band_kernel<MODE, 4, FINAL>, dim3(g.nb), dim3(g.NT), 0, s, a, g.log2N, g.T);
@@ -1535,8 +1553,17 @@ cudaError_t launch_band_final(cudaStream_t s, const BandGeom &g, int mode, const
 
 cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const void *agg, void *carry)
 {
-    int ng = (g.nb + kCarryCache - 1) / kCarryCache;  // groups of at most kCarryCache bands
-    ng = ng < 1 ? 1 : (ng > 32 ? 32 : ng);
+    // groups of bands per block (one warp each): as many as keep all blocks
+    // resident at once on 152 SMs of 2048 threads, at most 32 and nb
+    const int nblk = (g.lanes + 31) / 32;
+    int cap = 152 * 64 / nblk;
+    if (cap > 32) cap = 32;
+    if (cap > g.nb) cap = g.nb;
+    int ng = 1;
+    while (2 * ng <= cap) ng *= 2;
+    // but enough groups that each holds at most kCarryCache bands (registers)
+    const int need = (g.nb + kCarryCache - 1) / kCarryCache;
+    if (ng < need) ng = need > 32 ? 32 : need;
     const dim3 blocks((g.lanes + 31) / 32), threads(32 * ng);
     switch (mode) {
     case MODE_COUNT:
