@@ -104,6 +104,91 @@ __global__ void __launch_bounds__(256) smooth_kernel(const uint32_t *__restrict_
     }
 }
 
+// The same smoothing with register sliding windows: each thread computes R
+// consecutive outputs of a column (vertical pass) or of a row (horizontal
+// pass), loading R + 2r values instead of R (2r + 1).  Taps are summed in
+// the same order as smooth_kernel, one fused multiply-add each, so the two
+// kernels give identical results.  TS x TS outputs per CTA; the vertical
+// pass's output rows are padded to an odd stride so that the horizontal
+// pass's lanes (one row each) read conflict-free.
+template <int TS, int R>
+__global__ void __launch_bounds__(256) smooth_win_kernel(const uint32_t *__restrict__ counts,
+                                                         float *__restrict__ dens, int log2N, GaussW w,
+                                                         uint32_t *__restrict__ zero_out)
+{
+    extern __shared__ float s_sm[];
+    const int N = 1 << log2N;
+    const int r = w.r;
+    const int W = TS + 2 * r;
+    const int Wp = W | 1;
+    float *s_in = s_sm;           // W x W
+    float *s_mid = s_sm + W * W;  // TS x Wp
+    const int ox = blockIdx.x * TS, oy = blockIdx.y * TS;
+    const int tid = threadIdx.x;
+    pdl_wait();
+    {
+        const int lane = tid & 31, nwarp = blockDim.x >> 5;
+        for (int yy = tid >> 5; yy < W; yy += nwarp) {
+            const uint32_t *crow = counts + ((size_t)reflect_index(oy + yy - r, N) << log2N);
+            for (int xx = lane; xx < W; xx += 32) s_in[yy * W + xx] = (float)crow[reflect_index(ox + xx - r, N)];
+        }
+    }
+    if (zero_out) {
+        for (int idx = tid; idx < TS * TS / 4; idx += blockDim.x) {
+            const int y = idx / (TS / 4), x4 = idx - y * (TS / 4);
+            *reinterpret_cast<uint4 *>(zero_out + ((size_t)(oy + y) << log2N) + ox + 4 * x4) =
+                make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    __syncthreads();
+    // vertical: s_mid[y][xx] = sum_t g[t] s_in[y + t][xx], lanes along xx
+    for (int item = tid; item < (TS / R) * W; item += blockDim.x) {
+        const int seg = item / W, xx = item - seg * W;
+        const int y0 = seg * R;
+        float acc[R], win[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k + 1 < R; ++k) win[k + 1] = s_in[(y0 + k) * W + xx];
+#pragma unroll R
+        for (int t = 0; t <= 2 * r; ++t) {
+#pragma unroll
+            for (int k = 0; k + 1 < R; ++k) win[k] = win[k + 1];
+            win[R - 1] = s_in[(y0 + t + R - 1) * W + xx];
+            const float g = w.g[t];
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] = fmaf(g, win[k], acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) s_mid[(y0 + k) * Wp + xx] = acc[k];
+    }
+    __syncthreads();
+    // horizontal: out[y][x] = sum_t g[t] s_mid[y][x + t], lanes along y
+    for (int item = tid; item < TS * (TS / R); item += blockDim.x) {
+        const int seg = item / TS, y = item - seg * TS;
+        const int x0 = seg * R;
+        const float *row = s_mid + y * Wp + x0;
+        float acc[R], win[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k + 1 < R; ++k) win[k + 1] = row[k];
+#pragma unroll R
+        for (int t = 0; t <= 2 * r; ++t) {
+#pragma unroll
+            for (int k = 0; k + 1 < R; ++k) win[k] = win[k + 1];
+            win[R - 1] = row[t + R - 1];
+            const float g = w.g[t];
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] = fmaf(g, win[k], acc[k]);
+        }
+        float *o = dens + ((size_t)(oy + y) << log2N) + ox + x0;
+#pragma unroll
+        for (int k = 0; k < R; k += 4)
+            *reinterpret_cast<float4 *>(o + k) = make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
+    }
+}
+
 // ------------------------------------------------------------------------
 // Band kernels.
 // ------------------------------------------------------------------------
@@ -1388,6 +1473,14 @@ int smooth_smem_bytes(int r)
     return (W * W + TW * W) * (int)sizeof(float);
 }
 
+// tile of the sliding-window smoothing: 64 x 64 outputs from 1024 x 1024
+static int smooth_tile(int log2N) { return log2N >= 10 ? 64 : 32; }
+static int smooth_win_smem_bytes(int TS, int r)
+{
+    const int W = TS + 2 * r;
+    return (W * W + TS * (W | 1)) * (int)sizeof(float);
+}
+
 // Grids from 2048 x 2048 (1024 x 1024 for the exact 64-bit images) use the
 // interleaved kernels; smaller ones (few rows per band, latency-bound) the
 // per-thread-contiguous band_kernel, which measured faster there (512^2
@@ -1431,6 +1524,12 @@ cudaError_t prepare_kernels()
     // dynamic shared memory of the smoothing tile for the largest radius
     cudaError_t e = cudaFuncSetAttribute(smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smooth_smem_bytes(64));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(smooth_win_kernel<64, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smooth_win_smem_bytes(64, 64));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(smooth_win_kernel<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smooth_win_smem_bytes(32, 64));
     if (e == cudaSuccess) e = allow_band2_smem_all<MODE_COUNT>();
     if (e == cudaSuccess) e = allow_band2_smem_all<MODE_FLOAT>();
     if (e == cudaSuccess) e = allow_band2_smem_all<MODE_GRID64>();
@@ -1441,7 +1540,15 @@ cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, i
                           uint32_t *zero_out)
 {
     const int N = 1 << log2N;
-    const int TW = N < 32 ? N : 32;
+    if (N >= 32) {
+        const int TS = smooth_tile(log2N);
+        const size_t bytes = (size_t)smooth_win_smem_bytes(TS, w.r);
+        const dim3 grid(N / TS, N / TS);
+        if (TS == 64)
+            return launch_kernel(smooth_win_kernel<64, 8>, grid, dim3(256), bytes, s, counts, dens, log2N, w, zero_out);
+        return launch_kernel(smooth_win_kernel<32, 8>, grid, dim3(256), bytes, s, counts, dens, log2N, w, zero_out);
+    }
+    const int TW = N;
     const int bytes = smooth_smem_bytes(w.r);
     dim3 grid(N / TW, N / TW);
     return launch_kernel(smooth_kernel, grid, dim3(256), (size_t)bytes, s, counts, dens, log2N, w, zero_out);

@@ -109,6 +109,16 @@ __device__ __forceinline__ Moved advect_one(float2 z, const float2 *__restrict__
     return {z, (sj << log2N) + si};
 }
 
+// Position loads that bypass L1 (each float4 is read once).
+__device__ __forceinline__ float4 ldg_stream(const float4 *p)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
 // Splat one sample per lane with warp aggregation: lanes holding the same
 // pixel are merged and their leader adds the group's size.  All 32 lanes
 // must call this together; lanes with valid = false add nothing.
@@ -140,11 +150,24 @@ __global__ void __launch_bounds__(kThreads) advect_kernel(float2 *__restrict__ p
     float4 *pp = reinterpret_cast<float4 *>(pos + head);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int64_t qb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); qb < npairs; qb += 2 * stride) {
+    // the next trip's two pairs are loaded before this trip's gathers
+    int64_t qb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    float4 na = zero4, nb = zero4;
+    if (qb < npairs) {
+        if (qb + lane < npairs) na = ldg_stream(pp + qb + lane);
+        if (qb + lane + stride < npairs) nb = ldg_stream(pp + qb + lane + stride);
+    }
+    for (; qb < npairs; qb += 2 * stride) {
         const int64_t q1 = qb + lane, q2 = q1 + stride;
         const bool v1 = q1 < npairs, v2 = q2 < npairs;
-        const float4 a = v1 ? pp[q1] : zero4;
-        const float4 b = v2 ? pp[q2] : zero4;
+        const float4 a = na, b = nb;
+        const int64_t qn = qb + 2 * stride;
+        na = zero4;
+        nb = zero4;
+        if (qn < npairs) {
+            if (qn + lane < npairs) na = ldg_stream(pp + qn + lane);
+            if (qn + lane + stride < npairs) nb = ldg_stream(pp + qn + lane + stride);
+        }
         const Moved m0 = advect_one(make_float2(a.x, a.y), D, log2N, fN, off, clamp);
         const Moved m1 = advect_one(make_float2(a.z, a.w), D, log2N, fN, off, clamp);
         const Moved m2 = advect_one(make_float2(b.x, b.y), D, log2N, fN, off, clamp);
