@@ -597,7 +597,8 @@ def run_surrogate(args, dc, dev):
     on pairs the plain method generates, within a time budget, then compare
     one surrogate pass (+ plain iterations as fallback) with the plain
     iterations on held-out mixtures of 2M samples, at equal uniformity
-    (Sec. 6.2 bin std / mean)."""
+    (Sec. 6.2 bin std / mean).  The network sees the density and one plain
+    iteration's field and adds a fitted skip kappa * field."""
     import torch
 
     from paper_2408_06513_gb300 import surrogate as SG
@@ -605,20 +606,23 @@ def run_surrogate(args, dc, dev):
     rng = np.random.default_rng(5)
     gen = SG.PairGenerator(log2_res=8, iters=8, kernel_r=2, device=dev.index)
     t0 = time.perf_counter()
-    dens, scales, target = gen.make(args.surrogate_pairs, rng)
-    held = gen.make(32, np.random.default_rng(99))
+    dens, scales, field, target = gen.make(args.surrogate_pairs, rng)
+    hd, hs, hf, ht = gen.make(32, np.random.default_rng(99))
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
     gen.close()
-    sg = dc.surrogate_create(8, 4, 32, max_batch=16, seed=1, device=dev.index)
+    kappa = SG.fit_skip(field, target)
+    sg = dc.surrogate_create(8, 4, 32, max_batch=16, seed=1, device=dev.index, in_channels=3)
+    dc.surrogate_set_skip(sg, kappa)
     ctx = dc.declutter_create(8, kernel_r=2, device=dev.index)
     try:
+        skip_only = SG.field_error(sg, hd, hs, ht, field=hf)
         t0 = time.perf_counter()
         losses = SG.train(sg, dens, scales, target, steps=1_000_000, batch=16, lr=1e-3, rng=rng,
-                          time_budget_s=args.surrogate_budget, log_every=100)
+                          time_budget_s=args.surrogate_budget, log_every=100, field=field)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
-        err = SG.field_error(sg, *held)
+        err = SG.field_error(sg, hd, hs, ht, field=hf)
 
         def wall(fn):
             torch.cuda.synchronize()
@@ -650,7 +654,9 @@ def run_surrogate(args, dc, dev):
                          "ms_plain8": ms_plain8, "ms_surrogate_to_plain8_quality": ms_fb, "fallback_plain_iters": used,
                          "cv_after_fallback": cv_fb})
         avg = lambda k: float(np.mean([r[k] for r in rows]))  # noqa: E731
-        return {"model": "conv encoder-decoder, 4 levels, 32/64/128/256 channels, 3x3, bf16 weights, fp32 accumulation",
+        return {"model": "conv encoder-decoder, 4 levels, 32/64/128/256 channels, 3x3, bf16 weights, fp32 accumulation; "
+                         "input density + one iteration's field, output kappa * field + network",
+                "kappa": kappa, "skip_only_field_rms_px": skip_only["rms_px"],
                 "grid": 256, "target_iterations": 8, "pairs": int(dens.shape[0]), "pair_generation_s": t_gen,
                 "train_s": t_train, "train_steps": losses[-1][0] + 1 if losses else 0, "batch": 16,
                 "loss_first": losses[0][1] if losses else None, "loss_last": losses[-1][1] if losses else None,
@@ -680,7 +686,7 @@ def main():
     ap.add_argument("--no-inim-sweep", action="store_true", help="skip the standalone integral-image sweep")
     ap.add_argument("--surrogate-budget", type=float, default=60.0,
                     help="seconds of surrogate training before its comparison (0 skips it)")
-    ap.add_argument("--surrogate-pairs", type=int, default=1500)
+    ap.add_argument("--surrogate-pairs", type=int, default=4000)
     ap.add_argument("--ncu-inim", type=int, default=0, metavar="LOG2",
                     help="profiler capture of the standalone integral images of a 2^LOG2 grid: "
                          "warm-up plus --steps launches, no bench line")

@@ -273,14 +273,21 @@ dc_status declutter_batch_autotune(dc_batch *batch, float *const *pos_xy, const 
  * l = L-2..0, head (2 outputs); 3x3 convolutions with zero padding, ReLU
  * after every layer but the head, 2x2 average pooling down, nearest
  * upsampling and additive skips up.  Tensors are [batch][y][x][channel].
+ * Inputs: the scaled density, and with in_channels = 3 also the field of
+ * one plain iteration (x, y in pixels), which carries the method's global
+ * integrals past the network's receptive field; the output is then
+ * kappa * field + the network's output (kappa from surrogate_set_skip).
  * ------------------------------------------------------------------------ */
 typedef struct dc_surrogate dc_surrogate;
 
 /* Input and output grids are 2^log2_res square; levels 1..6 with
- * log2_res >= levels + 2; base_channels a multiple of 8 (<= 256); batches of
- * at most max_batch; He-normal initial weights from seed. */
-dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channels, int32_t max_batch,
-                           uint64_t seed, int device, void *cuda_stream, dc_surrogate **out);
+ * log2_res >= levels + 2; base_channels a multiple of 8 (<= 256);
+ * in_channels 1 (density) or 3 (density and one iteration's field); batches
+ * of at most max_batch; He-normal initial weights from seed; kappa 0. */
+dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channels, int32_t in_channels,
+                           int32_t max_batch, uint64_t seed, int device, void *cuda_stream, dc_surrogate **out);
+/* kappa of the output skip kappa * field (in_channels = 3). */
+dc_status surrogate_set_skip(dc_surrogate *sg, float kappa);
 dc_status surrogate_destroy(dc_surrogate *sg);
 
 /* Parameter counts in the unpadded layout used by get/set: for every layer
@@ -295,19 +302,22 @@ dc_status surrogate_get_grads(dc_surrogate *sg, float *gw_host, float *gb_host);
 
 /* density: device float[batch][H][W], multiplied on input by scales[b]
  * (device float[batch], e.g. N^2 / n so that the even layout reads 1; NULL
- * means 1); out: device float[batch][H][W][2] (pixels), or NULL. */
-dc_status surrogate_forward(dc_surrogate *sg, const float *density, const float *scales, int32_t batch,
-                            float *out);
+ * means 1); field: device float[batch][H][W][2] (pixels; required when
+ * in_channels = 3, ignored otherwise); out: device float[batch][H][W][2]
+ * (pixels), or NULL. */
+dc_status surrogate_forward(dc_surrogate *sg, const float *density, const float *scales, const float *field,
+                            int32_t batch, float *out);
 /* Forward + backward for 0.5 * mean((out - target)^2), target device
  * float[batch][H][W][2]; *loss_out (host) after synchronising, if given. */
-dc_status surrogate_loss_grad(dc_surrogate *sg, const float *density, const float *scales, const float *target,
-                              int32_t batch, float *loss_out);
+dc_status surrogate_loss_grad(dc_surrogate *sg, const float *density, const float *scales, const float *field,
+                              const float *target, int32_t batch, float *loss_out);
 /* surrogate_loss_grad followed by one Adam step (beta 0.9 / 0.999). */
-dc_status surrogate_train_step(dc_surrogate *sg, const float *density, const float *scales, const float *target,
-                               int32_t batch, float lr, float *loss_out);
+dc_status surrogate_train_step(dc_surrogate *sg, const float *density, const float *scales, const float *field,
+                               const float *target, int32_t batch, float lr, float *loss_out);
 /* One-shot regularisation of device samples with the surrogate (context in
  * float mode at the surrogate's resolution): predict the composed field from
- * the samples' density, move every sample once by it, then run plain
+ * the samples' density (and, with in_channels = 3, the field of one plain
+ * iteration, computed here), move every sample once by it, then run plain
  * iterations while the Sec. 6.2 bin std / mean exceeds target_cv (at most
  * max_plain_iters).  Returns the plain iterations used and the final ratio.
  * Synchronises. */

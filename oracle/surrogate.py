@@ -12,6 +12,7 @@ Architecture (``levels`` L, base width ``c0``; widths c_l = c0 * 2^l):
                              x = avgpool2(h) (not after the last level)
     decoder, l = L-2 .. 0:   u = relu(conv(upsample2(x)));  x = relu(conv(u + skip_l))
     head:                    out = conv(x)   (2 channels, no activation)
+                             [+ skip * skip_field, a fixed skip of an input field]
 
 conv is a 3x3 cross-correlation with zero padding and a bias; tensors are
 [batch, height, width, channels]; weights are [out, 3, 3, in].  The loss is
@@ -120,8 +121,10 @@ def mse_loss(out, target):
     return 0.5 * float(np.mean(d * d)), d / d.size
 
 
-def forward(P, x, levels: int, round_bf16: bool = True):
-    """Forward pass; returns (output float64, cache for backward)."""
+def forward(P, x, levels: int, round_bf16: bool = True, skip: float = 0.0, skip_field=None):
+    """Forward pass; returns (output float64, cache for backward).  With
+    skip_field ([batch, H, W, 2], not rounded), skip * skip_field is added to
+    the output (it holds no parameters, so backward is unchanged)."""
     r = lambda a: bf16(a, round_bf16)  # noqa: E731
     W = {k: (r(v) if k.endswith(".w") else v) for k, v in P.items()}
     cache = {"x": r(x)}
@@ -147,6 +150,8 @@ def forward(P, x, levels: int, round_bf16: bool = True):
         cache[f"dec{l}c.in"], cache[f"dec{l}c.out"] = s, yc
         h = yc
     out = conv3x3(h, W["head.w"], W["head.b"])
+    if skip_field is not None and skip != 0.0:
+        out = out + skip * np.asarray(skip_field, dtype=np.float64)
     cache["head.in"] = h
     cache["W"] = W
     return out, cache

@@ -53,21 +53,36 @@ __global__ void __launch_bounds__(kThreads) splat_rank_kernel(const float2 *__re
     const float fN = (float)N;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        const int64_t k = base + lane;
-        int pix = -1 - lane;
-        if (k < n) {
-            const float2 z = pos[k];
-            const int i = min((int)(clamp01(z.x) * fN), N - 1);
-            const int j = min((int)(clamp01(z.y) * fN), N - 1);
-            pix = (j << log2N) + i;
+    // kU warp-rows of samples a trip: loads, then the independent atomics
+    constexpr int kU = 4;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += kU * stride) {
+        int pix[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t k = base + u * stride + lane;
+            pix[u] = -1 - lane;
+            if (k < n) {
+                const float2 z = pos[k];
+                const int i = min((int)(clamp01(z.x) * fN), N - 1);
+                const int j = min((int)(clamp01(z.y) * fN), N - 1);
+                pix[u] = (j << log2N) + i;
+            }
         }
-        const unsigned m = __match_any_sync(0xffffffffu, pix);
-        const int leader = __ffs(m) - 1;
-        uint32_t r0 = 0;
-        if (k < n && lane == leader) r0 = atomicAdd(&counts[pix], (uint32_t)__popc(m));
-        r0 = __shfl_sync(0xffffffffu, r0, leader);
-        if (k < n) rank[k] = r0 + __popc(m & ((1u << lane) - 1u));
+        unsigned m[kU];
+        uint32_t r0[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            m[u] = __match_any_sync(0xffffffffu, pix[u]);
+            r0[u] = 0;
+            if (base + u * stride + lane < n && lane == __ffs(m[u]) - 1)
+                r0[u] = atomicAdd(&counts[pix[u]], (uint32_t)__popc(m[u]));
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t k = base + u * stride + lane;
+            const uint32_t lead = __shfl_sync(0xffffffffu, r0[u], __ffs(m[u]) - 1);
+            if (k < n) rank[k] = lead + __popc(m[u] & ((1u << lane) - 1u));
+        }
     }
 }
 

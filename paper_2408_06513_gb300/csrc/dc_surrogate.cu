@@ -156,15 +156,37 @@ cudaError_t run_gemm(cudaStream_t s, const P &p, int splits = 1)
 #define GRID_STRIDE(i, n) for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
                                i += (int64_t)gridDim.x * blockDim.x)
 
-// x[p][0] = bf16(dens[p] * scales[p / HW]) (scales null: 1), channels 1..7 zero
-__global__ void pack_input_kernel(const float *__restrict__ dens, const float *__restrict__ scales, int log2HW,
-                                  int64_t P, bf16 *__restrict__ x)
+// x[p][0] = bf16(dens[p] * scales[p / HW]) (scales null: 1); with field,
+// x[p][1..2] = bf16(field[p][0..1]); the other channels up to 8 zero
+__global__ void pack_input_kernel(const float *__restrict__ dens, const float *__restrict__ scales,
+                                  const float *__restrict__ field, int log2HW, int64_t P, bf16 *__restrict__ x)
 {
     pdl_wait();
     GRID_STRIDE(i, P * 8) {
         const int64_t p = i >> 3;
-        const float sc = scales ? scales[p >> log2HW] : 1.f;
-        x[i] = __float2bfloat16_rn((i & 7) == 0 ? dens[p] * sc : 0.f);
+        const int c = (int)(i & 7);
+        float v = 0.f;
+        if (c == 0) v = dens[p] * (scales ? scales[p >> log2HW] : 1.f);
+        else if (c < 3 && field) v = field[2 * p + (c - 1)];
+        x[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// out[p][c] += kappa * field[p][c]
+__global__ void add_skip_kernel(float *__restrict__ out, const float *__restrict__ field, float kappa, int64_t n)
+{
+    pdl_wait();
+    GRID_STRIDE(i, n) out[i] += kappa * field[i];
+}
+
+// field[p] = disp[p] * N (domain units to pixels)
+__global__ void disp_to_field_kernel(const float2 *__restrict__ disp, int64_t P, float N, float *__restrict__ field)
+{
+    pdl_wait();
+    GRID_STRIDE(p, P) {
+        const float2 d = disp[p];
+        field[2 * p] = d.x * N;
+        field[2 * p + 1] = d.y * N;
     }
 }
 
@@ -351,6 +373,8 @@ dc_status sfail(dc_status st, const char *fmt, ...)
 
 struct dc_surrogate {
     int levels = 4, c0 = 32, log2H = 8, max_batch = 1;
+    int in_channels = 1;
+    float kappa = 0.f;                  // output skip kappa * field
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -367,6 +391,7 @@ struct dc_surrogate {
     float *out = nullptr;
     float *loss = nullptr;
     float *scale1 = nullptr;            // input scale of surrogate_apply
+    float *field1 = nullptr;            // one iteration's field (pixels) in surrogate_apply
     bf16 *ghead = nullptr;
     float *g1 = nullptr, *g2 = nullptr, *g3 = nullptr;  // fp32 gradient scratch (largest tensor)
     std::vector<float *> dskip;
@@ -437,11 +462,12 @@ cudaError_t conv_backward(dc_surrogate *s, const Layer &L, const bf16 *x, const 
     return run_gemm(s->stream, d);
 }
 
-cudaError_t forward_pass(dc_surrogate *s, const float *dens, const float *scales, int B)
+cudaError_t forward_pass(dc_surrogate *s, const float *dens, const float *scales, const float *field, int B)
 {
     const int L = s->levels;
     const int64_t P0 = (int64_t)B << (2 * s->log2H);
-    cudaError_t e = launch_kernel(pack_input_kernel, dim3(eb(P0 * 8)), dim3(256), 0, s->stream, dens, scales,
+    if (s->in_channels < 3) field = nullptr;
+    cudaError_t e = launch_kernel(pack_input_kernel, dim3(eb(P0 * 8)), dim3(256), 0, s->stream, dens, scales, field,
                                   2 * s->log2H, P0, s->xin);
     const bf16 *h = s->xin;
     for (int l = 0; l < L && e == cudaSuccess; ++l) {
@@ -472,6 +498,8 @@ cudaError_t forward_pass(dc_surrogate *s, const float *dens, const float *scales
         h = s->yc[l];
     }
     if (e == cudaSuccess) e = conv_forward(s, s->layers.back(), h, B, nullptr, s->out, 0);
+    if (e == cudaSuccess && field && s->kappa != 0.f)
+        e = launch_kernel(add_skip_kernel, dim3(eb(P0 * 2)), dim3(256), 0, s->stream, s->out, field, s->kappa, P0 * 2);
     return e;
 }
 
@@ -557,11 +585,12 @@ struct SgGuard {
 
 extern "C" {
 
-dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channels, int32_t max_batch, uint64_t seed,
-                           int device, void *cuda_stream, dc_surrogate **out)
+dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channels, int32_t in_channels,
+                           int32_t max_batch, uint64_t seed, int device, void *cuda_stream, dc_surrogate **out)
 {
     if (!out) return sfail(DC_ERR_INVALID_ARG, "null out");
     *out = nullptr;
+    if (in_channels != 1 && in_channels != 3) return sfail(DC_ERR_INVALID_ARG, "in_channels = %d", in_channels);
     if (levels < 1 || levels > 6 || base_channels < 8 || base_channels > 256 || (base_channels & 7))
         return sfail(DC_ERR_INVALID_ARG, "levels = %d, base_channels = %d", levels, base_channels);
     if (log2_res < levels + 2 || log2_res > 11) return sfail(DC_ERR_INVALID_ARG, "log2_res = %d", log2_res);
@@ -570,6 +599,7 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
     dc_surrogate *s = new dc_surrogate();
     s->levels = levels;
     s->c0 = base_channels;
+    s->in_channels = in_channels;
     s->log2H = log2_res;
     s->max_batch = max_batch;
     s->device = device;
@@ -600,7 +630,7 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
         s->nb += L.cout_p;
         s->layers.push_back(L);
     };
-    int cin = 1;
+    int cin = in_channels;
     for (int l = 0; l < levels; ++l) {
         add("enc" + std::to_string(l) + "a", ch[l], cin, log2_res - l);
         add("enc" + std::to_string(l) + "b", ch[l], ch[l], log2_res - l);
@@ -675,6 +705,7 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
     s->out = (float *)A(P0 * 2 * 4);
     s->loss = (float *)A(4);
     s->scale1 = (float *)A(4);
+    s->field1 = (float *)A(((size_t)8 << (2 * log2_res)));
     s->ghead = (bf16 *)A(P0 * 8 * 2);
     s->g1 = (float *)A(maxe * 4);
     s->g2 = (float *)A(maxe * 4);
@@ -779,25 +810,36 @@ dc_status surrogate_set_params(dc_surrogate *s, const float *w_host, const float
     return DC_OK;
 }
 
-dc_status surrogate_forward(dc_surrogate *s, const float *density, const float *scales, int32_t batch, float *out)
+dc_status surrogate_set_skip(dc_surrogate *s, float kappa)
+{
+    if (dc_status st = check_sg(s)) return st;
+    if (!(kappa == kappa)) return sfail(DC_ERR_INVALID_ARG, "kappa is NaN");
+    s->kappa = kappa;
+    return DC_OK;
+}
+
+dc_status surrogate_forward(dc_surrogate *s, const float *density, const float *scales, const float *field,
+                            int32_t batch, float *out)
 {
     if (dc_status st = check_sg(s)) return st;
     if (!density || batch < 1 || batch > s->max_batch) return sfail(DC_ERR_INVALID_ARG, "density / batch");
+    if (s->in_channels == 3 && !field) return sfail(DC_ERR_INVALID_ARG, "field required (in_channels = 3)");
     SgGuard guard(s->device);
-    SG_CUDA(forward_pass(s, density, scales, batch));
+    SG_CUDA(forward_pass(s, density, scales, field, batch));
     if (out)
         SG_CUDA(cudaMemcpyAsync(out, s->out, sizeof(float) * 2 * ((size_t)batch << (2 * s->log2H)),
                                 cudaMemcpyDeviceToDevice, s->stream));
     return DC_OK;
 }
 
-dc_status surrogate_loss_grad(dc_surrogate *s, const float *density, const float *scales, const float *target,
-                              int32_t batch, float *loss_out)
+dc_status surrogate_loss_grad(dc_surrogate *s, const float *density, const float *scales, const float *field,
+                              const float *target, int32_t batch, float *loss_out)
 {
     if (dc_status st = check_sg(s)) return st;
     if (!density || !target || batch < 1 || batch > s->max_batch) return sfail(DC_ERR_INVALID_ARG, "arguments");
+    if (s->in_channels == 3 && !field) return sfail(DC_ERR_INVALID_ARG, "field required (in_channels = 3)");
     SgGuard guard(s->device);
-    SG_CUDA(forward_pass(s, density, scales, batch));
+    SG_CUDA(forward_pass(s, density, scales, field, batch));
     SG_CUDA(backward_pass(s, target, batch));
     if (loss_out) {
         SG_CUDA(cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToHost, s->stream));
@@ -806,10 +848,10 @@ dc_status surrogate_loss_grad(dc_surrogate *s, const float *density, const float
     return DC_OK;
 }
 
-dc_status surrogate_train_step(dc_surrogate *s, const float *density, const float *scales, const float *target,
-                               int32_t batch, float lr, float *loss_out)
+dc_status surrogate_train_step(dc_surrogate *s, const float *density, const float *scales, const float *field,
+                               const float *target, int32_t batch, float lr, float *loss_out)
 {
-    if (dc_status st = surrogate_loss_grad(s, density, scales, target, batch, nullptr)) return st;
+    if (dc_status st = surrogate_loss_grad(s, density, scales, field, target, batch, nullptr)) return st;
     SgGuard guard(s->device);
     s->step += 1;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -838,11 +880,17 @@ dc_status surrogate_apply(dc_ctx *ctx, dc_surrogate *s, float *pos_xy, int64_t n
     if (ctx->mode != MODE_FLOAT) return sfail(DC_ERR_INVALID_ARG, "the surrogate takes a smoothed density");
     SgGuard guard(s->device);
     if (dc_status st = splat_density(ctx, pos_xy, n, nullptr, nullptr)) return st;
-    SG_CUDA(cudaStreamSynchronize(ctx->stream));
     const int N = 1 << s->log2H;
+    if (s->in_channels == 3) {
+        // the field of one plain iteration, in pixels
+        if (dc_status st = displacement_field(ctx, nullptr)) return st;
+        SG_CUDA(launch_kernel(disp_to_field_kernel, dim3(eb((int64_t)N * N)), dim3(256), 0, ctx->stream,
+                              (const float2 *)ctx->disp, (int64_t)N * N, (float)N, s->field1));
+    }
+    SG_CUDA(cudaStreamSynchronize(ctx->stream));
     const float scale = (float)((double)N * N / (double)n);
     SG_CUDA(cudaMemcpyAsync(s->scale1, &scale, sizeof(float), cudaMemcpyHostToDevice, s->stream));
-    SG_CUDA(forward_pass(s, ctx->dens, s->scale1, 1));
+    SG_CUDA(forward_pass(s, ctx->dens, s->scale1, s->in_channels == 3 ? s->field1 : nullptr, 1));
     SG_CUDA(launch_kernel(field_to_disp_kernel, dim3(eb((int64_t)N * N)), dim3(256), 0, s->stream,
                           (const float *)s->out, (int64_t)N * N, 1.0f / N, ctx->disp));
     SG_CUDA(cudaStreamSynchronize(s->stream));

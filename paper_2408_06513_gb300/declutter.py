@@ -32,7 +32,7 @@ __all__ = [
     "declutter_batch_destroy", "declutter_batch_regularize", "declutter_batch_sync",
     "declutter_autotune_band_rows", "declutter_batch_autotune", "regularize_tracers", "Surrogate",
     "surrogate_create", "surrogate_destroy", "surrogate_num_params", "surrogate_get_params", "surrogate_set_params",
-    "surrogate_get_grads", "surrogate_forward", "surrogate_loss_grad", "surrogate_train_step", "surrogate_apply",
+    "surrogate_get_grads", "surrogate_set_skip", "surrogate_forward", "surrogate_loss_grad", "surrogate_train_step", "surrogate_apply",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -109,15 +109,16 @@ _SIGS = [
     ("declutter_batch_autotune", ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P]),
     ("regularize_tracers", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32]),
     ("surrogate_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                        ctypes.c_uint64, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+                                        ctypes.c_int32, ctypes.c_uint64, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    ("surrogate_set_skip", ctypes.c_int, [_P, ctypes.c_float]),
     ("surrogate_destroy", ctypes.c_int, [_P]),
     ("surrogate_num_params", ctypes.c_int, [_P, _P, _P]),
     ("surrogate_get_params", ctypes.c_int, [_P, _P, _P]),
     ("surrogate_set_params", ctypes.c_int, [_P, _P, _P]),
     ("surrogate_get_grads", ctypes.c_int, [_P, _P, _P]),
-    ("surrogate_forward", ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P]),
-    ("surrogate_loss_grad", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, _P]),
-    ("surrogate_train_step", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_float, _P]),
+    ("surrogate_forward", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, _P]),
+    ("surrogate_loss_grad", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32, _P]),
+    ("surrogate_train_step", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_float, _P]),
     ("surrogate_apply", ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_int32, _P, _P]),
     ("declutter_kernel_name", ctypes.c_char_p, [ctypes.c_int32]),
     ("declutter_status_string", ctypes.c_char_p, [ctypes.c_int]),
@@ -498,6 +499,7 @@ class Surrogate:
     base_channels: int
     max_batch: int
     device: int
+    in_channels: int = 1
 
     def __enter__(self):
         return self
@@ -507,15 +509,20 @@ class Surrogate:
 
 
 def surrogate_create(log2_res: int, levels: int = 4, base_channels: int = 32, max_batch: int = 16, seed: int = 0,
-                     device: int | None = None, stream=None) -> Surrogate:
+                     device: int | None = None, stream=None, in_channels: int = 1) -> Surrogate:
+    """``in_channels``: 1 (density) or 3 (density and one plain iteration's field)."""
     import torch
     if device is None:
         device = torch.cuda.current_device()
     h = ctypes.c_void_p()
-    _check(load_library().surrogate_create(int(log2_res), int(levels), int(base_channels), int(max_batch), int(seed),
-                                           int(device), _stream_ptr(stream, device), ctypes.byref(h)),
-           "surrogate_create")
-    return Surrogate(h, int(log2_res), int(levels), int(base_channels), int(max_batch), int(device))
+    _check(load_library().surrogate_create(int(log2_res), int(levels), int(base_channels), int(in_channels),
+                                           int(max_batch), int(seed), int(device), _stream_ptr(stream, device),
+                                           ctypes.byref(h)), "surrogate_create")
+    return Surrogate(h, int(log2_res), int(levels), int(base_channels), int(max_batch), int(device), int(in_channels))
+
+
+def surrogate_set_skip(sg: Surrogate, kappa: float) -> None:
+    _check(load_library().surrogate_set_skip(sg.handle, float(kappa)), "surrogate_set_skip")
 
 
 def surrogate_destroy(sg: Surrogate) -> None:
@@ -567,33 +574,40 @@ def _scales_arg(scales, batch):
     return _ptr(scales, torch.float32, batch, "scales")
 
 
-def surrogate_forward(sg: Surrogate, density, scales=None, out=None) -> None:
-    """``density``: CUDA float32 [B, H, W]; ``scales``: CUDA float32 [B] or None."""
+def _field_arg(field, B, H):
+    return _grid_arg(field, B, H, 2, "field") if field is not None else None
+
+
+def surrogate_forward(sg: Surrogate, density, scales=None, out=None, field=None) -> None:
+    """``density``: CUDA float32 [B, H, W]; ``scales``: CUDA float32 [B] or None;
+    ``field``: CUDA float32 [B, H, W, 2] (pixels), required with in_channels = 3."""
     B = density.shape[0]
     H = 1 << sg.log2_res
     _check(load_library().surrogate_forward(sg.handle, _grid_arg(density, B, H, 1, "density"), _scales_arg(scales, B),
-                                            B, _grid_arg(out, B, H, 2, "out") if out is not None else None),
+                                            _field_arg(field, B, H), B,
+                                            _grid_arg(out, B, H, 2, "out") if out is not None else None),
            "surrogate_forward")
 
 
-def surrogate_loss_grad(sg: Surrogate, density, scales, target) -> float:
+def surrogate_loss_grad(sg: Surrogate, density, scales, target, field=None) -> float:
     B = density.shape[0]
     H = 1 << sg.log2_res
     loss = ctypes.c_float()
     _check(load_library().surrogate_loss_grad(sg.handle, _grid_arg(density, B, H, 1, "density"),
-                                              _scales_arg(scales, B), _grid_arg(target, B, H, 2, "target"), B,
-                                              ctypes.byref(loss)), "surrogate_loss_grad")
+                                              _scales_arg(scales, B), _field_arg(field, B, H),
+                                              _grid_arg(target, B, H, 2, "target"), B, ctypes.byref(loss)),
+           "surrogate_loss_grad")
     return float(loss.value)
 
 
-def surrogate_train_step(sg: Surrogate, density, scales, target, lr: float, want_loss: bool = True):
+def surrogate_train_step(sg: Surrogate, density, scales, target, lr: float, want_loss: bool = True, field=None):
     B = density.shape[0]
     H = 1 << sg.log2_res
     loss = ctypes.c_float()
     _check(load_library().surrogate_train_step(sg.handle, _grid_arg(density, B, H, 1, "density"),
-                                               _scales_arg(scales, B), _grid_arg(target, B, H, 2, "target"), B,
-                                               float(lr), ctypes.byref(loss) if want_loss else None),
-           "surrogate_train_step")
+                                               _scales_arg(scales, B), _field_arg(field, B, H),
+                                               _grid_arg(target, B, H, 2, "target"), B, float(lr),
+                                               ctypes.byref(loss) if want_loss else None), "surrogate_train_step")
     return float(loss.value) if want_loss else None
 
 

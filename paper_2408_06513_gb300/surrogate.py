@@ -6,8 +6,14 @@ density of the samples (``splat_density``) and the target is the displacement
 field composed over ``iters`` plain iterations, obtained by moving the pixel
 nodes as massless tracers through the same iterations
 (``regularize_tracers``): target = (final - initial node positions) * N, in
-pixels.  Every step of the method and of the network runs in the CUDA
-library; PyTorch only holds device memory and draws the random samples.
+pixels.  With a 3-channel network the input also holds the field of one
+plain iteration (``displacement_field``, in pixels): the displacement is a
+function of global integrals of the density, which a convolutional network
+of limited receptive field cannot see, while one iteration's field carries
+them; the network then learns the composed field as a skip kappa * field
+(kappa fitted by least squares, ``fit_skip``) plus a correction.  Every step
+of the method and of the network runs in the CUDA library; PyTorch only holds
+device memory, draws the random samples and fits the one scalar kappa.
 """
 
 from __future__ import annotations
@@ -61,9 +67,12 @@ class PairGenerator:
         dc.declutter_destroy(self.ctx)
 
     def make(self, count: int, rng: np.random.Generator, n_range=(10_000, 2_000_000), comps=(2, 30)):
+        """Returns (density [P,N,N], scales [P], field [P,N,N,2], target [P,N,N,2]):
+        field = one plain iteration's displacement, target = the composed one (pixels)."""
         import torch
         N = self.N
         dens = torch.empty(count, N, N, device=self.device)
+        field = torch.empty(count, N, N, 2, device=self.device)
         target = torch.empty(count, N, N, 2, device=self.device)
         scales = torch.empty(count, device=self.device)
         for k in range(count):
@@ -71,27 +80,40 @@ class PairGenerator:
             K = int(rng.integers(comps[0], comps[1] + 1))
             pos = gmm_samples(n, K, rng, self.device)
             dc.splat_density(self.ctx, pos, density_out=dens[k].view(-1))
+            dc.displacement_field(self.ctx, field[k].view(-1))
+            field[k] *= N
             tr = self.nodes.clone()
             dc.regularize_tracers(self.ctx, pos, tr, self.iters)
             target[k] = ((tr - self.nodes) * N).view(N, N, 2)
             scales[k] = float(N * N) / n
         dc.declutter_sync(self.ctx)
-        return dens, scales, target
+        return dens, scales, field, target
+
+
+def fit_skip(field, target) -> float:
+    """Least-squares kappa of target ~ kappa * field over all pairs."""
+    f = field.double()
+    return float((target.double() * f).sum() / (f * f).sum().clamp_min(1e-30))
 
 
 def train(sg, dens, scales, target, steps: int, batch: int, lr: float, rng: np.random.Generator,
-          time_budget_s: float | None = None, log_every: int = 0):
-    """Adam on random mini-batches of the given pairs (cosine learning-rate decay)."""
+          time_budget_s: float | None = None, log_every: int = 0, field=None):
+    """Adam on random mini-batches of the given pairs, cosine learning-rate
+    decay over the steps or, with a time budget, over the budget."""
     import torch
     count = dens.shape[0]
     losses = []
     t0 = time.perf_counter()
     for s in range(steps):
         idx = torch.from_numpy(rng.choice(count, size=batch, replace=False)).to(dens.device)
-        lr_s = lr * 0.5 * (1 + math.cos(math.pi * s / max(steps, 1)))
+        frac = s / max(steps, 1)
+        if time_budget_s:
+            frac = max(frac, (time.perf_counter() - t0) / time_budget_s)
+        lr_s = lr * 0.5 * (1 + math.cos(math.pi * min(frac, 1.0)))
         want = log_every and (s % log_every == 0 or s == steps - 1)
         loss = dc.surrogate_train_step(sg, dens[idx].contiguous(), scales[idx].contiguous(),
-                                       target[idx].contiguous(), lr_s, want_loss=bool(want))
+                                       target[idx].contiguous(), lr_s, want_loss=bool(want),
+                                       field=field[idx].contiguous() if field is not None else None)
         if want:
             losses.append((s, loss))
         if time_budget_s is not None and time.perf_counter() - t0 > time_budget_s:
@@ -99,7 +121,7 @@ def train(sg, dens, scales, target, steps: int, batch: int, lr: float, rng: np.r
     return losses
 
 
-def field_error(sg, dens, scales, target, batch: int = 8):
+def field_error(sg, dens, scales, target, batch: int = 8, field=None):
     """RMS and mean-abs error (pixels) of the predicted composed displacement."""
     import torch
     se, ae, cnt = 0.0, 0.0, 0
@@ -107,7 +129,8 @@ def field_error(sg, dens, scales, target, batch: int = 8):
     for b0 in range(0, dens.shape[0], batch):
         b1 = min(dens.shape[0], b0 + batch)
         o = out[: b1 - b0]
-        dc.surrogate_forward(sg, dens[b0:b1].contiguous(), scales[b0:b1].contiguous(), o)
+        dc.surrogate_forward(sg, dens[b0:b1].contiguous(), scales[b0:b1].contiguous(), o,
+                             field=field[b0:b1].contiguous() if field is not None else None)
         d = (o - target[b0:b1]).double()
         se += float((d * d).sum())
         ae += float(d.abs().sum())

@@ -43,19 +43,22 @@ def test_pool_upsample_adjoint():
     assert abs(np.sum(S.avgpool2(z) * x) - np.sum(z * S.avgpool2_backward(x))) < 1e-10
 
 
-@pytest.mark.parametrize("levels", [2, 3])
-def test_backward_matches_finite_differences(levels):
+@pytest.mark.parametrize("levels,c_in,skip", [(2, 1, 0.0), (3, 1, 0.0), (2, 3, 2.5)])
+def test_backward_matches_finite_differences(levels, c_in, skip):
+    # with three input channels (density and a field) and the output skip
+    # skip * field, which holds no parameters: the same gradients must hold
     rng = np.random.default_rng(3 + levels)
-    P = S.init_params(levels, 4, seed=levels)
+    P = S.init_params(levels, 4, seed=levels, c_in=c_in)
     H = 8
-    x = rng.random((2, H, H, 1))
+    x = rng.random((2, H, H, c_in))
+    f = x[..., 1:3] if c_in == 3 else None
     t = rng.normal(size=(2, H, H, 2))
 
     def loss(PP):
-        out, _ = S.forward(PP, x, levels, round_bf16=False)
+        out, _ = S.forward(PP, x, levels, round_bf16=False, skip=skip, skip_field=f)
         return S.mse_loss(out, t)[0]
 
-    out, cache = S.forward(P, x, levels, round_bf16=False)
+    out, cache = S.forward(P, x, levels, round_bf16=False, skip=skip, skip_field=f)
     _, dout = S.mse_loss(out, t)
     G = S.backward(cache, dout, levels, round_bf16=False)
     eps = 1e-6
