@@ -2,7 +2,8 @@
 // network (forward, backward-data, weight gradient).
 //
 // C[m][n] = sum_k A[m][k] B[k][n], FP32 accumulation, mma.sync m16n8k16 with
-// bf16 operands.  CTA tile 64 x 64 x 32, 4 warps (2 x 2), warp tile 32 x 32.
+// bf16 operands.  CTA tile 64 x TN x 32, 4 warps: TN = 64 as 2 x 2 warps of
+// 32 x 32, TN = 32 (narrow layers) as 4 x 1 warps of 16 x 32.
 // Operands are staged into shared memory in 16-byte chunks of 8 bf16 by
 // cp.async (zero-filled where the problem's loader returns null, e.g. the
 // zero padding of the convolution), double-buffered along k.  Each operand is
@@ -68,20 +69,22 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
 //   const void *base() const;   // any mapped global address (zero-fill source)
 //   void epilogue(int m, int n, float v0, float v1) const;  // C[m][n], C[m][n+1]
 //   k range of a CTA: [k_begin, k_end) from blockIdx.z (split-K)
-template <class P>
+template <class P, int TN = BN>
 __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(P p, int k_per_split)
 {
+    static_assert(TN == 64 || TN == 32, "tile width");
+    constexpr int MI = TN == 64 ? 2 : 1;  // m16 blocks a warp
     // stage buffers: A and B, two stages each
     constexpr int A_ROWS = P::ALAYOUT == K_CONTIG ? BM : BK;
     constexpr int A_COLS = P::ALAYOUT == K_CONTIG ? BK : BM;
-    constexpr int B_ROWS = P::BLAYOUT == K_CONTIG ? BN : BK;
-    constexpr int B_COLS = P::BLAYOUT == K_CONTIG ? BK : BN;
+    constexpr int B_ROWS = P::BLAYOUT == K_CONTIG ? TN : BK;
+    constexpr int B_COLS = P::BLAYOUT == K_CONTIG ? BK : TN;
     __shared__ __align__(16) __nv_bfloat16 sA[2][A_ROWS][A_COLS + PAD];
     __shared__ __align__(16) __nv_bfloat16 sB[2][B_ROWS][B_COLS + PAD];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int wm = TN == 64 ? (warp >> 1) * 32 : warp * 16, wn = TN == 64 ? (warp & 1) * 32 : 0;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * TN;
     const int k_begin = blockIdx.z * k_per_split;
     const int k_end = min(p.K, k_begin + k_per_split);
     if (k_begin >= k_end) return;
@@ -102,14 +105,15 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(P p, int k_per_split
             }
         }
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < TN / 32; ++i) {
             const int c = tid + i * GEMM_THREADS;
             if constexpr (P::BLAYOUT == K_CONTIG) {
                 const int r = c >> 2, kc = (c & 3) * 8;
                 const int n = n0 + r, k = k0 + kc;
                 cp_async16(&sB[buf][r][kc], (n < p.N && k < k_end) ? p.b_chunk(k, n) : nullptr, p.base());
             } else {
-                const int r = c >> 3, nc = (c & 7) * 8;
+                constexpr int CPR = TN / 8;  // 16-byte chunks a row
+                const int r = c / CPR, nc = (c % CPR) * 8;
                 const int k = k0 + r, n = n0 + nc;
                 cp_async16(&sB[buf][r][nc], (n < p.N && k < k_end) ? p.b_chunk(k, n) : nullptr, p.base());
             }
@@ -117,9 +121,9 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(P p, int k_per_split
         cp_async_commit();
     };
 
-    float acc[2][4][4];
+    float acc[MI][4][4];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < MI; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -138,9 +142,9 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(P p, int k_per_split
         __syncthreads();
 #pragma unroll
         for (int ks = 0; ks < BK; ks += 16) {
-            unsigned af[2][4];
+            unsigned af[MI][4];
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
+            for (int i = 0; i < MI; ++i) {
                 const int mb = wm + i * 16;
                 const int mi = lane >> 3, rr = lane & 7;
                 if constexpr (P::ALAYOUT == K_CONTIG) {
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(P p, int k_per_split
                 bf[2 * jj + 1][1] = r4[3];
             }
 #pragma unroll
-            for (int i = 0; i < 2; ++i)
+            for (int i = 0; i < MI; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j][0], bf[j][1]);
         }
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(P p, int k_per_split
 
     const int gid = lane >> 2, tig = lane & 3;
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < MI; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int m = m0 + wm + i * 16 + gid;

@@ -44,17 +44,57 @@ int round8(int c) { return (c + 7) & ~7; }
 // ------------------------------------------------------------------------
 // Convolution problems for the implicit GEMM
 // ------------------------------------------------------------------------
+// Input pixel (yy, xx) of a 2^log2H grid; with up, the input is stored at
+// half resolution and read through nearest 2x upsampling.
+__device__ __forceinline__ const bf16 *conv_in(const bf16 *X, int b, int yy, int xx, int log2H, int up, int cin_p,
+                                               int ci)
+{
+    const int lg = log2H - up;
+    yy >>= up;
+    xx >>= up;
+    return X + ((((size_t)b << lg) + yy) << lg) * cin_p + (size_t)xx * cin_p + ci;
+}
+
+// Epilogue of a convolution output pair (n, n + 1) of row m: bias, ReLU,
+// bf16 store, the decoder's skip sum S = bf16(Y + skip), fp32 head output.
+struct ConvOut {
+    int cout_p, out_ch, relu;
+    const float *bias;
+    bf16 *Y;            // bf16 output [M][cout_p] or null
+    const bf16 *skip;   // with S: S = bf16(bf16(out) + skip)
+    bf16 *S;
+    float *Yf;          // fp32 output [M][out_ch] or null
+    __device__ void store(int m, int n, float v0, float v1) const
+    {
+        v0 += bias[n];
+        v1 += bias[n + 1];
+        if (relu) {
+            v0 = fmaxf(v0, 0.f);
+            v1 = fmaxf(v1, 0.f);
+        }
+        const __nv_bfloat162 y = __floats2bfloat162_rn(v0, v1);
+        if (Y) *reinterpret_cast<__nv_bfloat162 *>(Y + (size_t)m * cout_p + n) = y;
+        if (S) {
+            const float2 a = __bfloat1622float2(y);
+            const float2 k = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(skip + (size_t)m * cout_p + n));
+            *reinterpret_cast<__nv_bfloat162 *>(S + (size_t)m * cout_p + n) = __floats2bfloat162_rn(a.x + k.x, a.y + k.y);
+        }
+        if (Yf) {
+            if (n < out_ch) Yf[(size_t)m * out_ch + n] = v0;
+            if (n + 1 < out_ch) Yf[(size_t)m * out_ch + n + 1] = v1;
+        }
+    }
+};
+
 struct ConvFwd {
     static constexpr int ALAYOUT = K_CONTIG, BLAYOUT = K_CONTIG;
     int M, N, K;
     int log2H, cin_p, cout_p;
+    int up;         // input at half resolution, upsampled on the fly
     const bf16 *X;
     const bf16 *W;
-    const float *bias;
-    bf16 *Y;        // bf16 output [M][cout_p] or null
-    float *Yf;      // fp32 output [M][out_ch] or null
-    int out_ch;
-    int relu;
+    ConvOut out;
+    float *acc;     // split-K: fp32 partial sums [M][cout_p] (atomic), epilogue later
     __device__ const void *base() const { return W; }
     __device__ const void *a_chunk(int m, int k) const
     {
@@ -64,21 +104,16 @@ struct ConvFwd {
         const int x = m & (H - 1), y = (m >> log2H) & (H - 1), b = m >> (2 * log2H);
         const int yy = y + dy - 1, xx = x + dx - 1;
         if (yy < 0 || yy >= H || xx < 0 || xx >= H) return nullptr;
-        return X + ((((size_t)b << log2H) + yy) << log2H) * cin_p + (size_t)xx * cin_p + ci;
+        return conv_in(X, b, yy, xx, log2H, up, cin_p, ci);
     }
     __device__ const void *b_chunk(int k, int n) const { return W + (size_t)n * K + k; }
     __device__ void epilogue(int m, int n, float v0, float v1) const
     {
-        v0 += bias[n];
-        v1 += bias[n + 1];
-        if (relu) {
-            v0 = fmaxf(v0, 0.f);
-            v1 = fmaxf(v1, 0.f);
-        }
-        if (Y) *reinterpret_cast<__nv_bfloat162 *>(Y + (size_t)m * cout_p + n) = __floats2bfloat162_rn(v0, v1);
-        if (Yf) {
-            if (n < out_ch) Yf[(size_t)m * out_ch + n] = v0;
-            if (n + 1 < out_ch) Yf[(size_t)m * out_ch + n + 1] = v1;
+        if (acc) {
+            atomicAdd(&acc[(size_t)m * cout_p + n], v0);
+            atomicAdd(&acc[(size_t)m * cout_p + n + 1], v1);
+        } else {
+            out.store(m, n, v0, v1);
         }
     }
 };
@@ -118,6 +153,7 @@ struct ConvWgrad {
     static constexpr int ALAYOUT = MN_CONTIG, BLAYOUT = MN_CONTIG;
     int M, N, K;
     int log2H, cin_p, cout_p;
+    int up;         // X at half resolution, read upsampled
     const bf16 *dZ;
     const bf16 *X;
     float *dW;  // fp32 [cout_p][9 * cin_p]
@@ -131,7 +167,7 @@ struct ConvWgrad {
         const int x = k & (H - 1), y = (k >> log2H) & (H - 1), b = k >> (2 * log2H);
         const int yy = y + dy - 1, xx = x + dx - 1;
         if (yy < 0 || yy >= H || xx < 0 || xx >= H) return nullptr;
-        return X + ((((size_t)b << log2H) + yy) << log2H) * cin_p + (size_t)xx * cin_p + ci;
+        return conv_in(X, b, yy, xx, log2H, up, cin_p, ci);
     }
     __device__ void epilogue(int m, int n, float v0, float v1) const
     {
@@ -146,8 +182,12 @@ cudaError_t run_gemm(cudaStream_t s, const P &p, int splits = 1)
     int kps = (p.K + splits - 1) / splits;
     kps = (kps + BK - 1) / BK * BK;
     splits = (p.K + kps - 1) / kps;
+    if (p.N <= 32) {  // narrow layers: 64 x 32 tiles
+        dim3 grid((p.M + BM - 1) / BM, (p.N + 31) / 32, splits);
+        return launch_kernel(gemm_kernel<P, 32>, grid, dim3(GEMM_THREADS), 0, s, p, kps);
+    }
     dim3 grid((p.M + BM - 1) / BM, (p.N + BN - 1) / BN, splits);
-    return launch_kernel(gemm_kernel<P>, grid, dim3(GEMM_THREADS), 0, s, p, kps);
+    return launch_kernel(gemm_kernel<P, BN>, grid, dim3(GEMM_THREADS), 0, s, p, kps);
 }
 
 // ------------------------------------------------------------------------
@@ -171,6 +211,19 @@ __global__ void pack_input_kernel(const float *__restrict__ dens, const float *_
         x[i] = __float2bfloat16_rn(v);
     }
 }
+
+// split-K epilogue: ConvOut of the summed partials, pairs of columns
+__global__ void conv_finalize_kernel(const float *__restrict__ acc, int64_t M, int cout_p, ConvOut o)
+{
+    pdl_wait();
+    GRID_STRIDE(i, M * (cout_p / 2)) {
+        const int64_t m = i / (cout_p / 2);
+        const int n = 2 * (int)(i - m * (cout_p / 2));
+        o.store((int)m, n, acc[m * cout_p + n], acc[m * cout_p + n + 1]);
+    }
+}
+
+__global__ void set_value_kernel(float *p, float v) { *p = v; }
 
 // out[p][c] += kappa * field[p][c]
 __global__ void add_skip_kernel(float *__restrict__ out, const float *__restrict__ field, float kappa, int64_t n)
@@ -206,27 +259,6 @@ __global__ void avgpool_kernel(const bf16 *__restrict__ in, int log2H_out, int C
                         __bfloat162float(in[base + (int64_t)Hi * C]) + __bfloat162float(in[base + (int64_t)Hi * C + C]);
         out[i] = __float2bfloat16_rn(0.25f * s);
     }
-}
-
-// out (2H) = nearest upsampling of in (H)
-__global__ void upsample_kernel(const bf16 *__restrict__ in, int log2H_out, int C, int64_t total, bf16 *__restrict__ out)
-{
-    pdl_wait();
-    GRID_STRIDE(i, total) {
-        const int c = (int)(i % C);
-        const int64_t p = i / C;
-        const int Ho = 1 << log2H_out;
-        const int x = (int)(p & (Ho - 1)), y = (int)((p >> log2H_out) & (Ho - 1));
-        const int64_t b = p >> (2 * log2H_out);
-        const int Hi = Ho / 2;
-        out[i] = in[((b * Hi + y / 2) * Hi + x / 2) * C + c];
-    }
-}
-
-__global__ void add_bf16_kernel(const bf16 *__restrict__ a, const bf16 *__restrict__ b, int64_t n, bf16 *__restrict__ out)
-{
-    pdl_wait();
-    GRID_STRIDE(i, n) out[i] = __float2bfloat16_rn(__bfloat162float(a[i]) + __bfloat162float(b[i]));
 }
 
 // loss += 0.5 (out - t)^2 over the 2 logical channels; g (8 channels) = bf16((out - t) / count)
@@ -378,6 +410,12 @@ struct dc_surrogate {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaEvent_t ev[2] = {nullptr, nullptr};  // stream ordering with a context in surrogate_apply
+    // surrogate_apply's forward pass + field conversion as one CUDA graph,
+    // captured on a private stream for the context buffers it was made for
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t apply_exec = nullptr;
+    const void *apply_key[2] = {nullptr, nullptr};
     std::vector<Layer> layers;
     size_t nw = 0, nb = 0;   // padded parameter counts
     float *w32 = nullptr, *b32 = nullptr, *gw = nullptr, *gb = nullptr;
@@ -387,7 +425,8 @@ struct dc_surrogate {
     // activations (bf16) and gradients (fp32), sized for max_batch
     std::vector<void *> bufs;
     bf16 *xin = nullptr;
-    std::vector<bf16 *> ya, yb, pool, up, yu, sadd, yc;
+    std::vector<bf16 *> ya, yb, pool, yu, sadd, yc;
+    float *acc = nullptr;               // split-K partial sums of the forward convolutions
     float *out = nullptr;
     float *loss = nullptr;
     float *scale1 = nullptr;            // input scale of surrogate_apply
@@ -408,7 +447,15 @@ int find_layer(const dc_surrogate *s, const std::string &name)
     return -1;
 }
 
-cudaError_t conv_forward(dc_surrogate *s, const Layer &L, const bf16 *x, int B, bf16 *y, float *yf, int relu)
+// Split-K workspace of the forward convolutions (fp32 partial sums).
+constexpr size_t kSplitAccElems = (size_t)2 * 152 * BM * BN;
+
+// y = act(conv(x) + bias) (bf16), optionally the decoder skip sum
+// sadd = bf16(y + skip) and the fp32 head output yf.  up: x at half
+// resolution, upsampled in the loader.  Layers with fewer than two CTA tiles
+// per SM split K and finish in conv_finalize_kernel.
+cudaError_t conv_forward(dc_surrogate *s, const Layer &L, const bf16 *x, int B, bf16 *y, float *yf, int relu,
+                         int up = 0, const bf16 *skip = nullptr, bf16 *sadd = nullptr)
 {
     ConvFwd p;
     p.M = B << (2 * L.log2H);
@@ -417,18 +464,38 @@ cudaError_t conv_forward(dc_surrogate *s, const Layer &L, const bf16 *x, int B, 
     p.log2H = L.log2H;
     p.cin_p = L.cin_p;
     p.cout_p = L.cout_p;
+    p.up = up;
     p.X = x;
     p.W = s->w16 + L.woff;
-    p.bias = s->b32 + L.boff;
-    p.Y = y;
-    p.Yf = yf;
-    p.out_ch = L.cout;
-    p.relu = relu;
-    return run_gemm(s->stream, p);
+    p.out.cout_p = L.cout_p;
+    p.out.out_ch = L.cout;
+    p.out.relu = relu;
+    p.out.bias = s->b32 + L.boff;
+    p.out.Y = y;
+    p.out.skip = skip;
+    p.out.S = sadd;
+    p.out.Yf = yf;
+    p.acc = nullptr;
+    const int tiles = ((p.M + BM - 1) / BM) * ((p.N + BN - 1) / BN);
+    const int ksteps = p.K / BK;
+    int splits = 1;
+    if (tiles < 2 * 152 && (size_t)p.M * p.N <= kSplitAccElems) {
+        splits = (2 * 152 + tiles - 1) / tiles;
+        if (splits > ksteps / 8) splits = ksteps / 8;  // at least 8 k-steps a split
+    }
+    if (splits <= 1) return run_gemm(s->stream, p);
+    cudaError_t e = cudaMemsetAsync(s->acc, 0, (size_t)p.M * p.N * sizeof(float), s->stream);
+    if (e != cudaSuccess) return e;
+    p.acc = s->acc;
+    e = run_gemm(s->stream, p, splits);
+    if (e != cudaSuccess) return e;
+    const int64_t pairs = (int64_t)p.M * (p.N / 2);
+    return launch_kernel(conv_finalize_kernel, dim3(eb(pairs)), dim3(256), 0, s->stream, (const float *)s->acc,
+                         (int64_t)p.M, p.N, p.out);
 }
 
-// weight and bias gradients of layer L, and optionally its input gradient dx (fp32)
-cudaError_t conv_backward(dc_surrogate *s, const Layer &L, const bf16 *x, const bf16 *dz, int B, float *dx)
+cudaError_t conv_backward(dc_surrogate *s, const Layer &L, const bf16 *x, const bf16 *dz, int B, float *dx,
+                          int up = 0)
 {
     const int64_t P = (int64_t)B << (2 * L.log2H);
     ConvWgrad w;
@@ -438,6 +505,7 @@ cudaError_t conv_backward(dc_surrogate *s, const Layer &L, const bf16 *x, const 
     w.log2H = L.log2H;
     w.cin_p = L.cin_p;
     w.cout_p = L.cout_p;
+    w.up = up;
     w.dZ = dz;
     w.X = x;
     w.dW = s->gw + L.woff;
@@ -486,14 +554,9 @@ cudaError_t forward_pass(dc_surrogate *s, const float *dens, const float *scales
     for (int l = L - 2; l >= 0 && e == cudaSuccess; --l) {
         const Layer &Lu = s->layers[find_layer(s, "dec" + std::to_string(l) + "up")];
         const Layer &Lc = s->layers[find_layer(s, "dec" + std::to_string(l) + "c")];
-        const int64_t tot = ((int64_t)B << (2 * Lu.log2H)) * Lu.cin_p;
-        e = launch_kernel(upsample_kernel, dim3(eb(tot)), dim3(256), 0, s->stream, h, Lu.log2H, Lu.cin_p, tot,
-                          s->up[l]);
-        if (e == cudaSuccess) e = conv_forward(s, Lu, s->up[l], B, s->yu[l], nullptr, 1);
-        const int64_t tc = ((int64_t)B << (2 * Lc.log2H)) * Lc.cout_p;
-        if (e == cudaSuccess)
-            e = launch_kernel(add_bf16_kernel, dim3(eb(tc)), dim3(256), 0, s->stream, (const bf16 *)s->yu[l],
-                              (const bf16 *)s->yb[l], tc, s->sadd[l]);
+        // conv of the upsampled coarser output; the epilogue also forms the
+        // skip sum yu + yb[l] that the next convolution reads
+        e = conv_forward(s, Lu, h, B, s->yu[l], nullptr, 1, 1, s->yb[l], s->sadd[l]);
         if (e == cudaSuccess) e = conv_forward(s, Lc, s->sadd[l], B, s->yc[l], nullptr, 1);
         h = s->yc[l];
     }
@@ -530,7 +593,8 @@ cudaError_t backward_pass(dc_surrogate *s, const float *target, int B)
             e = launch_kernel(relu_grad_kernel, dim3(eb(nc)), dim3(256), 0, s->stream, (const float *)s->dskip[l],
                               (const float *)nullptr, (const bf16 *)s->yu[l], nc, s->dz);
         float *du = s->g2;
-        if (e == cudaSuccess) e = conv_backward(s, Lu, s->up[l], s->dz, B, du);
+        const bf16 *coarse = l == L - 2 ? s->yb[L - 1] : s->yc[l + 1];  // dec{l}up's input, before upsampling
+        if (e == cudaSuccess) e = conv_backward(s, Lu, coarse, s->dz, B, du, 1);
         const int64_t tot = ((int64_t)B << (2 * (Lu.log2H - 1))) * Lu.cin_p;
         if (e == cudaSuccess)
             e = launch_kernel(upsample_bwd_kernel, dim3(eb(tot)), dim3(256), 0, s->stream, (const float *)du,
@@ -613,6 +677,9 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
         if (cudaStreamCreate(&s->stream) != cudaSuccess) return bail(sfail(DC_ERR_CUDA, "cudaStreamCreate"));
         s->own_stream = true;
     }
+    for (cudaEvent_t &ev : s->ev)
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            return bail(sfail(DC_ERR_CUDA, "cudaEventCreate"));
     // layers, in the order of the oracle's layer list
     std::vector<int> ch(levels);
     for (int l = 0; l < levels; ++l) ch[l] = base_channels << l;
@@ -680,7 +747,6 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
     s->ya.resize(levels);
     s->yb.resize(levels);
     s->pool.resize(levels);
-    s->up.resize(levels);
     s->yu.resize(levels);
     s->sadd.resize(levels);
     s->yc.resize(levels);
@@ -693,7 +759,6 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
         s->yb[l] = (bf16 *)A(e * 2);
         if (l < levels - 1) {
             s->pool[l] = (bf16 *)A(e / 4 * 2);
-            s->up[l] = (bf16 *)A(Pl * (size_t)round8(ch[l + 1]) * 2);
             s->yu[l] = (bf16 *)A(e * 2);
             s->sadd[l] = (bf16 *)A(e * 2);
             s->yc[l] = (bf16 *)A(e * 2);
@@ -703,6 +768,7 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
         maxe = std::max(maxe, e);
     }
     s->out = (float *)A(P0 * 2 * 4);
+    s->acc = (float *)A(kSplitAccElems * 4);
     s->loss = (float *)A(4);
     s->scale1 = (float *)A(4);
     s->field1 = (float *)A(((size_t)8 << (2 * log2_res)));
@@ -731,6 +797,10 @@ dc_status surrogate_destroy(dc_surrogate *s)
     SgGuard guard(s->device);
     if (s->stream) cudaStreamSynchronize(s->stream);
     for (void *p : s->bufs) cudaFree(p);
+    for (cudaEvent_t &ev : s->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (s->apply_exec) cudaGraphExecDestroy(s->apply_exec);
+    if (s->cap) cudaStreamDestroy(s->cap);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return DC_OK;
@@ -814,6 +884,11 @@ dc_status surrogate_set_skip(dc_surrogate *s, float kappa)
 {
     if (dc_status st = check_sg(s)) return st;
     if (!(kappa == kappa)) return sfail(DC_ERR_INVALID_ARG, "kappa is NaN");
+    if (kappa != s->kappa && s->apply_exec) {  // the captured forward holds kappa
+        SgGuard guard(s->device);
+        cudaGraphExecDestroy(s->apply_exec);
+        s->apply_exec = nullptr;
+    }
     s->kappa = kappa;
     return DC_OK;
 }
@@ -879,6 +954,8 @@ dc_status surrogate_apply(dc_ctx *ctx, dc_surrogate *s, float *pos_xy, int64_t n
     if (n <= 0 || !pos_xy) return sfail(DC_ERR_INVALID_ARG, "samples");
     if (ctx->mode != MODE_FLOAT) return sfail(DC_ERR_INVALID_ARG, "the surrogate takes a smoothed density");
     SgGuard guard(s->device);
+    // no host synchronisation until the quality measure: the context's
+    // stream and the network's are ordered by events
     if (dc_status st = splat_density(ctx, pos_xy, n, nullptr, nullptr)) return st;
     const int N = 1 << s->log2H;
     if (s->in_channels == 3) {
@@ -887,13 +964,39 @@ dc_status surrogate_apply(dc_ctx *ctx, dc_surrogate *s, float *pos_xy, int64_t n
         SG_CUDA(launch_kernel(disp_to_field_kernel, dim3(eb((int64_t)N * N)), dim3(256), 0, ctx->stream,
                               (const float2 *)ctx->disp, (int64_t)N * N, (float)N, s->field1));
     }
-    SG_CUDA(cudaStreamSynchronize(ctx->stream));
-    const float scale = (float)((double)N * N / (double)n);
-    SG_CUDA(cudaMemcpyAsync(s->scale1, &scale, sizeof(float), cudaMemcpyHostToDevice, s->stream));
-    SG_CUDA(forward_pass(s, ctx->dens, s->scale1, s->in_channels == 3 ? s->field1 : nullptr, 1));
-    SG_CUDA(launch_kernel(field_to_disp_kernel, dim3(eb((int64_t)N * N)), dim3(256), 0, s->stream,
-                          (const float *)s->out, (int64_t)N * N, 1.0f / N, ctx->disp));
-    SG_CUDA(cudaStreamSynchronize(s->stream));
+    SG_CUDA(launch_kernel(set_value_kernel, dim3(1), dim3(1), 0, ctx->stream, s->scale1,
+                          (float)((double)N * N / (double)n)));
+    SG_CUDA(cudaEventRecord(s->ev[0], ctx->stream));
+    SG_CUDA(cudaStreamWaitEvent(s->stream, s->ev[0], 0));
+    if (!s->apply_exec || s->apply_key[0] != ctx->dens || s->apply_key[1] != ctx->disp) {
+        if (s->apply_exec) {
+            cudaGraphExecDestroy(s->apply_exec);
+            s->apply_exec = nullptr;
+        }
+        if (!s->cap) SG_CUDA(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
+        cudaStream_t keep = s->stream;
+        s->stream = s->cap;
+        SG_CUDA(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = forward_pass(s, ctx->dens, s->scale1, s->in_channels == 3 ? s->field1 : nullptr, 1);
+        if (e == cudaSuccess)
+            e = launch_kernel(field_to_disp_kernel, dim3(eb((int64_t)N * N)), dim3(256), 0, s->cap,
+                              (const float *)s->out, (int64_t)N * N, 1.0f / N, ctx->disp);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(s->cap, &g);
+        s->stream = keep;
+        if (e == cudaSuccess) e = ee;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&s->apply_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            s->apply_exec = nullptr;
+            return sfail(DC_ERR_CUDA, "surrogate_apply graph: %s", cudaGetErrorString(e));
+        }
+        s->apply_key[0] = ctx->dens;
+        s->apply_key[1] = ctx->disp;
+    }
+    SG_CUDA(cudaGraphLaunch(s->apply_exec, s->stream));
+    SG_CUDA(cudaEventRecord(s->ev[1], s->stream));
+    SG_CUDA(cudaStreamWaitEvent(ctx->stream, s->ev[1], 0));
     ctx->have_disp = true;
     if (dc_status st = advect_samples(ctx, pos_xy, n)) return st;
     int used = 0;
