@@ -23,6 +23,7 @@
 
 #include "dc_internal.cuh"
 #include "dc_sg_gemm.cuh"
+#include "dc_sg_umma.cuh"
 
 using namespace dc;
 using namespace dc::sg;
@@ -90,6 +91,7 @@ struct ConvFwd {
     static constexpr int ALAYOUT = K_CONTIG, BLAYOUT = K_CONTIG;
     int M, N, K;
     int log2H, cin_p, cout_p;
+    int lg_cin;     // log2(cin_p): cin_p is a power of two (8 .. 256)
     int up;         // input at half resolution, upsampled on the fly
     const bf16 *X;
     const bf16 *W;
@@ -98,8 +100,8 @@ struct ConvFwd {
     __device__ const void *base() const { return W; }
     __device__ const void *a_chunk(int m, int k) const
     {
-        const int tap = k / cin_p, ci = k - tap * cin_p;
-        const int dy = tap / 3, dx = tap - 3 * dy;
+        const int tap = k >> lg_cin, ci = k & (cin_p - 1);
+        const int dy = (tap * 11) >> 5, dx = tap - 3 * dy;  // tap / 3 for tap < 9
         const int H = 1 << log2H;
         const int x = m & (H - 1), y = (m >> log2H) & (H - 1), b = m >> (2 * log2H);
         const int yy = y + dy - 1, xx = x + dx - 1;
@@ -410,6 +412,9 @@ struct dc_surrogate {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    bool tcgen05 = false;               // forward convolutions of 64..256 channels on tcgen05
+                                        // (DECLUTTER_SG_TCGEN05=1; measured slower at these sizes)
+    unsigned *status = nullptr;         // DC_ERR_TIMEOUT from a bounded wait in a kernel
     cudaEvent_t ev[2] = {nullptr, nullptr};  // stream ordering with a context in surrogate_apply
     // surrogate_apply's forward pass + field conversion as one CUDA graph,
     // captured on a private stream for the context buffers it was made for
@@ -464,6 +469,7 @@ cudaError_t conv_forward(dc_surrogate *s, const Layer &L, const bf16 *x, int B, 
     p.log2H = L.log2H;
     p.cin_p = L.cin_p;
     p.cout_p = L.cout_p;
+    p.lg_cin = 31 - __builtin_clz((unsigned)L.cin_p);
     p.up = up;
     p.X = x;
     p.W = s->w16 + L.woff;
@@ -476,19 +482,35 @@ cudaError_t conv_forward(dc_surrogate *s, const Layer &L, const bf16 *x, int B, 
     p.out.S = sadd;
     p.out.Yf = yf;
     p.acc = nullptr;
-    const int tiles = ((p.M + BM - 1) / BM) * ((p.N + BN - 1) / BN);
-    const int ksteps = p.K / BK;
+    // tcgen05 for 64..256 output channels; the 32-channel full-resolution
+    // layers are loader-bound and faster on the 64 x 32 mma.sync tiles
+    const bool um = s->tcgen05 && (p.N == 64 || p.N == 128 || p.N == 256) && p.M % UM_TM == 0;
+    const int tm = um ? UM_TM : BM, tk = um ? UM_TK : BK;
+    const int tiles = ((p.M + tm - 1) / tm) * (um ? 1 : (p.N + BN - 1) / BN);
+    const int ksteps = (p.K + tk - 1) / tk;
+    const int min_steps = um ? 2 : 8;  // k-steps a split at least
     int splits = 1;
     if (tiles < 2 * 152 && (size_t)p.M * p.N <= kSplitAccElems) {
         splits = (2 * 152 + tiles - 1) / tiles;
-        if (splits > ksteps / 8) splits = ksteps / 8;  // at least 8 k-steps a split
+        if (splits > ksteps / min_steps) splits = ksteps / min_steps;
+        if (splits < 1) splits = 1;
     }
-    if (splits <= 1) return run_gemm(s->stream, p);
-    cudaError_t e = cudaMemsetAsync(s->acc, 0, (size_t)p.M * p.N * sizeof(float), s->stream);
-    if (e != cudaSuccess) return e;
-    p.acc = s->acc;
-    e = run_gemm(s->stream, p, splits);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (splits > 1) {
+        e = cudaMemsetAsync(s->acc, 0, (size_t)p.M * p.N * sizeof(float), s->stream);
+        if (e != cudaSuccess) return e;
+        p.acc = s->acc;
+    }
+    if (um) {
+        int kps = (p.K + splits - 1) / splits;
+        kps = (kps + UM_TK - 1) / UM_TK * UM_TK;
+        const int sp = (p.K + kps - 1) / kps;
+        e = launch_kernel(umma_gemm_kernel<ConvFwd>, dim3(p.M / UM_TM, 1, sp), dim3(UM_THREADS), umma_smem_bytes(p.N),
+                          s->stream, p, kps, s->status);
+    } else {
+        e = run_gemm(s->stream, p, splits);
+    }
+    if (e != cudaSuccess || splits <= 1) return e;
     const int64_t pairs = (int64_t)p.M * (p.N / 2);
     return launch_kernel(conv_finalize_kernel, dim3(eb(pairs)), dim3(256), 0, s->stream, (const float *)s->acc,
                          (int64_t)p.M, p.N, p.out);
@@ -655,6 +677,7 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
     if (!out) return sfail(DC_ERR_INVALID_ARG, "null out");
     *out = nullptr;
     if (in_channels != 1 && in_channels != 3) return sfail(DC_ERR_INVALID_ARG, "in_channels = %d", in_channels);
+    const char *tc = getenv("DECLUTTER_SG_TCGEN05");
     if (levels < 1 || levels > 6 || base_channels < 8 || base_channels > 256 || (base_channels & 7))
         return sfail(DC_ERR_INVALID_ARG, "levels = %d, base_channels = %d", levels, base_channels);
     if (log2_res < levels + 2 || log2_res > 11) return sfail(DC_ERR_INVALID_ARG, "log2_res = %d", log2_res);
@@ -664,6 +687,7 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
     s->levels = levels;
     s->c0 = base_channels;
     s->in_channels = in_channels;
+    s->tcgen05 = tc && tc[0] == '1';
     s->log2H = log2_res;
     s->max_batch = max_batch;
     s->device = device;
@@ -769,6 +793,7 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
     }
     s->out = (float *)A(P0 * 2 * 4);
     s->acc = (float *)A(kSplitAccElems * 4);
+    s->status = (unsigned *)A(4);
     s->loss = (float *)A(4);
     s->scale1 = (float *)A(4);
     s->field1 = (float *)A(((size_t)8 << (2 * log2_res)));
@@ -781,8 +806,12 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
     if (cudaMemcpy(s->w32, w.data(), s->nw * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(s->b32, b.data(), s->nb * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(s->mw, 0, s->nw * 4) != cudaSuccess || cudaMemset(s->vw, 0, s->nw * 4) != cudaSuccess ||
-        cudaMemset(s->mb, 0, s->nb * 4) != cudaSuccess || cudaMemset(s->vb, 0, s->nb * 4) != cudaSuccess)
+        cudaMemset(s->mb, 0, s->nb * 4) != cudaSuccess || cudaMemset(s->vb, 0, s->nb * 4) != cudaSuccess ||
+        cudaMemset(s->status, 0, 4) != cudaSuccess)
         return bail(sfail(DC_ERR_CUDA, "parameter upload"));
+    if (cudaFuncSetAttribute(umma_gemm_kernel<ConvFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)umma_smem_bytes(256)) != cudaSuccess)
+        return bail(sfail(DC_ERR_CUDA, "kernel attributes"));
     if (launch_kernel(to_bf16_kernel, dim3(eb((int64_t)s->nw)), dim3(256), 0, s->stream, (const float *)s->w32,
                       (int64_t)s->nw, s->w16) != cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)
@@ -880,6 +909,19 @@ dc_status surrogate_set_params(dc_surrogate *s, const float *w_host, const float
     return DC_OK;
 }
 
+// after a synchronisation: DC_ERR_TIMEOUT if a kernel's bounded wait expired
+static dc_status sg_status(dc_surrogate *s)
+{
+    unsigned st = 0;
+    if (cudaMemcpy(&st, s->status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return sfail(DC_ERR_CUDA, "status read");
+    if (st) {
+        cudaMemset(s->status, 0, sizeof(unsigned));
+        return sfail((dc_status)st, "device status %u", st);
+    }
+    return DC_OK;
+}
+
 dc_status surrogate_set_skip(dc_surrogate *s, float kappa)
 {
     if (dc_status st = check_sg(s)) return st;
@@ -919,6 +961,7 @@ dc_status surrogate_loss_grad(dc_surrogate *s, const float *density, const float
     if (loss_out) {
         SG_CUDA(cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToHost, s->stream));
         SG_CUDA(cudaStreamSynchronize(s->stream));
+        return sg_status(s);
     }
     return DC_OK;
 }
@@ -938,6 +981,7 @@ dc_status surrogate_train_step(dc_surrogate *s, const float *density, const floa
     if (loss_out) {
         SG_CUDA(cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToHost, s->stream));
         SG_CUDA(cudaStreamSynchronize(s->stream));
+        return sg_status(s);
     }
     return DC_OK;
 }
@@ -1010,7 +1054,8 @@ dc_status surrogate_apply(dc_ctx *ctx, dc_surrogate *s, float *pos_xy, int64_t n
     }
     if (plain_iters_out) *plain_iters_out = used;
     if (cv_out) *cv_out = m[1];
-    return declutter_sync(ctx);
+    if (dc_status st = declutter_sync(ctx)) return st;
+    return sg_status(s);
 }
 
 }  // extern "C"

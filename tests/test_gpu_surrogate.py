@@ -50,10 +50,13 @@ def split_params(w, b, levels, c0, c_in=1):
     return out
 
 
-@pytest.mark.parametrize("levels,c0,log2,batch,c_in,kappa", [
-    (2, 8, 4, 2, 1, 0.0), (3, 8, 5, 2, 1, 0.0), (2, 16, 4, 3, 1, 0.0), (4, 32, 6, 1, 1, 0.0),
-    (2, 8, 4, 2, 3, 1.7), (4, 32, 6, 1, 3, 3.0)])
-def test_forward_and_gradients_match_oracle(dc, levels, c0, log2, batch, c_in, kappa):
+@pytest.mark.parametrize("levels,c0,log2,batch,c_in,kappa,tc", [
+    (2, 8, 4, 2, 1, 0.0, "0"), (3, 8, 5, 2, 1, 0.0, "0"), (2, 16, 4, 3, 1, 0.0, "0"), (4, 32, 6, 1, 1, 0.0, "0"),
+    (2, 8, 4, 2, 3, 1.7, "0"), (4, 32, 6, 1, 3, 3.0, "0"),
+    # the tcgen05 path of the forward convolutions (64..256 output channels)
+    (4, 32, 7, 1, 3, 3.0, "1"), (3, 64, 7, 2, 1, 0.0, "1")])
+def test_forward_and_gradients_match_oracle(dc, monkeypatch, levels, c0, log2, batch, c_in, kappa, tc):
+    monkeypatch.setenv("DECLUTTER_SG_TCGEN05", tc)
     H = 1 << log2
     rng = np.random.default_rng(levels * 10 + c0 + c_in)
     P = S.init_params(levels, c0, seed=levels + c0, c_in=c_in)
