@@ -172,7 +172,7 @@ def band_record_bytes(N: int, T: int, elem: int = 4):
     """(aggregate bytes, carry bytes) of the band decomposition: nb compact
     aggregates of 3N + 2T + 2 values; carries of nb windows of 3N + 2T - 2
     values (rounded to 4) plus the 5N marginals."""
-    nb = N // T
+    nb = (N + T - 1) // T
     agg = nb * (3 * N + 2 * T + 2) * elem
     carry = (nb * ((3 * N + 2 * T - 2 + 3) // 4 * 4) + 5 * N) * elem
     return agg, carry

@@ -80,8 +80,10 @@ typedef struct {
     int32_t pixel_center;    /* 0: pixel at (i, j)/N; 1: at (i + 1/2, j + 1/2)/N */
     int32_t clamp_positions; /* 1: clamp each updated sample to [0, 1]^2 */
     int32_t carry_mode;      /* DC_CARRY_* (float mode only) */
-    int32_t band_rows;       /* rows per band of the integral-image kernels, a
-                                power of two dividing N; 0 = automatic */
+    int32_t band_rows;       /* rows per band of the integral-image kernels,
+                                1..64 (the last band may be shorter); 0 =
+                                automatic: one band per SM of a 152-SM GPU
+                                from 1024 x 1024, N / 128 below */
     int32_t keep_order;      /* regularize(): 0 = iterate on an internal copy of the
                                 samples sorted by pixel (faster; results identical),
                                 1 = iterate in the caller's order */
@@ -94,7 +96,7 @@ typedef struct {
     int32_t kernel_r;        /* effective radius (0 = exact integer mode) */
     float sigma;             /* effective Gaussian width */
     int32_t band_rows;       /* rows per band */
-    int32_t n_bands;         /* N / band_rows */
+    int32_t n_bands;         /* ceil(N / band_rows) */
     int32_t band_threads;    /* threads per band CTA */
     int32_t kernels_per_iter;/* kernel launches per iteration of regularize */
     int32_t device;          /* CUDA device ordinal */
@@ -249,7 +251,8 @@ dc_status declutter_batch_sync(dc_batch *batch);
 
 /* Autotuner of the integral-image band height (rows per band): times
  * regularize(iters) on a copy of the given samples for every band height
- * 1, 2, 4, ... 64 with at most 1024 bands, and returns the fastest in
+ * 1, 2, 4, ... 64 with at most 1024 bands and for the automatic height, and
+ * returns the fastest in
  * *best_out (its median time in *best_ms_out, or -1 when the answer came
  * from the cache).  Answers are cached per (device, resolution, radius, carry
  * mode, floor(log2 n)) for the life of the process.  The samples are not

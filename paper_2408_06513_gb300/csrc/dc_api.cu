@@ -378,7 +378,7 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
         return fail(DC_ERR_INVALID_ARG, "carry_mode");
     if (p.band_rows != 0) {
         const int T = p.band_rows;
-        if (T < 1 || T > 64 || (T & (T - 1)) || T > N) return fail(DC_ERR_INVALID_ARG, "band_rows = %d", T);
+        if (T < 1 || T > 64 || T > N) return fail(DC_ERR_INVALID_ARG, "band_rows = %d", T);
     }
     if (!(p.sigma == p.sigma) || !(p.d0 == p.d0)) return fail(DC_ERR_INVALID_ARG, "NaN parameter");
 

@@ -123,8 +123,12 @@ dc_status declutter_autotune_band_rows(const dc_params *params, int device, void
     int best = 0;
     float best_ms = 0.f;
     dc_status st = DC_OK;
-    for (int T = 1; T <= 64 && st == DC_OK; T *= 2) {
-        if (T > N || N / T > 1024) continue;
+    // powers of two, then the automatic height (one band per SM)
+    const int T_auto = make_band_geom(params->log2_res, 0).T;
+    for (int Tk = 1; Tk <= 128 && st == DC_OK; Tk *= 2) {
+        const int T = Tk <= 64 ? Tk : T_auto;
+        if (Tk > 64 && (T_auto & (T_auto - 1)) == 0) continue;  // already timed
+        if (T > N || (N + T - 1) / T > 1024) continue;
         dc_params p = *params;
         p.band_rows = T;
         dc_ctx *c = nullptr;

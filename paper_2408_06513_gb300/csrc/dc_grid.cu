@@ -33,12 +33,13 @@ BandGeom make_band_geom(int log2N, int band_rows)
     g.N = 1 << log2N;
     int T = band_rows;
     if (T <= 0) {
-        T = g.N / 128;
+        // from 1024^2 one band for each of the 152 SMs (the last one shorter)
+        T = g.N >= 1024 ? (g.N + 151) / 152 : g.N / 128;
         if (T < 1) T = 1;
         if (T > 64) T = 64;
     }
     g.T = T;
-    g.nb = g.N / T;
+    g.nb = (g.N + T - 1) / T;  // band b: rows [b T, min(N, b T + T))
     // at most 512 threads per band CTA (128 registers a thread)
     g.CPT = g.N >= 128 ? (g.N / 512 > 4 ? g.N / 512 : 4) : 1;
     g.NT = g.N / g.CPT;
@@ -343,8 +344,8 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
     const int nw = blockDim.x >> 5;
     const int b = blockIdx.x;
     const int j0 = b * T;
+    const int Tb = min(T, N - j0);  // rows of this band (the last one may be shorter)
     const int c0 = t * CPT;
-    const int lanes = 5 * N;
 
     __shared__ Acc s_wt[2][32];
     __shared__ Acc s_uf[2][32];
@@ -364,7 +365,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
     float kappa = 0.f, scale = 0.f;
     if constexpr (FINAL) {
         cb = static_cast<const Acc *>(a.carry) + (size_t)b * carry_stride(N, T);
-        ce = static_cast<const Acc *>(a.carry) + (size_t)(N / T) * carry_stride(N, T);
+        ce = static_cast<const Acc *>(a.carry) + (size_t)((N + T - 1) / T) * carry_stride(N, T);
 #pragma unroll
         for (int k = 0; k < CPT; ++k) {
             const int c = min(c0 + k, N - 1);
@@ -384,13 +385,13 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
 
     Acc vnext[CPT];
     load_row<MODE, CPT>(a.src, log2N, j0, c0, a.mu, vnext);
-    for (int r = 0; r < T; ++r) {
+    for (int r = 0; r < Tb; ++r) {
         const int j = j0 + r;
         const int par = r & 1;
         Acc v[CPT];
 #pragma unroll
         for (int k = 0; k < CPT; ++k) v[k] = vnext[k];
-        if (r + 1 < T) load_row<MODE, CPT>(a.src, log2N, j + 1, c0, a.mu, vnext);  // prefetch
+        if (r + 1 < Tb) load_row<MODE, CPT>(a.src, log2N, j + 1, c0, a.mu, vnext);  // prefetch
         if constexpr (!FINAL) {
             if (a.zero_out) {
                 uint32_t zz[CPT];
@@ -469,7 +470,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
                 const int u = cc + j;
                 const int vi = cc - j + N - 1;
                 const Acc al = cvb[k] + arun[k];
-                const Acc at = (cb[N + (u - j0)] + Un[k]) - (cb[2 * N + T - 1 + (vi - (N - j0 - T))] + Vn[k]);
+                const Acc at = (cb[N + (u - j0)] + Un[k]) - (cb[2 * N + T - 1 + (vi - (N - j0 - Tb))] + Vn[k]);
                 const Acc A = ce[N + u];
                 const Acc Bv = Ctot - ce[3 * N + vi];
                 const Acc R = Rk[k];
@@ -566,9 +567,9 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
                 ag[2 * N + c] = Vo[k];
             }
         }
-        for (int rr = t; rr < T; rr += blockDim.x) {
+        for (int rr = t; rr < Tb; rr += blockDim.x) {
             Acc below = Acc(0);
-            for (int q = rr + 1; q < T; ++q) below = below + s_RT[q];
+            for (int q = rr + 1; q < Tb; ++q) below = below + s_RT[q];
             ag[3 * N + rr] = s_U0[rr];
             ag[3 * N + T + rr] = s_VN[rr] + below;
         }
@@ -712,7 +713,7 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int b = blockIdx.x;
     const int j0 = b * T;
-    const int lanes = 5 * N;
+    const int Tb = min(T, N - j0);  // rows of this band (the last one may be shorter)
 
     __shared__ S s_wt[2][G][16];
     __shared__ S s_uf[2][G][16];
@@ -740,7 +741,7 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
         }
         __syncthreads();
         if (t == 0)
-            for (int k = 0; k < ring && k < T; ++k)
+            for (int k = 0; k < ring && k < Tb; ++k)
                 tma_row(ringp + (size_t)k * rowbytes, src + (size_t)(j0 + k) * rowbytes, rowbytes, &s_mbar[k]);
     }
 
@@ -761,14 +762,14 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
             sBm = p;
         }
         const C *cb = static_cast<const C *>(a.carry) + (size_t)b * carry_stride(N, T);
-        const C *ce = static_cast<const C *>(a.carry) + (size_t)(N / T) * carry_stride(N, T);
-        const int ubase = N + j0;              // marginal lane of window element 0: u = j0
-        const int vbase = 3 * N + N - j0 - T;  // marginal lane of window element 0: v = -(j0 + T - 1)
+        const C *ce = static_cast<const C *>(a.carry) + (size_t)((N + T - 1) / T) * carry_stride(N, T);
+        const int ubase = N + j0;               // marginal lane of window element 0: u = j0
+        const int vbase = 3 * N + N - j0 - Tb;  // marginal lane of window element 0: v = -(j0 + Tb - 1)
         for (int i = t; i < N; i += NT) {
             sA[wpos(i, L4a)] = cb[i];
             if constexpr (MODE != MODE_GRID64) sR[wpos(i, L4a)] = ce[i];
         }
-        for (int i = t; i < N + T - 1; i += NT) {
+        for (int i = t; i < N + Tb - 1; i += NT) {
             sU[wpos(i, L4w)] = cb[N + i];
             sV[wpos(i, L4w)] = cb[2 * N + T - 1 + i];
             if constexpr (MODE != MODE_GRID64) {
@@ -809,7 +810,7 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
 
     const bool out32 = ((reinterpret_cast<uintptr_t>(a.alpha_out) | reinterpret_cast<uintptr_t>(a.alpha_t_out)) & 31) == 0;
 
-    for (int r = 0; r < T; ++r) {
+    for (int r = 0; r < Tb; ++r) {
         const int j = j0 + r;
         const int par = r & 1;
         uint4 cur[G];
@@ -824,7 +825,7 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
         } else {
 #pragma unroll
             for (int q = 0; q < G; ++q) cur[q] = buf[q];
-            if (r + 1 < T) load(j + 1, buf);
+            if (r + 1 < Tb) load(j + 1, buf);
         }
 
         if constexpr (!FINAL) {
@@ -877,7 +878,7 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
         __syncthreads();
         if constexpr (RING) {
             // every thread has read this row's slot: refill it with row j + ring
-            if (t == 0 && r + ring < T && !dead) {
+            if (t == 0 && r + ring < Tb && !dead) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 tma_row(ringp + (size_t)rslot * rowbytes, src + (size_t)(j + ring) * rowbytes, rowbytes,
                         &s_mbar[rslot]);
@@ -952,7 +953,7 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
             int offU[4], offV[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int iu = e + r, iv = e - r + T - 1;
+                const int iu = e + r, iv = e - r + Tb - 1;
                 offU[e] = (iu & 3) * L4w + (iu >> 2) + t;
                 offV[e] = (iv & 3) * L4w + (iv >> 2) + t;
             }
@@ -968,7 +969,7 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
                         const int c = cq + e;
                         oal[e] = sA[wpos(c, L4a)] + (unsigned long long)arun[q][e];
                         oat[e] = (sU[wpos(c + r, L4w)] + (unsigned long long)Uo[q][e]) -
-                                 (sV[wpos(c - r + T - 1, L4w)] + (unsigned long long)Vo[q][e]);
+                                 (sV[wpos(c - r + Tb - 1, L4w)] + (unsigned long long)Vo[q][e]);
                     }
                     if (a.alpha_out)
                         store4_u64(static_cast<unsigned long long *>(a.alpha_out) + rowoff + cq, oal[0], oal[1],
@@ -1078,9 +1079,9 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
                 ag[2 * N + cq + e] = C(Vo[q][e]);
             }
         }
-        for (int rr = t; rr < T; rr += NT) {
+        for (int rr = t; rr < Tb; rr += NT) {
             S below = S(0);
-            for (int q = rr + 1; q < T; ++q) below = below + s_RT[q];
+            for (int q = rr + 1; q < Tb; ++q) below = below + s_RT[q];
             ag[3 * N + rr] = C(s_U0[rr]);
             ag[3 * N + T + rr] = C(s_VN[rr] + below);
         }
@@ -1154,6 +1155,7 @@ __global__ void __launch_bounds__(NT) agg_proj_kernel(BandArgs a, int log2N, int
     const int t = threadIdx.x;
     const int b = blockIdx.x;
     const int j0 = b * T;
+    const int Tb = min(T, N - j0);  // rows of this band (the last one may be shorter)
     const int P0 = ring_pad(T);
     const int slotw = N + 2 * P0;  // words per ring slot
     const unsigned rowbytes = 4u << log2N;
@@ -1175,7 +1177,7 @@ __global__ void __launch_bounds__(NT) agg_proj_kernel(BandArgs a, int log2N, int
     }
     __syncthreads();
     if (t == 0)
-        for (int k = 0; k < ring && k < T; ++k)
+        for (int k = 0; k < ring && k < Tb; ++k)
             tma_row(ringw + k * slotw + P0, src + (size_t)(j0 + k) * rowbytes, rowbytes, &s_mbar[k]);
 
     S K[G][4], A[CPT + 2], D[CPT + 2];
@@ -1186,13 +1188,13 @@ __global__ void __launch_bounds__(NT) agg_proj_kernel(BandArgs a, int log2N, int
 #pragma unroll
     for (int k = 0; k < CPT + 2; ++k) { A[k] = S(0); D[k] = S(0); }
     // lines N + t and N + NT + t of the diagonal projections (T - 1 <= 63, NT >= 32)
-    const bool extra = t < T - 1, extra2 = NT + t < T - 1;
+    const bool extra = t < Tb - 1, extra2 = NT + t < Tb - 1;
     uint32_t vor = 0u;
     int rslot = 0;
     unsigned rpar = 0;
     bool dead = false;
 
-    for (int r = 0; r < T; ++r) {
+    for (int r = 0; r < Tb; ++r) {
         const int j = j0 + r;
         if (!dead && !mbar_wait(&s_mbar[rslot], rpar)) {
             dead = true;
@@ -1224,7 +1226,7 @@ __global__ void __launch_bounds__(NT) agg_proj_kernel(BandArgs a, int log2N, int
             }
         }
         const S *ra = row + t - r;            // A: column (t + NT k) - r
-        const S *rd = row + t + r - (T - 1);  // D: column (t + NT k) + r - (T - 1)
+        const S *rd = row + t + r - (Tb - 1);  // D: column (t + NT k) + r - (Tb - 1)
 #pragma unroll
         for (int k = 0; k < CPT; ++k) {
             if constexpr (MODE == MODE_FLOAT) {
@@ -1254,7 +1256,7 @@ __global__ void __launch_bounds__(NT) agg_proj_kernel(BandArgs a, int log2N, int
             }
         }
         __syncthreads();
-        if (t == 0 && r + ring < T && !dead) {
+        if (t == 0 && r + ring < Tb && !dead) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tma_row(ringw + rslot * slotw + P0, src + (size_t)(j + ring) * rowbytes, rowbytes, &s_mbar[rslot]);
         }
@@ -1276,7 +1278,7 @@ __global__ void __launch_bounds__(NT) agg_proj_kernel(BandArgs a, int log2N, int
     }
 
     // projections into shared memory (the ring is no longer read), then scans
-    const int L = N + T - 1;
+    const int L = N + Tb - 1;
     S *pk = ringw, *pa = ringw + N, *pd = ringw + N + L;
 #pragma unroll
     for (int q = 0; q < G; ++q)
@@ -1303,12 +1305,12 @@ __global__ void __launch_bounds__(NT) agg_proj_kernel(BandArgs a, int log2N, int
     // compact aggregate [alpha N][U N][V N][U0 T][E T][S][flag]
     for (int i = t; i < N; i += NT) {
         ag[i] = C(pk[i]);
-        ag[N + i] = C(pa[i + T - 1]);
+        ag[N + i] = C(pa[i + Tb - 1]);
         ag[2 * N + i] = i > 0 ? C(pd[i - 1]) : C(0);
     }
-    for (int r = t; r < T; r += NT) {
+    for (int r = t; r < Tb; r += NT) {
         ag[3 * N + r] = C(pa[r]);
-        ag[3 * N + T + r] = C(pd[N + T - 3 - r]);
+        ag[3 * N + T + r] = C(pd[N + Tb - 3 - r]);
     }
     if (t == 0) {
         ag[3 * N + 2 * T] = C(pk[N - 1]);
@@ -1325,7 +1327,7 @@ __global__ void __launch_bounds__(NT) agg_proj_kernel(BandArgs a, int log2N, int
 template <typename Acc>
 __device__ __forceinline__ Acc band_contrib(const Acc *__restrict__ ab, int b, int lane, int N, int T)
 {
-    const int j0 = b * T, jl = j0 + T - 1;
+    const int j0 = b * T, Tb = min(T, N - j0), jl = j0 + Tb - 1;
     if (lane < N) return ab[lane];
     if (lane < 3 * N) {
         const int u = lane - N;
@@ -1338,7 +1340,7 @@ __device__ __forceinline__ Acc band_contrib(const Acc *__restrict__ ab, int b, i
     if (v < -jl) return Acc(0);
     if (v <= N - 1 - jl) return ab[2 * N + (v + jl)];
     const int m = v - (N - 1 - jl);
-    if (m <= T - 1) return ab[3 * N + T + (T - 1 - m)];
+    if (m <= Tb - 1) return ab[3 * N + T + (Tb - 1 - m)];
     return ab[3 * N + 2 * T];
 }
 
@@ -1436,13 +1438,13 @@ __global__ void __launch_bounds__(1024) carry_kernel(const Acc *__restrict__ agg
     // where lane's value goes in band b's window (or -1)
     auto slot = [&](int b) -> int {
         if (lane < N) return lane;
-        const int j0 = b * T;
+        const int j0 = b * T, Tb = min(T, N - j0);
         if (lane < 3 * N) {
             const int o = lane - N - j0;
-            return (o >= 0 && o < N + T - 1) ? N + o : -1;
+            return (o >= 0 && o < N + Tb - 1) ? N + o : -1;
         }
-        const int o = lane - 3 * N - (N - j0 - T);
-        return (o >= 0 && o < N + T - 1) ? 2 * N + T - 1 + o : -1;
+        const int o = lane - 3 * N - (N - j0 - Tb);
+        return (o >= 0 && o < N + Tb - 1) ? 2 * N + T - 1 + o : -1;
     };
     if (bpg <= kCarryCache) {
 #pragma unroll

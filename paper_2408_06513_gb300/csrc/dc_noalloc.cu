@@ -18,8 +18,8 @@ using namespace dc;
 
 namespace {
 
-// 8.5 MiB: the aggregates and carries of the largest supported grid,
-// 1024 x 1024 with the default band height (8,450,048 bytes).  Every GPU
+// 8.5 MiB: room for the aggregates and carries of the largest supported
+// grid, 1024 x 1024 with the default band height (7,299,360 bytes).  Every GPU
 // that loads the library holds this array until the process exits.
 constexpr size_t kNoallocScratchBytes = DC_NOALLOC_SCRATCH_BYTES;
 constexpr uint32_t kNoallocMaxLog2Res = DC_NOALLOC_MAX_LOG2_RES;
@@ -88,7 +88,9 @@ extern "C" dc_status integral_images_u32_noalloc(const uint32_t *grid, uint32_t 
 
     const BandGeom g = make_band_geom((int)log2_res, 0);
     const size_t agg_bytes = ((size_t)g.nb * g.agg_stride * sizeof(unsigned long long) + 255) & ~size_t(255);
-    const size_t carry_bytes = (size_t)(g.nb + 1) * g.lanes * sizeof(unsigned long long);
+    // per band the lanes its final pass reads, then the 5N totals
+    const size_t carry_bytes =
+        ((size_t)g.nb * ((3 * g.N + 2 * g.T - 2 + 3) & ~3) + (size_t)g.lanes) * sizeof(unsigned long long);
     if (agg_bytes + carry_bytes > kNoallocScratchBytes) {
         snprintf(g_noalloc_msg, sizeof(g_noalloc_msg), "grid needs %zu scratch bytes, limit %zu",
                  agg_bytes + carry_bytes, kNoallocScratchBytes);

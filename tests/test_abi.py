@@ -69,7 +69,8 @@ def _params(**kw):
     (dict(log2_res=4, kernel_r=16), 1),
     (dict(pixel_center=2), 1),
     (dict(carry_mode=5), 1),
-    (dict(band_rows=3), 1),
+    (dict(band_rows=-1), 1),
+    (dict(band_rows=65), 1),
     (dict(band_rows=128), 1),
     (dict(keep_order=2), 1),
 ])

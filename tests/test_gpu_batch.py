@@ -77,7 +77,8 @@ def test_autotune_band_rows(dc, panels):
     before = pos.clone()
     T, ms = dc.declutter_autotune_band_rows(pos, 2, log2, kernel_r=0)
     N = 1 << log2
-    assert T in (1, 2, 4, 8, 16, 32, 64) and T <= N and N // T <= 1024
+    # a power of two or the automatic one-band-per-SM height, at most 1024 bands
+    assert 1 <= T <= 64 and T <= N and (N + T - 1) // T <= 1024
     assert ms > 0
     assert torch.equal(pos, before)              # samples untouched
     T2, ms2 = dc.declutter_autotune_band_rows(pos, 2, log2, kernel_r=0)

@@ -117,7 +117,9 @@ def test_tiny_teacher_forced_iterations(dc, r):
 
 
 @pytest.mark.parametrize("k,r,band_rows", [(4, 0, 0), (4, 2, 1), (5, 0, 2), (6, 3, 4), (7, 0, 8),
-                                           (8, 2, 16), (9, 0, 64), (9, 4, 1)])
+                                           (8, 2, 16), (9, 0, 64), (9, 4, 1),
+                                           # heights that do not divide N: a shorter last band
+                                           (7, 0, 3), (8, 2, 5), (11, 4, 0), (11, 0, 13)])
 def test_sizes_and_band_heights(dc, k, r, band_rows):
     z, _ = synth.tiny_mixture(5003, seed=k + r)
     p = oracle.Params(log2_res=k, kernel_r=r)
@@ -192,10 +194,12 @@ def test_integral_images_u32_large_exact(dc, k):
         dc.declutter_destroy(ctx)
 
 
-@pytest.mark.parametrize("k,T", [(7, 1), (7, 64), (8, 2), (11, 64), (12, 1), (12, 16), (13, 8)])
+@pytest.mark.parametrize("k,T", [(7, 1), (7, 64), (8, 2), (9, 5), (10, 7), (11, 64), (11, 14), (12, 1), (12, 16),
+                                 (12, 27), (13, 8), (13, 54), (13, 0)])
 def test_integral_images_u32_band_heights(dc, k, T):
     # every column layout of the band kernels (4, 8 and 16 columns a thread)
-    # and band heights from one row to 64
+    # and band heights from one row to 64, including heights that do not
+    # divide N (a shorter last band) and the automatic height (T = 0)
     N = 1 << k
     grid = synth.sat_grid(k, seed=T)
     a_ref, at_ref = oracle.sat_u64(grid)
