@@ -187,6 +187,8 @@ def algorithmic_bytes(kind: str, n: int, N: int, info) -> float:
         "band_aggregate": 4.0 * NN + agg,       # read d_r, write the compact aggregates
         "band_carry": agg + carry,              # read aggregates, write carries
         "band_final": 12.0 * NN + 2 * carry,    # read d_r and the carry/marginal windows, write the field
+        # the three band phases in one cooperative launch
+        "band_fused": 4.0 * NN + agg + (agg + carry) + 12.0 * NN + 2 * carry,
         "advect": 16.0 * n,                     # read + write the samples
         "quality": 4.0 * NN,
         "reorder": 4.0 * NN * 3 + 8.0 * n * 2 + 4.0 * n * 2 + 8.0 * n,  # scan, scatter, way back

@@ -104,6 +104,15 @@ cudaError_t enqueue_density(dc_ctx *c, cudaStream_t s, const float *pos, int64_t
 cudaError_t enqueue_inims(dc_ctx *c, cudaStream_t s, const BandArgs &a, int mode, Recorder &rec)
 {
     cudaError_t e = cudaSuccess;
+    if (c->fused && mode != MODE_GRID64) {
+        // the three phases in one cooperative launch (small grids)
+        BandArgs f = a;
+        f.zero_out = nullptr;
+        rec.count(K_BAND_FUSED);
+        for (int t = 0; t < rec.times(K_BAND_FUSED) && e == cudaSuccess; ++t)
+            e = launch_band_fused(s, c->g, mode, c->p.carry_mode, a, f, c->status + kBarWord);
+        return e;
+    }
     rec.count(K_BAND_AGG);
     for (int t = 0; t < rec.times(K_BAND_AGG) && e == cudaSuccess; ++t) e = launch_band_agg(s, c->g, mode, a);
     if (e != cudaSuccess) return e;
@@ -296,8 +305,8 @@ dc_status check_samples(const dc_ctx *, const void *pos, int64_t n)
     return DC_OK;
 }
 
-const char *kKernelNames[DC_KERNEL_KINDS] = {"splat",  "smooth", "band_aggregate", "band_carry",
-                                             "band_final", "advect", "quality",   "reorder"};
+const char *kKernelNames[DC_KERNEL_KINDS] = {"splat",  "smooth",  "band_aggregate", "band_carry", "band_final",
+                                             "advect", "quality", "reorder",        "band_fused"};
 
 }  // namespace
 
@@ -453,6 +462,10 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
     if (ensure_qslots(c, 1) != DC_OK) return bail(DC_ERR_OOM);
     if (cudaMemset(c->status, 0, 256) != cudaSuccess) return bail(fail(DC_ERR_CUDA, "cudaMemset status"));
     if (prepare_kernels() != cudaSuccess) return bail(fail(DC_ERR_CUDA, "kernel attributes"));
+    // DECLUTTER_FUSED_BANDS=1: the three band phases as one cooperative
+    // launch on small grids (measured slower than three launches at 512^2)
+    const char *fz = getenv("DECLUTTER_FUSED_BANDS");
+    c->fused = fz && fz[0] == '1' && band_fused_available(c->g, c->mode, c->p.carry_mode, c->device);
     *out = c;
     return DC_OK;
 }
@@ -586,7 +599,7 @@ dc_status declutter_sync(dc_ctx *c)
     unsigned st = 0;
     DC_CUDA(cudaMemcpy(&st, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (st != 0) {
-        cudaMemset(c->status, 0, sizeof(unsigned));
+        cudaMemset(c->status, 0, 256);  // the status word and the grid-barrier words
         return fail((dc_status)st, "device status %u", st);
     }
     return DC_OK;

@@ -199,6 +199,9 @@ dc_status declutter_batch_create(const dc_params *base, const uint32_t *log2_res
         pp.log2_res = log2_res[p];
         dc_ctx *c = nullptr;
         if (dc_status st = declutter_create(&pp, device, b->stream, &c)) return bail(st);
+        // panels run as concurrent graph branches: no cooperative launches,
+        // whose CTAs must all be resident at once
+        c->fused = false;
         b->ctx.push_back(c);
         b->log2.push_back(log2_res[p]);
         b->cap.push_back(max_samples[p]);
@@ -262,6 +265,7 @@ dc_status declutter_batch_autotune(dc_batch *b, float *const *pos_xy, const int6
             pp.band_rows = T;
             dc_ctx *c = nullptr;
             if (dc_status st = declutter_create(&pp, b->device, b->stream, &c)) return st;
+            c->fused = false;
             if (dc_status st = prepare_regularize(c, b->cap[p], 1, 0)) {
                 declutter_destroy(c);
                 return st;

@@ -335,7 +335,16 @@ __device__ __forceinline__ void store_row(T *dst, const T (&v)[CPT], int c0, int
 // bands whose sums may reach 2^32 (the interleaved kernels below keep
 // band-local sums in 32 bits).  FINAL = false: write the band's compact
 // aggregate.  FINAL = true: combine with the carries and evaluate the outputs.
-template <int MODE, int CPT, bool FINAL>
+// carry loads: L2 (coherent with stores of other CTAs earlier in the same
+// launch, for the fused kernel) or the default cached path
+template <bool COH, typename Acc>
+__device__ __forceinline__ Acc ld_carry(const Acc *p)
+{
+    if constexpr (COH) return __ldcg(p);
+    else return *p;
+}
+
+template <int MODE, int CPT, bool FINAL, bool COH = false>
 __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
 {
     using Acc = typename ModeT<MODE>::Acc;
@@ -369,11 +378,11 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
 #pragma unroll
         for (int k = 0; k < CPT; ++k) {
             const int c = min(c0 + k, N - 1);
-            cvb[k] = cb[c];
-            Rk[k] = ce[c];
+            cvb[k] = ld_carry<COH>(cb + c);
+            Rk[k] = ld_carry<COH>(ce + c);
         }
-        Ctot = ce[N - 1];
-        CVbN = cb[N - 1];
+        Ctot = ld_carry<COH>(ce + N - 1);
+        CVbN = ld_carry<COH>(cb + N - 1);
         if constexpr (MODE == MODE_FLOAT) {
             const float NN = (float)N * (float)N;
             kappa = Ctot / NN;
@@ -470,9 +479,10 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
                 const int u = cc + j;
                 const int vi = cc - j + N - 1;
                 const Acc al = cvb[k] + arun[k];
-                const Acc at = (cb[N + (u - j0)] + Un[k]) - (cb[2 * N + T - 1 + (vi - (N - j0 - Tb))] + Vn[k]);
-                const Acc A = ce[N + u];
-                const Acc Bv = Ctot - ce[3 * N + vi];
+                const Acc at = (ld_carry<COH>(cb + N + (u - j0)) + Un[k]) -
+                               (ld_carry<COH>(cb + 2 * N + T - 1 + (vi - (N - j0 - Tb))) + Vn[k]);
+                const Acc A = ld_carry<COH>(ce + N + u);
+                const Acc Bv = Ctot - ld_carry<COH>(ce + 3 * N + vi);
                 const Acc R = Rk[k];
                 Acc w[8];
                 w[0] = al;
@@ -1324,24 +1334,26 @@ __global__ void __launch_bounds__(NT) agg_proj_kernel(BandArgs a, int log2N, int
 // [3N, 5N): diagonal v = lane - 3N - (N - 1).  Row b of the output holds
 // the sum over bands < b; row nb the total (the marginals).
 // ------------------------------------------------------------------------
-template <typename Acc>
-__device__ __forceinline__ Acc band_contrib(const Acc *__restrict__ ab, int b, int lane, int N, int T)
+template <typename Acc, bool COH = false>
+__device__ __forceinline__ Acc band_contrib(const Acc *ab, int b, int lane, int N, int T)
 {
+    // COH: L2 loads, for the fused kernel (records written by other CTAs of
+    // the same launch)
     const int j0 = b * T, Tb = min(T, N - j0), jl = j0 + Tb - 1;
-    if (lane < N) return ab[lane];
+    if (lane < N) return ld_carry<COH>(ab + lane);
     if (lane < 3 * N) {
         const int u = lane - N;
         if (u < j0) return Acc(0);
-        if (u < jl) return ab[3 * N + (u - j0)];
-        if (u <= jl + N - 1) return ab[N + (u - jl)];
-        return ab[3 * N + 2 * T];
+        if (u < jl) return ld_carry<COH>(ab + 3 * N + (u - j0));
+        if (u <= jl + N - 1) return ld_carry<COH>(ab + N + (u - jl));
+        return ld_carry<COH>(ab + 3 * N + 2 * T);
     }
     const int v = lane - 3 * N - (N - 1);
     if (v < -jl) return Acc(0);
-    if (v <= N - 1 - jl) return ab[2 * N + (v + jl)];
+    if (v <= N - 1 - jl) return ld_carry<COH>(ab + 2 * N + (v + jl));
     const int m = v - (N - 1 - jl);
-    if (m <= Tb - 1) return ab[3 * N + T + (Tb - 1 - m)];
-    return ab[3 * N + 2 * T];
+    if (m <= Tb - 1) return ld_carry<COH>(ab + 3 * N + T + (Tb - 1 - m));
+    return ld_carry<COH>(ab + 3 * N + 2 * T);
 }
 
 template <typename Acc> struct ScanSum {
@@ -1464,6 +1476,130 @@ __global__ void __launch_bounds__(1024) carry_kernel(const Acc *__restrict__ agg
         }
     }
     if (b_beg < nb && b_end == nb) carry[(size_t)nb * cs + lane] = pre.value();
+}
+
+// ------------------------------------------------------------------------
+// Aggregate, carries and final pass in one cooperative launch (grids below
+// 2048^2, where the three launches are latency-bound).  One CTA per band as
+// in band_kernel; between the phases a grid barrier (all CTAs are resident:
+// cooperative launch); the carries are computed by the CTAs together, CTA c
+// taking lanes [c LPC, c LPC + LPC) split into G = NT / LPC groups of bands.
+// ------------------------------------------------------------------------
+
+// Sense-reversing grid barrier on bar[0] (arrivals) and bar[1] (generation);
+// reusable across barriers and launches without a reset.  Waits at most one
+// second (then DC_ERR_TIMEOUT in status, and the CTA goes on).
+__device__ __noinline__ void grid_barrier(unsigned *bar, unsigned nblocks, unsigned *status)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g0) {
+                if (global_ns() - t0 > 1000000000ull) {
+                    if (status) atomicOr(status, (unsigned)DC_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+template <typename Acc, typename Sum>
+__device__ void carry_phase(const Acc *agg, Acc *carry, int N, int T, int nb, int agg_stride, Sum *s_part)
+{
+    const int NT = blockDim.x, t = threadIdx.x;
+    const int lanes = 5 * N;
+    const int cs = carry_stride(N, T);
+    const int LPC = (lanes + gridDim.x - 1) / gridDim.x;  // <= NT (checked by the launcher)
+    const int G = NT / LPC;
+    const int li = t % LPC, g = t / LPC;
+    const int lane = blockIdx.x * LPC + li;
+    const bool active = g < G && lane < lanes;
+    const int bpg = (nb + G - 1) / G;
+    const int b_beg = g * bpg, b_end = min(nb, b_beg + bpg);
+    // a group's contributions in registers (all loads in flight at once)
+    constexpr int kCache = 32;
+    Acc cache[kCache];
+    const bool cached = b_end - b_beg <= kCache;
+    Sum sm;
+    sm.zero();
+    if (active) {
+        if (cached) {
+#pragma unroll
+            for (int k = 0; k < kCache; ++k)
+                if (b_beg + k < b_end) cache[k] = band_contrib<Acc, true>(agg + (size_t)(b_beg + k) * agg_stride, b_beg + k, lane, N, T);
+#pragma unroll
+            for (int k = 0; k < kCache; ++k)
+                if (b_beg + k < b_end) sm.add(cache[k]);
+        } else {
+            for (int b = b_beg; b < b_end; ++b) sm.add(band_contrib<Acc, true>(agg + (size_t)b * agg_stride, b, lane, N, T));
+        }
+    }
+    if (g < G) s_part[t] = sm;
+    __syncthreads();
+    if (!active) return;
+    Sum pre;
+    pre.zero();
+    for (int q = 0; q < g; ++q) pre.add(s_part[q * LPC + li]);
+#pragma unroll
+    for (int k = 0; k < kCache; ++k) {
+        const int b = b_beg + k;
+        if (!cached || b >= b_end) break;
+        int o = -1;
+        const int j0 = b * T, Tb = min(T, N - j0);
+        if (lane < N) {
+            o = lane;
+        } else if (lane < 3 * N) {
+            const int w = lane - N - j0;
+            if (w >= 0 && w < N + Tb - 1) o = N + w;
+        } else {
+            const int w = lane - 3 * N - (N - j0 - Tb);
+            if (w >= 0 && w < N + Tb - 1) o = 2 * N + T - 1 + w;
+        }
+        if (o >= 0) carry[(size_t)b * cs + o] = pre.value();
+        pre.add(cache[k]);
+    }
+    for (int b = cached ? b_end : b_beg; b < b_end; ++b) {
+        int o = -1;
+        const int j0 = b * T, Tb = min(T, N - j0);
+        if (lane < N) {
+            o = lane;
+        } else if (lane < 3 * N) {
+            const int w = lane - N - j0;
+            if (w >= 0 && w < N + Tb - 1) o = N + w;
+        } else {
+            const int w = lane - 3 * N - (N - j0 - Tb);
+            if (w >= 0 && w < N + Tb - 1) o = 2 * N + T - 1 + w;
+        }
+        if (o >= 0) carry[(size_t)b * cs + o] = pre.value();
+        pre.add(band_contrib<Acc, true>(agg + (size_t)b * agg_stride, b, lane, N, T));
+    }
+    if (b_beg < nb && b_end == nb) carry[(size_t)nb * cs + lane] = pre.value();
+}
+
+template <int MODE, int CPT, typename Sum>
+__global__ void __launch_bounds__(CPT == 1 ? 64 : 512) band_fused_kernel(BandArgs aagg, BandArgs afin, int log2N, int T,
+                                                                        unsigned *bar)
+{
+    using Acc = typename ModeT<MODE>::Acc;
+    __shared__ Sum s_part[CPT == 1 ? 64 : 512];
+    band_body<MODE, CPT, false>(aagg, log2N, T);
+    grid_barrier(bar, gridDim.x, afin.status);
+    const int N = 1 << log2N;
+    carry_phase<Acc, Sum>(static_cast<const Acc *>(aagg.agg), static_cast<Acc *>(const_cast<void *>(afin.carry)), N,
+                          T, (N + T - 1) / T, aagg.agg_stride, s_part);
+    grid_barrier(bar, gridDim.x, afin.status);
+    band_body<MODE, CPT, true, true>(afin, log2N, T);
 }
 
 }  // namespace
@@ -1658,6 +1794,53 @@ cudaError_t launch_band_final(cudaStream_t s, const BandGeom &g, int mode, const
     case MODE_GRID64: return launch_band_mode<MODE_GRID64, true>(s, g, a);
     }
     return cudaErrorInvalidValue;
+}
+
+template <int MODE, typename Sum>
+static void (*fused_ptr(int CPT))(BandArgs, BandArgs, int, int, unsigned *)
+{
+    if (CPT == 1) return band_fused_kernel<MODE, 1, Sum>;
+    if (CPT == 4) return band_fused_kernel<MODE, 4, Sum>;
+    return nullptr;
+}
+static void (*fused_kernel_for(const BandGeom &g, int mode, int carry_mode))(BandArgs, BandArgs, int, int, unsigned *)
+{
+    if (g.log2N >= interleaved_min_log2(mode) || (mode != MODE_COUNT && mode != MODE_FLOAT)) return nullptr;
+    if (5 * g.T > g.NT) return nullptr;  // carry lanes of a CTA: at most one per thread
+    if (mode == MODE_COUNT) return fused_ptr<MODE_COUNT, ScanSum<uint32_t>>(g.CPT);
+    if (carry_mode == DC_CARRY_F64) return fused_ptr<MODE_FLOAT, ScanF64>(g.CPT);
+    return fused_ptr<MODE_FLOAT, ScanF2>(g.CPT);
+}
+
+bool band_fused_available(const BandGeom &g, int mode, int carry_mode, int device)
+{
+    auto k = fused_kernel_for(g, mode, carry_mode);
+    if (!k) return false;
+    int per_sm = 0, sms = 0, coop = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, g.NT, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return coop && per_sm * sms >= g.nb;
+}
+
+cudaError_t launch_band_fused(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const BandArgs &aagg,
+                              const BandArgs &afin, unsigned *bar)
+{
+    auto k = fused_kernel_for(g, mode, carry_mode);
+    if (!k) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g.nb);
+    cfg.blockDim = dim3(g.NT);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, aagg, afin, g.log2N, g.T, bar);
 }
 
 cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const void *agg, void *carry)

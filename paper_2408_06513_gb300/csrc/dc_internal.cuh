@@ -37,6 +37,10 @@ cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// word of the context's status buffer where the fused band kernel's grid
+// barrier (arrivals, generation) lives
+constexpr int kBarWord = 16;
+
 // Kernel kinds, in the order reported by declutter_profile_regularize().
 enum KernelKind {
     K_SPLAT = 0,
@@ -47,6 +51,7 @@ enum KernelKind {
     K_ADVECT = 5,
     K_QUALITY = 6,
     K_REORDER = 7,  // counting sort of the samples by pixel, and the way back
+    K_BAND_FUSED = 8,  // aggregate + carries + final pass in one cooperative launch
 };
 
 // Accumulation mode of the integral-image kernels.
@@ -127,6 +132,11 @@ cudaError_t launch_band_agg(cudaStream_t s, const BandGeom &g, int mode, const B
 cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const void *agg,
                          void *carry);
 cudaError_t launch_band_final(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a);
+// one cooperative launch of the three band phases (grids below 2048^2);
+// available when all CTAs fit on the device at once; bar: two device words
+bool band_fused_available(const BandGeom &g, int mode, int carry_mode, int device);
+cudaError_t launch_band_fused(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const BandArgs &aagg,
+                              const BandArgs &afin, unsigned *bar);
 int smooth_smem_bytes(int r);
 cudaError_t prepare_kernels();  // per-device kernel attributes; call with the device current
 void set_last_error(const char *msg);  // message returned by declutter_last_error()
@@ -158,7 +168,8 @@ struct dc_ctx {
     float2 *disp = nullptr;
     void *agg = nullptr;
     void *carry = nullptr;
-    unsigned *status = nullptr;
+    unsigned *status = nullptr;         // [0] sticky status; [kBarWord, +2) grid barrier of the fused band kernel
+    bool fused = false;                 // band phases as one cooperative launch (see band_fused_available)
     unsigned long long *qacc = nullptr; // [3 * (qslots)]
     int qslots = 0;
     float *hpos = nullptr;              // device staging for regularize_host

@@ -427,7 +427,11 @@ def test_regularize_host_matches_device(dc):
         dc.declutter_destroy(ctx)
 
 
-def test_profile_counts_launches(dc):
+@pytest.mark.parametrize("fused", ["1", "0"])
+def test_profile_counts_launches(dc, monkeypatch, fused):
+    # the three band phases run as one cooperative launch on small grids,
+    # or as three launches (DECLUTTER_FUSED_BANDS=0)
+    monkeypatch.setenv("DECLUTTER_FUSED_BANDS", fused)
     z, _ = synth.tiny_mixture()
     ctx = dc.declutter_create(7, kernel_r=2)
     try:
@@ -439,8 +443,29 @@ def test_profile_counts_launches(dc):
     k = prof["kernels"]
     assert prof["step_ms"] > 0
     assert k["splat"]["launches"] == 1
-    for name in ("smooth", "band_aggregate", "band_carry", "band_final", "advect"):
+    bands = ("band_fused",) if k["band_fused"]["launches"] else ("band_aggregate", "band_carry", "band_final")
+    if fused == "0":
+        assert bands != ("band_fused",)
+    for name in ("smooth", "advect") + bands:
         assert k[name]["launches"] == 3 and k[name]["ms"] >= 0
+
+
+@pytest.mark.parametrize("r", [0, 2])
+def test_fused_and_separate_band_launches_agree(dc, monkeypatch, r):
+    # bitwise: the fused launch runs the same code as the three launches
+    z, _ = synth.tiny_mixture()
+    outs = []
+    for fused in ("1", "0"):
+        monkeypatch.setenv("DECLUTTER_FUSED_BANDS", fused)
+        ctx = dc.declutter_create(9, kernel_r=r)
+        try:
+            pos = to_dev(z)
+            dc.regularize(ctx, pos, 4)
+            dc.declutter_sync(ctx)
+            outs.append(pos.cpu())
+        finally:
+            dc.declutter_destroy(ctx)
+    assert torch.equal(outs[0], outs[1])
 
 
 def test_bad_arguments_are_rejected(dc):
