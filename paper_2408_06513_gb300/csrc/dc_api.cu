@@ -185,7 +185,7 @@ cudaError_t enqueue_iterations(dc_ctx *c, cudaStream_t s, float *pos, int64_t n,
         rec.count(K_ADVECT);
         for (int t = 0; t < rec.times(K_ADVECT) && e == cudaSuccess; ++t)
             e = launch_advect(s, reinterpret_cast<float2 *>(ipos), n, c->disp, c->g.log2N, c->p.pixel_center,
-                              c->p.clamp_positions, need_next ? cb[nxt] : nullptr);
+                              c->p.clamp_positions, need_next ? cb[nxt] : nullptr, ipos != pos);
         if (e != cudaSuccess) return e;
         if (n_tracers > 0) {
             // massless tracers: moved by the same field, not splatted
@@ -461,6 +461,10 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
     }
     if (ensure_qslots(c, 1) != DC_OK) return bail(DC_ERR_OOM);
     if (cudaMemset(c->status, 0, 256) != cudaSuccess) return bail(fail(DC_ERR_CUDA, "cudaMemset status"));
+    if (cudaMallocHost(&c->status_host, sizeof(unsigned)) != cudaSuccess) {
+        c->status_host = nullptr;
+        return bail(fail(DC_ERR_OOM, "pinned status word"));
+    }
     if (prepare_kernels() != cudaSuccess) return bail(fail(DC_ERR_CUDA, "kernel attributes"));
     // DECLUTTER_FUSED_BANDS=1: the three band phases as one cooperative
     // launch on small grids (measured slower than three launches at 512^2)
@@ -486,6 +490,7 @@ dc_status declutter_destroy(dc_ctx *c)
     cudaFree(c->agg);
     cudaFree(c->carry);
     cudaFree(c->status);
+    if (c->status_host) cudaFreeHost(c->status_host);
     cudaFree(c->qacc);
     cudaFree(c->hpos);
     cudaFree(c->spos);
@@ -595,9 +600,10 @@ dc_status declutter_sync(dc_ctx *c)
 {
     if (dc_status st = check_ctx(c)) return st;
     DeviceGuard guard(c->device);
+    // the status word comes back with the same synchronisation
+    DC_CUDA(cudaMemcpyAsync(c->status_host, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     DC_CUDA(cudaStreamSynchronize(c->stream));
-    unsigned st = 0;
-    DC_CUDA(cudaMemcpy(&st, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    const unsigned st = *c->status_host;
     if (st != 0) {
         cudaMemset(c->status, 0, 256);  // the status word and the grid-barrier words
         return fail((dc_status)st, "device status %u", st);

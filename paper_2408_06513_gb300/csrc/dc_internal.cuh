@@ -109,9 +109,10 @@ struct GraphEntry {
 
 // Launchers (all enqueue on `s`; return cudaGetLastError()).
 cudaError_t launch_splat(cudaStream_t s, const float2 *pos, int64_t n, uint32_t *counts, int log2N);
-// counts_next: if not null, the moved samples are also splatted into it (must be zero)
+// counts_next: if not null, the moved samples are also splatted into it (must
+// be zero); sorted: the samples are in pixel order (run aggregation pays)
 cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *disp, int log2N,
-                          int pixel_center, int clamp, uint32_t *counts_next);
+                          int pixel_center, int clamp, uint32_t *counts_next, bool sorted = false);
 cudaError_t launch_quality(cudaStream_t s, const uint32_t *counts, int log2N, unsigned long long *acc);
 // reordering of the samples by pixel: the first splat also records each
 // sample's rank within its pixel; exclusive scan of the counts into cursor
@@ -170,6 +171,7 @@ struct dc_ctx {
     void *carry = nullptr;
     unsigned *status = nullptr;         // [0] sticky status; [kBarWord, +2) grid barrier of the fused band kernel
     bool fused = false;                 // band phases as one cooperative launch (see band_fused_available)
+    unsigned *status_host = nullptr;    // pinned copy of the status word read by declutter_sync
     unsigned long long *qacc = nullptr; // [3 * (qslots)]
     int qslots = 0;
     float *hpos = nullptr;              // device staging for regularize_host

@@ -145,6 +145,21 @@ __device__ __forceinline__ void splat_warp(uint32_t *__restrict__ counts, int pi
     if (valid && lane == __ffs(m) - 1) atomicAdd(&counts[pix], (uint32_t)__popc(m));
 }
 
+// The same with runs: after the reordering by pixel, lanes holding the same
+// pixel are mostly neighbours, so a run of equal keys (found with one shuffle
+// and one ballot) shares one atomic; cheaper than __match_any_sync, but equal
+// keys that are not adjacent get separate atomics (faster up to 1024^2).
+__device__ __forceinline__ void splat_warp_runs(uint32_t *__restrict__ counts, int pix, bool valid)
+{
+    const int lane = threadIdx.x & 31;
+    const int key = valid ? pix : -1 - lane;
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || key != prev);
+    const unsigned above = heads & ~((2u << lane) - 1u);  // heads after this lane (lane 31: none)
+    const int next = above ? __ffs(above) - 1 : 32;
+    if (valid && ((heads >> lane) & 1u)) atomicAdd(&counts[pix], (uint32_t)(next - lane));
+}
+
 // Samples are processed in aligned pairs (one float4 = two samples), two
 // pairs per thread and loop trip, so that all eight corner gathers of a trip
 // are independent.  The loop runs warp-uniformly so that, with counts_next
@@ -153,6 +168,7 @@ __device__ __forceinline__ void splat_warp(uint32_t *__restrict__ counts, int pi
 // pixel, neighbouring lanes mostly hold samples of the same pixel.  A sample
 // before the first 16-byte boundary and one left after the last pair are
 // handled by thread 0 of block 0.
+template <bool RUNS>
 __global__ void __launch_bounds__(kThreads) advect_kernel(float2 *__restrict__ pos, int64_t n,
                                                           const float2 *__restrict__ D, int log2N, float off,
                                                           int clamp, uint32_t *__restrict__ counts_next)
@@ -190,10 +206,17 @@ __global__ void __launch_bounds__(kThreads) advect_kernel(float2 *__restrict__ p
         if (v1) pp[q1] = make_float4(m0.z.x, m0.z.y, m1.z.x, m1.z.y);
         if (v2) pp[q2] = make_float4(m2.z.x, m2.z.y, m3.z.x, m3.z.y);
         if (counts_next) {
-            splat_warp(counts_next, m0.pix, v1);
-            splat_warp(counts_next, m1.pix, v1);
-            splat_warp(counts_next, m2.pix, v2);
-            splat_warp(counts_next, m3.pix, v2);
+            if constexpr (RUNS) {
+                splat_warp_runs(counts_next, m0.pix, v1);
+                splat_warp_runs(counts_next, m1.pix, v1);
+                splat_warp_runs(counts_next, m2.pix, v2);
+                splat_warp_runs(counts_next, m3.pix, v2);
+            } else {
+                splat_warp(counts_next, m0.pix, v1);
+                splat_warp(counts_next, m1.pix, v1);
+                splat_warp(counts_next, m2.pix, v2);
+                splat_warp(counts_next, m3.pix, v2);
+            }
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -410,12 +433,17 @@ cudaError_t launch_splat(cudaStream_t s, const float2 *pos, int64_t n, uint32_t 
 }
 
 cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *disp, int log2N,
-                          int pixel_center, int clamp, uint32_t *counts_next)
+                          int pixel_center, int clamp, uint32_t *counts_next, bool sorted)
 {
     if (n <= 0) return cudaSuccess;
-    // two pairs (four samples) per thread and trip
-    return launch_kernel(advect_kernel, dim3(grid_for((n + 3) / 4, kThreads, 152 * 8)), dim3(kThreads), 0, s, pos, n,
-                         disp, log2N, pixel_center ? 0.5f : 0.0f, clamp, counts_next);
+    // two pairs (four samples) per thread and trip; run aggregation for
+    // samples in pixel order up to 1024^2 (measured faster there)
+    const dim3 grid(grid_for((n + 3) / 4, kThreads, 152 * 8));
+    if (sorted && log2N <= 10)
+        return launch_kernel(advect_kernel<true>, grid, dim3(kThreads), 0, s, pos, n, disp, log2N,
+                             pixel_center ? 0.5f : 0.0f, clamp, counts_next);
+    return launch_kernel(advect_kernel<false>, grid, dim3(kThreads), 0, s, pos, n, disp, log2N,
+                         pixel_center ? 0.5f : 0.0f, clamp, counts_next);
 }
 
 int64_t reorder_scan_chunk(int log2N)
