@@ -335,6 +335,27 @@ void dc::finish_regularize(dc_ctx *c, int64_t n, int iters, int metrics)
 
 void dc::read_metrics(const dc_ctx *c, const unsigned long long *acc, double *out3) { metrics_from_acc(c, acc, out3); }
 
+PanelDesc dc::panel_desc(const dc_ctx *c, float *pos, int64_t n)
+{
+    PanelDesc d{};
+    d.pos = reinterpret_cast<float2 *>(pos);
+    d.n = n;
+    d.counts[0] = c->counts_buf[0];
+    d.counts[1] = c->counts_buf[1];
+    d.dens = c->dens;
+    d.disp = c->disp;
+    d.spos = c->spos;
+    d.rank = c->rank;
+    d.inv = c->inv;
+    d.cursor = c->cursor;
+    d.partials = c->partials;
+    d.qacc = c->qacc;
+    d.status = c->status;
+    d.band = band_args(c, nullptr, c->mode, n);
+    d.band.disp = c->disp;
+    return d;
+}
+
 bool dc::pdl_enabled()
 {
     static const bool on = [] {

@@ -113,9 +113,8 @@ __global__ void __launch_bounds__(256) smooth_kernel(const uint32_t *__restrict_
 // pass's output rows are padded to an odd stride so that the horizontal
 // pass's lanes (one row each) read conflict-free.
 template <int TS, int R>
-__global__ void __launch_bounds__(256) smooth_win_kernel(const uint32_t *__restrict__ counts,
-                                                         float *__restrict__ dens, int log2N, GaussW w,
-                                                         uint32_t *__restrict__ zero_out)
+__device__ __forceinline__ void smooth_win_body(const uint32_t *__restrict__ counts, float *__restrict__ dens,
+                                                int log2N, const GaussW &w, uint32_t *__restrict__ zero_out)
 {
     extern __shared__ float s_sm[];
     const int N = 1 << log2N;
@@ -188,6 +187,13 @@ __global__ void __launch_bounds__(256) smooth_win_kernel(const uint32_t *__restr
         for (int k = 0; k < R; k += 4)
             *reinterpret_cast<float4 *>(o + k) = make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
     }
+}
+template <int TS, int R>
+__global__ void __launch_bounds__(256) smooth_win_kernel(const uint32_t *__restrict__ counts,
+                                                         float *__restrict__ dens, int log2N, GaussW w,
+                                                         uint32_t *__restrict__ zero_out)
+{
+    smooth_win_body<TS, R>(counts, dens, log2N, w, zero_out);
 }
 
 // ------------------------------------------------------------------------
@@ -1395,8 +1401,8 @@ struct ScanF64 {
 constexpr int kCarryCache = 16;
 
 template <typename Acc, typename Sum>
-__global__ void __launch_bounds__(1024) carry_kernel(const Acc *__restrict__ agg, Acc *__restrict__ carry,
-                                                     int log2N, int T, int nb, int agg_stride)
+__device__ __forceinline__ void carry_body(const Acc *__restrict__ agg, Acc *__restrict__ carry, int log2N, int T,
+                                           int nb, int agg_stride)
 {
     const int N = 1 << log2N;
     const int lanes = 5 * N;
@@ -1476,6 +1482,12 @@ __global__ void __launch_bounds__(1024) carry_kernel(const Acc *__restrict__ agg
         }
     }
     if (b_beg < nb && b_end == nb) carry[(size_t)nb * cs + lane] = pre.value();
+}
+template <typename Acc, typename Sum>
+__global__ void __launch_bounds__(1024) carry_kernel(const Acc *__restrict__ agg, Acc *__restrict__ carry,
+                                                     int log2N, int T, int nb, int agg_stride)
+{
+    carry_body<Acc, Sum>(agg, carry, log2N, T, nb, agg_stride);
 }
 
 // ------------------------------------------------------------------------
@@ -1602,6 +1614,44 @@ __global__ void __launch_bounds__(CPT == 1 ? 64 : 512) band_fused_kernel(BandArg
     band_body<MODE, CPT, true, true>(afin, log2N, T);
 }
 
+// ------------------------------------------------------------------------
+// Batched wrappers: panel blockIdx.y (blockIdx.z for the smoothing tiles) of
+// a PanelDesc table
+// ------------------------------------------------------------------------
+template <int TS, int R>
+__global__ void __launch_bounds__(256) smooth_batched_kernel(const PanelDesc *__restrict__ tab, int log2N, GaussW w,
+                                                             int cur, int zero_next)
+{
+    const PanelDesc &d = tab[blockIdx.z];
+    smooth_win_body<TS, R>(d.counts[cur], d.dens, log2N, w, zero_next ? d.counts[cur ^ 1] : nullptr);
+}
+
+template <int MODE, int CPT, bool FINAL>
+__global__ void __launch_bounds__(CPT == 1 ? 64 : 512) band_batched_kernel(const PanelDesc *__restrict__ tab,
+                                                                          int log2N, int T, int cur, int zero_next)
+{
+    const PanelDesc &d = tab[blockIdx.y];
+    BandArgs a = d.band;
+    if constexpr (MODE == MODE_FLOAT) {
+        a.src = d.dens;
+        a.zero_out = nullptr;
+    } else {
+        a.src = d.counts[cur];
+        a.zero_out = (!FINAL && zero_next) ? d.counts[cur ^ 1] : nullptr;
+    }
+    if constexpr (FINAL) a.zero_out = nullptr;
+    band_body<MODE, CPT, FINAL>(a, log2N, T);
+}
+
+template <typename Acc, typename Sum>
+__global__ void __launch_bounds__(1024) carry_batched_kernel(const PanelDesc *__restrict__ tab, int log2N, int T,
+                                                             int nb, int agg_stride)
+{
+    const PanelDesc &d = tab[blockIdx.y];
+    carry_body<Acc, Sum>(static_cast<const Acc *>(d.band.agg), static_cast<Acc *>(const_cast<void *>(d.band.carry)),
+                         log2N, T, nb, agg_stride);
+}
+
 }  // namespace
 
 int smooth_smem_bytes(int r)
@@ -1667,6 +1717,12 @@ cudaError_t prepare_kernels()
                                  smooth_win_smem_bytes(64, 64));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(smooth_win_kernel<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smooth_win_smem_bytes(32, 64));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(smooth_batched_kernel<64, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smooth_win_smem_bytes(64, 64));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(smooth_batched_kernel<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smooth_win_smem_bytes(32, 64));
     if (e == cudaSuccess) e = allow_band2_smem_all<MODE_COUNT>();
     if (e == cudaSuccess) e = allow_band2_smem_all<MODE_FLOAT>();
@@ -1874,6 +1930,68 @@ cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_
                              static_cast<float *>(carry), g.log2N, g.T, g.nb, g.agg_stride);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_smooth_batched(cudaStream_t s, const PanelDesc *tab, int P, int log2N, const GaussW &w, int cur,
+                                  bool zero_next)
+{
+    const int N = 1 << log2N;
+    if (N < 32) return cudaErrorInvalidValue;
+    const int TS = smooth_tile(log2N);
+    const size_t bytes = (size_t)smooth_win_smem_bytes(TS, w.r);
+    const dim3 grid(N / TS, N / TS, P);
+    if (TS == 64)
+        return launch_kernel(smooth_batched_kernel<64, 8>, grid, dim3(256), bytes, s, tab, log2N, w, cur,
+                             zero_next ? 1 : 0);
+    return launch_kernel(smooth_batched_kernel<32, 8>, grid, dim3(256), bytes, s, tab, log2N, w, cur,
+                         zero_next ? 1 : 0);
+}
+
+template <int MODE, int CPT>
+static cudaError_t band_batched_mode(cudaStream_t s, const BandGeom &g, int carry_mode, const PanelDesc *tab, int P,
+                                     int cur, bool zero_next)
+{
+    const dim3 grid(g.nb, P), block(g.NT);
+    cudaError_t e =
+        launch_kernel(band_batched_kernel<MODE, CPT, false>, grid, block, 0, s, tab, g.log2N, g.T, cur, zero_next ? 1 : 0);
+    if (e != cudaSuccess) return e;
+    int ng = 32;  // groups of bands per carry block: as launch_carry, so that
+    {             // float carries are summed in the same order as for one panel
+        const int nblk = (g.lanes + 31) / 32;
+        int cap = 152 * 64 / nblk;
+        if (cap > 32) cap = 32;
+        if (cap > g.nb) cap = g.nb;
+        ng = 1;
+        while (2 * ng <= cap) ng *= 2;
+        const int need = (g.nb + kCarryCache - 1) / kCarryCache;
+        if (ng < need) ng = need > 32 ? 32 : need;
+    }
+    const dim3 cgrid((g.lanes + 31) / 32, P), cblock(32 * ng);
+    if constexpr (MODE == MODE_COUNT)
+        e = launch_kernel(carry_batched_kernel<uint32_t, ScanSum<uint32_t>>, cgrid, cblock, 0, s, tab, g.log2N, g.T,
+                          g.nb, g.agg_stride);
+    else if (carry_mode == DC_CARRY_F64)
+        e = launch_kernel(carry_batched_kernel<float, ScanF64>, cgrid, cblock, 0, s, tab, g.log2N, g.T, g.nb,
+                          g.agg_stride);
+    else
+        e = launch_kernel(carry_batched_kernel<float, ScanF2>, cgrid, cblock, 0, s, tab, g.log2N, g.T, g.nb,
+                          g.agg_stride);
+    if (e != cudaSuccess) return e;
+    return launch_kernel(band_batched_kernel<MODE, CPT, true>, grid, block, 0, s, tab, g.log2N, g.T, cur, 0);
+}
+
+cudaError_t launch_band_batched(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const PanelDesc *tab,
+                                int P, int cur, bool zero_next)
+{
+    if (g.log2N >= interleaved_min_log2(mode)) return cudaErrorInvalidValue;  // per-thread-contiguous kernels only
+    if (mode == MODE_COUNT) {
+        if (g.CPT == 1) return band_batched_mode<MODE_COUNT, 1>(s, g, carry_mode, tab, P, cur, zero_next);
+        if (g.CPT == 4) return band_batched_mode<MODE_COUNT, 4>(s, g, carry_mode, tab, P, cur, zero_next);
+    } else if (mode == MODE_FLOAT) {
+        if (g.CPT == 1) return band_batched_mode<MODE_FLOAT, 1>(s, g, carry_mode, tab, P, cur, zero_next);
+        if (g.CPT == 4) return band_batched_mode<MODE_FLOAT, 4>(s, g, carry_mode, tab, P, cur, zero_next);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace dc

@@ -99,6 +99,22 @@ struct BandArgs {
     unsigned *status;         // sticky device status word (DC_ERR_TIMEOUT), or null
 };
 
+// One panel of a batch of same-resolution panels, for the batched launches:
+// kernel wrappers take a device array of these and read their panel's
+// buffers from entry blockIdx.y (blockIdx.z for the 2D smoothing grid).
+struct PanelDesc {
+    float2 *pos;              // the caller's samples
+    int64_t n;
+    uint32_t *counts[2];      // count grids (iterations alternate)
+    float *dens;
+    float2 *disp;
+    float2 *spos;             // samples in pixel order
+    uint32_t *rank, *inv, *cursor, *partials;
+    unsigned long long *qacc; // [3 * iters]
+    unsigned *status;
+    BandArgs band;            // agg, carry, disp, mu, d0, inv_den_exact, status (src and zero_out per launch)
+};
+
 struct GraphEntry {
     const void *pos = nullptr;
     int64_t n = 0;
@@ -139,6 +155,21 @@ bool band_fused_available(const BandGeom &g, int mode, int carry_mode, int devic
 cudaError_t launch_band_fused(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const BandArgs &aagg,
                               const BandArgs &afin, unsigned *bar);
 int smooth_smem_bytes(int r);
+// batched launches over P same-resolution panels (tab: device PanelDesc[P]);
+// max_n: the largest n; which / cur: count grid index; nxt: grid to splat the
+// moved samples into, or -1
+cudaError_t launch_zero_batched(cudaStream_t s, const PanelDesc *tab, int P, int log2N, int which, int qacc_words);
+cudaError_t launch_splat_rank_batched(cudaStream_t s, const PanelDesc *tab, int P, int64_t max_n, int log2N);
+cudaError_t launch_reorder_batched(cudaStream_t s, const PanelDesc *tab, int P, int64_t max_n, int log2N);
+cudaError_t launch_advect_batched(cudaStream_t s, const PanelDesc *tab, int P, int64_t max_n, int log2N,
+                                  int pixel_center, int clamp, int nxt, bool sorted);
+cudaError_t launch_quality_batched(cudaStream_t s, const PanelDesc *tab, int P, int log2N, int which, int slot);
+cudaError_t launch_back_batched(cudaStream_t s, const PanelDesc *tab, int P, int64_t max_n);
+cudaError_t launch_smooth_batched(cudaStream_t s, const PanelDesc *tab, int P, int log2N, const GaussW &w, int cur,
+                                  bool zero_next);
+// aggregate, carries and final pass (grids below 2048^2, the per-thread-contiguous band kernels)
+cudaError_t launch_band_batched(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const PanelDesc *tab,
+                                int P, int cur, bool zero_next);
 cudaError_t prepare_kernels();  // per-device kernel attributes; call with the device current
 void set_last_error(const char *msg);  // message returned by declutter_last_error()
 // regularize() building blocks for the batched runtime: buffers for n samples
@@ -148,6 +179,8 @@ dc_status prepare_regularize(dc_ctx *c, int64_t n, int iters, int metrics);
 cudaError_t enqueue_regularize(dc_ctx *c, cudaStream_t s, float *pos, int64_t n, int iters, int metrics);
 void finish_regularize(dc_ctx *c, int64_t n, int iters, int metrics);
 void read_metrics(const dc_ctx *c, const unsigned long long *acc, double *out3);
+// the panel table entry of a context and its samples (after prepare_regularize)
+PanelDesc panel_desc(const dc_ctx *c, float *pos, int64_t n);
 
 }  // namespace dc
 

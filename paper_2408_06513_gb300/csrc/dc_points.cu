@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kThreads) splat_kernel(const float2 *__restric
 // The same splat, also recording each sample's rank among the samples of its
 // pixel (the counter value its atomic increment returned), for the
 // reordering below.  Ranks of a pixel's samples are exactly 0 .. count - 1.
-__global__ void __launch_bounds__(kThreads) splat_rank_kernel(const float2 *__restrict__ pos, int64_t n,
+__device__ __forceinline__ void splat_rank_body(const float2 *__restrict__ pos, int64_t n,
                                                               uint32_t *__restrict__ counts, int log2N,
                                                               uint32_t *__restrict__ rank)
 {
@@ -84,6 +84,12 @@ __global__ void __launch_bounds__(kThreads) splat_rank_kernel(const float2 *__re
             if (k < n) rank[k] = lead + __popc(m[u] & ((1u << lane) - 1u));
         }
     }
+}
+__global__ void __launch_bounds__(kThreads) splat_rank_kernel(const float2 *__restrict__ pos, int64_t n,
+                                                              uint32_t *__restrict__ counts, int log2N,
+                                                              uint32_t *__restrict__ rank)
+{
+    splat_rank_body(pos, n, counts, log2N, rank);
 }
 
 // Bilinear advection (Sec. 4.2): p = x N (- 1/2 for pixel centres),
@@ -169,9 +175,8 @@ __device__ __forceinline__ void splat_warp_runs(uint32_t *__restrict__ counts, i
 // before the first 16-byte boundary and one left after the last pair are
 // handled by thread 0 of block 0.
 template <bool RUNS>
-__global__ void __launch_bounds__(kThreads) advect_kernel(float2 *__restrict__ pos, int64_t n,
-                                                          const float2 *__restrict__ D, int log2N, float off,
-                                                          int clamp, uint32_t *__restrict__ counts_next)
+__device__ __forceinline__ void advect_body(float2 *__restrict__ pos, int64_t n, const float2 *__restrict__ D,
+                                            int log2N, float off, int clamp, uint32_t *__restrict__ counts_next)
 {
     pdl_wait();
     const float fN = (float)(1 << log2N);
@@ -229,6 +234,13 @@ __global__ void __launch_bounds__(kThreads) advect_kernel(float2 *__restrict__ p
         }
     }
 }
+template <bool RUNS>
+__global__ void __launch_bounds__(kThreads) advect_kernel(float2 *__restrict__ pos, int64_t n,
+                                                          const float2 *__restrict__ D, int log2N, float off,
+                                                          int clamp, uint32_t *__restrict__ counts_next)
+{
+    advect_body<RUNS>(pos, n, D, log2N, off, clamp, counts_next);
+}
 
 // ------------------------------------------------------------------------
 // Reordering of the samples by pixel (a counting sort keyed by the splat
@@ -255,7 +267,7 @@ __device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *s_red)
 }
 
 // partials[b] = sum of counts[b * chunk, (b + 1) * chunk)
-__global__ void __launch_bounds__(kScanThreads) scan_partials_kernel(const uint32_t *__restrict__ counts, int64_t M,
+__device__ __forceinline__ void scan_partials_body(const uint32_t *__restrict__ counts, int64_t M,
                                                                      int64_t chunk, uint32_t *__restrict__ partials)
 {
     __shared__ uint32_t s_red[kScanThreads / 32];
@@ -270,9 +282,14 @@ __global__ void __launch_bounds__(kScanThreads) scan_partials_kernel(const uint3
     v = block_sum_u32(v, s_red);
     if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
+__global__ void __launch_bounds__(kScanThreads) scan_partials_kernel(const uint32_t *__restrict__ counts, int64_t M,
+                                                                     int64_t chunk, uint32_t *__restrict__ partials)
+{
+    scan_partials_body(counts, M, chunk, partials);
+}
 
 // cursor[k] = sum of counts[0, k) (exclusive prefix in row-major order).
-__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t *__restrict__ counts, int64_t M,
+__device__ __forceinline__ void scan_apply_body(const uint32_t *__restrict__ counts, int64_t M,
                                                                   int64_t chunk, const uint32_t *__restrict__ partials,
                                                                   uint32_t *__restrict__ cursor)
 {
@@ -315,6 +332,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t
         carry += tile;
     }
 }
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t *__restrict__ counts, int64_t M,
+                                                                  int64_t chunk, const uint32_t *__restrict__ partials,
+                                                                  uint32_t *__restrict__ cursor)
+{
+    scan_apply_body(counts, M, chunk, partials, cursor);
+}
 
 __device__ __forceinline__ int sample_pixel(float2 z, int log2N, float fN)
 {
@@ -329,7 +352,7 @@ __device__ __forceinline__ int sample_pixel(float2 z, int log2N, float fN)
 // [prefix(p), prefix(p) + counts(p)), so every slot < n when cursor and rank
 // come from the splat of these same samples; a slot out of range sets
 // DC_ERR_RANGE in the status word and is skipped.
-__global__ void __launch_bounds__(kThreads) reorder_scatter_kernel(const float2 *__restrict__ pos, int64_t n,
+__device__ __forceinline__ void reorder_scatter_body(const float2 *__restrict__ pos, int64_t n,
                                                                    int log2N, const uint32_t *__restrict__ cursor,
                                                                    const uint32_t *__restrict__ rank,
                                                                    float2 *__restrict__ spos,
@@ -351,9 +374,18 @@ __global__ void __launch_bounds__(kThreads) reorder_scatter_kernel(const float2 
         }
     }
 }
+__global__ void __launch_bounds__(kThreads) reorder_scatter_kernel(const float2 *__restrict__ pos, int64_t n,
+                                                                   int log2N, const uint32_t *__restrict__ cursor,
+                                                                   const uint32_t *__restrict__ rank,
+                                                                   float2 *__restrict__ spos,
+                                                                   uint32_t *__restrict__ inv,
+                                                                   unsigned *__restrict__ status)
+{
+    reorder_scatter_body(pos, n, log2N, cursor, rank, spos, inv, status);
+}
 
 // pos[k] = spos[inv[k]]
-__global__ void __launch_bounds__(kThreads) reorder_gather_back_kernel(const float2 *__restrict__ spos,
+__device__ __forceinline__ void reorder_gather_back_body(const float2 *__restrict__ spos,
                                                                        const uint32_t *__restrict__ inv, int64_t n,
                                                                        float2 *__restrict__ pos,
                                                                        unsigned *__restrict__ status)
@@ -366,10 +398,17 @@ __global__ void __launch_bounds__(kThreads) reorder_gather_back_kernel(const flo
         else atomicOr(status, (unsigned)DC_ERR_RANGE);
     }
 }
+__global__ void __launch_bounds__(kThreads) reorder_gather_back_kernel(const float2 *__restrict__ spos,
+                                                                       const uint32_t *__restrict__ inv, int64_t n,
+                                                                       float2 *__restrict__ pos,
+                                                                       unsigned *__restrict__ status)
+{
+    reorder_gather_back_body(spos, inv, n, pos, status);
+}
 
 // Sec. 6.2: sum of squared 4x4-bin counts and number of occupied pixels.
 // acc[0] += sum of b^2 over bins, acc[1] += occupied pixels, acc[2] += sum b.
-__global__ void __launch_bounds__(kThreads) quality_kernel(const uint32_t *__restrict__ counts, int log2N,
+__device__ __forceinline__ void quality_body(const uint32_t *__restrict__ counts, int log2N,
                                                            unsigned long long *__restrict__ acc)
 {
     pdl_wait();
@@ -413,6 +452,11 @@ __global__ void __launch_bounds__(kThreads) quality_kernel(const uint32_t *__res
         atomicAdd(&acc[1], c);
         atomicAdd(&acc[2], t);
     }
+}
+__global__ void __launch_bounds__(kThreads) quality_kernel(const uint32_t *__restrict__ counts, int log2N,
+                                                           unsigned long long *__restrict__ acc)
+{
+    quality_body(counts, log2N, acc);
 }
 
 int grid_for(int64_t n, int per_block, int max_blocks)
@@ -496,6 +540,120 @@ cudaError_t launch_quality(cudaStream_t s, const uint32_t *counts, int log2N, un
     const int B = (1 << log2N) >> 2;
     return launch_kernel(quality_kernel, dim3(grid_for((int64_t)B * B, kThreads, 152 * 4)), dim3(kThreads), 0, s,
                          counts, log2N, acc);
+}
+
+// ------------------------------------------------------------------------
+// Batched wrappers: panel blockIdx.y of a PanelDesc table
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) zero_batched_kernel(const PanelDesc *__restrict__ tab, int log2N,
+                                                                int which, int qacc_words)
+{
+    pdl_wait();
+    const PanelDesc &d = tab[blockIdx.y];
+    const int64_t M4 = ((int64_t)1 << (2 * log2N)) / 4;
+    uint4 *c = reinterpret_cast<uint4 *>(d.counts[which]);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M4; k += (int64_t)gridDim.x * blockDim.x)
+        c[k] = make_uint4(0u, 0u, 0u, 0u);
+    if (blockIdx.x == 0)
+        for (int k = threadIdx.x; k < qacc_words; k += blockDim.x) d.qacc[k] = 0ull;
+}
+__global__ void __launch_bounds__(kThreads) splat_rank_batched_kernel(const PanelDesc *__restrict__ tab, int log2N)
+{
+    const PanelDesc &d = tab[blockIdx.y];
+    splat_rank_body(d.pos, d.n, d.counts[0], log2N, d.rank);
+}
+__global__ void __launch_bounds__(kScanThreads) scan_partials_batched_kernel(const PanelDesc *__restrict__ tab,
+                                                                             int64_t M, int64_t chunk)
+{
+    const PanelDesc &d = tab[blockIdx.y];
+    if (d.n <= 0) return;  // no samples: no sort buffers, nothing to reorder
+    scan_partials_body(d.counts[0], M, chunk, d.partials);
+}
+__global__ void __launch_bounds__(kScanThreads) scan_apply_batched_kernel(const PanelDesc *__restrict__ tab,
+                                                                          int64_t M, int64_t chunk)
+{
+    const PanelDesc &d = tab[blockIdx.y];
+    if (d.n <= 0) return;
+    scan_apply_body(d.counts[0], M, chunk, d.partials, d.cursor);
+}
+__global__ void __launch_bounds__(kThreads) scatter_batched_kernel(const PanelDesc *__restrict__ tab, int log2N)
+{
+    const PanelDesc &d = tab[blockIdx.y];
+    reorder_scatter_body(d.pos, d.n, log2N, d.cursor, d.rank, d.spos, d.inv, d.status);
+}
+template <bool RUNS>
+__global__ void __launch_bounds__(kThreads) advect_batched_kernel(const PanelDesc *__restrict__ tab, int log2N,
+                                                                  float off, int clamp, int nxt)
+{
+    const PanelDesc &d = tab[blockIdx.y];
+    advect_body<RUNS>(d.spos, d.n, d.disp, log2N, off, clamp, nxt >= 0 ? d.counts[nxt] : nullptr);
+}
+__global__ void __launch_bounds__(kThreads) quality_batched_kernel(const PanelDesc *__restrict__ tab, int log2N,
+                                                                   int which, int slot)
+{
+    const PanelDesc &d = tab[blockIdx.y];
+    quality_body(d.counts[which], log2N, d.qacc + 3 * slot);
+}
+__global__ void __launch_bounds__(kThreads) back_batched_kernel(const PanelDesc *__restrict__ tab)
+{
+    const PanelDesc &d = tab[blockIdx.y];
+    reorder_gather_back_body(d.spos, d.inv, d.n, d.pos, d.status);
+}
+
+
+
+cudaError_t launch_zero_batched(cudaStream_t s, const PanelDesc *tab, int P, int log2N, int which, int qacc_words)
+{
+    const int64_t M4 = ((int64_t)1 << (2 * log2N)) / 4;
+    return launch_kernel(zero_batched_kernel, dim3(grid_for(M4, kThreads, 64), P), dim3(kThreads), 0, s, tab, log2N,
+                         which, qacc_words);
+}
+
+cudaError_t launch_splat_rank_batched(cudaStream_t s, const PanelDesc *tab, int P, int64_t max_n, int log2N)
+{
+    if (max_n <= 0) return cudaSuccess;
+    return launch_kernel(splat_rank_batched_kernel, dim3(grid_for(max_n, kThreads, 152 * 16), P), dim3(kThreads), 0,
+                         s, tab, log2N);
+}
+
+cudaError_t launch_reorder_batched(cudaStream_t s, const PanelDesc *tab, int P, int64_t max_n, int log2N)
+{
+    if (max_n <= 0) return cudaSuccess;
+    const int64_t M = (int64_t)1 << (2 * log2N);
+    const int64_t chunk = reorder_scan_chunk(log2N);
+    const unsigned nch = (unsigned)((M + chunk - 1) / chunk);
+    cudaError_t e = launch_kernel(scan_partials_batched_kernel, dim3(nch, P), dim3(kScanThreads), 0, s, tab, M, chunk);
+    if (e == cudaSuccess)
+        e = launch_kernel(scan_apply_batched_kernel, dim3(nch, P), dim3(kScanThreads), 0, s, tab, M, chunk);
+    if (e == cudaSuccess)
+        e = launch_kernel(scatter_batched_kernel, dim3(grid_for(max_n, kThreads, 152 * 8), P), dim3(kThreads), 0, s,
+                          tab, log2N);
+    return e;
+}
+
+cudaError_t launch_advect_batched(cudaStream_t s, const PanelDesc *tab, int P, int64_t max_n, int log2N,
+                                  int pixel_center, int clamp, int nxt, bool sorted)
+{
+    if (max_n <= 0) return cudaSuccess;
+    const dim3 grid(grid_for((max_n + 3) / 4, kThreads, 152 * 8), P);
+    if (sorted && log2N <= 10)
+        return launch_kernel(advect_batched_kernel<true>, grid, dim3(kThreads), 0, s, tab, log2N,
+                             pixel_center ? 0.5f : 0.0f, clamp, nxt);
+    return launch_kernel(advect_batched_kernel<false>, grid, dim3(kThreads), 0, s, tab, log2N,
+                         pixel_center ? 0.5f : 0.0f, clamp, nxt);
+}
+
+cudaError_t launch_quality_batched(cudaStream_t s, const PanelDesc *tab, int P, int log2N, int which, int slot)
+{
+    const int B = 1 << (log2N - 2);
+    return launch_kernel(quality_batched_kernel, dim3(grid_for((int64_t)B * B, kThreads, 152 * 4), P), dim3(kThreads),
+                         0, s, tab, log2N, which, slot);
+}
+
+cudaError_t launch_back_batched(cudaStream_t s, const PanelDesc *tab, int P, int64_t max_n)
+{
+    if (max_n <= 0) return cudaSuccess;
+    return launch_kernel(back_batched_kernel, dim3(grid_for(max_n, kThreads, 152 * 8), P), dim3(kThreads), 0, s, tab);
 }
 
 }  // namespace dc
