@@ -208,7 +208,7 @@ dc_status declutter_sync(dc_ctx *ctx);
  *   reset_src: device float[2n] copied into pos_xy before each run (outside
  *              the timed span), or NULL to let the samples keep moving.
  * Any output pointer may be NULL.  Synchronises. */
-#define DC_KERNEL_KINDS 9
+#define DC_KERNEL_KINDS 10
 dc_status declutter_profile_regularize(dc_ctx *ctx, float *pos_xy, const float *reset_src, int64_t n,
                                        int32_t iters, int32_t reps, float *step_ms_out,
                                        float *kernel_ms_out, int32_t *launches_out);

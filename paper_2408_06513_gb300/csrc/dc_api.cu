@@ -101,7 +101,10 @@ cudaError_t enqueue_density(dc_ctx *c, cudaStream_t s, const float *pos, int64_t
     return e;
 }
 
-cudaError_t enqueue_inims(dc_ctx *c, cudaStream_t s, const BandArgs &a, int mode, Recorder &rec)
+// With smooth_counts (float mode, c->smooth_agg) the aggregate pass also
+// smooths smooth_counts into c->dens (= a.src) and zeroes smooth_zero.
+cudaError_t enqueue_inims(dc_ctx *c, cudaStream_t s, const BandArgs &a, int mode, Recorder &rec,
+                          const uint32_t *smooth_counts = nullptr, uint32_t *smooth_zero = nullptr)
 {
     cudaError_t e = cudaSuccess;
     if (c->fused && mode != MODE_GRID64) {
@@ -113,8 +116,14 @@ cudaError_t enqueue_inims(dc_ctx *c, cudaStream_t s, const BandArgs &a, int mode
             e = launch_band_fused(s, c->g, mode, c->p.carry_mode, a, f, c->status + kBarWord);
         return e;
     }
-    rec.count(K_BAND_AGG);
-    for (int t = 0; t < rec.times(K_BAND_AGG) && e == cudaSuccess; ++t) e = launch_band_agg(s, c->g, mode, a);
+    if (smooth_counts) {
+        rec.count(K_SMOOTH_AGG);
+        for (int t = 0; t < rec.times(K_SMOOTH_AGG) && e == cudaSuccess; ++t)
+            e = launch_smooth_agg(s, c->g, a, c->w, smooth_counts, c->dens, smooth_zero);
+    } else {
+        rec.count(K_BAND_AGG);
+        for (int t = 0; t < rec.times(K_BAND_AGG) && e == cudaSuccess; ++t) e = launch_band_agg(s, c->g, mode, a);
+    }
     if (e != cudaSuccess) return e;
     rec.count(K_CARRY);
     for (int t = 0; t < rec.times(K_CARRY) && e == cudaSuccess; ++t)
@@ -171,7 +180,8 @@ cudaError_t enqueue_iterations(dc_ctx *c, cudaStream_t s, float *pos, int64_t n,
                 if (e != cudaSuccess) return e;
             }
         }
-        if (c->mode == MODE_FLOAT) {
+        const bool smooth_fused = c->mode == MODE_FLOAT && c->smooth_agg;
+        if (c->mode == MODE_FLOAT && !smooth_fused) {
             rec.count(K_SMOOTH);
             for (int t = 0; t < rec.times(K_SMOOTH) && e == cudaSuccess; ++t)
                 e = launch_smooth(s, cb[cur], c->dens, c->g.log2N, c->w, need_next ? cb[nxt] : nullptr);
@@ -181,7 +191,9 @@ cudaError_t enqueue_iterations(dc_ctx *c, cudaStream_t s, float *pos, int64_t n,
         BandArgs a = band_args(c, src, c->mode, n);
         a.disp = c->disp;
         a.zero_out = (c->mode != MODE_FLOAT && need_next) ? cb[nxt] : nullptr;
-        if ((e = enqueue_inims(c, s, a, c->mode, rec)) != cudaSuccess) return e;
+        e = smooth_fused ? enqueue_inims(c, s, a, c->mode, rec, cb[cur], need_next ? cb[nxt] : nullptr)
+                         : enqueue_inims(c, s, a, c->mode, rec);
+        if (e != cudaSuccess) return e;
         rec.count(K_ADVECT);
         for (int t = 0; t < rec.times(K_ADVECT) && e == cudaSuccess; ++t)
             e = launch_advect(s, reinterpret_cast<float2 *>(ipos), n, c->disp, c->g.log2N, c->p.pixel_center,
@@ -306,7 +318,7 @@ dc_status check_samples(const dc_ctx *, const void *pos, int64_t n)
 }
 
 const char *kKernelNames[DC_KERNEL_KINDS] = {"splat",  "smooth",  "band_aggregate", "band_carry", "band_final",
-                                             "advect", "quality", "reorder",        "band_fused"};
+                                             "advect", "quality", "reorder",        "band_fused", "smooth_aggregate"};
 
 }  // namespace
 
@@ -491,6 +503,10 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
     // launch on small grids (measured slower than three launches at 512^2)
     const char *fz = getenv("DECLUTTER_FUSED_BANDS");
     c->fused = fz && fz[0] == '1' && band_fused_available(c->g, c->mode, c->p.carry_mode, c->device);
+    // the smoothing runs inside the aggregate pass where it fits
+    // (DECLUTTER_FUSED_SMOOTH=0: separate launches, the same bits)
+    const char *fs = getenv("DECLUTTER_FUSED_SMOOTH");
+    c->smooth_agg = !(fs && fs[0] == '0') && !c->fused && c->mode == MODE_FLOAT && smooth_agg_available(c->g, c->w);
     *out = c;
     return DC_OK;
 }

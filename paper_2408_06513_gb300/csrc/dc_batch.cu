@@ -250,8 +250,12 @@ dc_status declutter_batch_create(const dc_params *base, const uint32_t *log2_res
         dc_ctx *c = nullptr;
         if (dc_status st = declutter_create(&pp, device, b->stream, &c)) return bail(st);
         // panels run as concurrent graph branches: no cooperative launches,
-        // whose CTAs must all be resident at once
+        // whose CTAs must all be resident at once; and the smoothing as its
+        // own launch (the fused kernel's wide CTAs, 3/4 of them idle during
+        // the aggregate, measured slower when panels overlap: 11.5 ms
+        // against 10.2 ms for 120 panels, the same bits)
         c->fused = false;
+        c->smooth_agg = false;
         b->ctx.push_back(c);
         b->log2.push_back(log2_res[p]);
         b->cap.push_back(max_samples[p]);
@@ -315,7 +319,8 @@ dc_status declutter_batch_autotune(dc_batch *b, float *const *pos_xy, const int6
             pp.band_rows = T;
             dc_ctx *c = nullptr;
             if (dc_status st = declutter_create(&pp, b->device, b->stream, &c)) return st;
-            c->fused = false;
+            c->fused = false;  // as in declutter_batch_create
+            c->smooth_agg = false;
             if (dc_status st = prepare_regularize(c, b->cap[p], 1, 0)) {
                 declutter_destroy(c);
                 return st;

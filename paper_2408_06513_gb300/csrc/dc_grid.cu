@@ -60,6 +60,9 @@ constexpr unsigned kFull = 0xffffffffu;
 // the totals (the marginals).
 __host__ __device__ __forceinline__ int carry_stride(int N, int T) { return (3 * N + 2 * T - 2 + 3) & ~3; }
 
+// shared memory the fused smoothing-aggregate kernel may use
+constexpr size_t kSmoothAggSmemMax = 200 * 1024;
+
 // ------------------------------------------------------------------------
 // Smoothing: one 2D tile per CTA with a halo of r on each side, vertical
 // then horizontal pass in shared memory; reflect border (-1 -> 0, N -> N-1).
@@ -350,13 +353,42 @@ __device__ __forceinline__ Acc ld_carry(const Acc *p)
     else return *p;
 }
 
-template <int MODE, int CPT, bool FINAL, bool COH = false>
-__device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
+// A band row from shared memory (float mode, rows of N values, CPT a
+// multiple of 4): the same values as load_row reads from the grid.
+template <int CPT>
+__device__ __forceinline__ void load_row_smem(const float *row, int c0, float mu, float (&v)[CPT])
 {
+#pragma unroll
+    for (int q = 0; q < CPT / 4; ++q) {
+        const float4 f = *reinterpret_cast<const float4 *>(row + c0 + 4 * q);
+        v[4 * q] = f.x - mu;
+        v[4 * q + 1] = f.y - mu;
+        v[4 * q + 2] = f.z - mu;
+        v[4 * q + 3] = f.w - mu;
+    }
+}
+
+// Barrier of the threads running band_body: the whole CTA, or (NAMED) the
+// first nt threads on barrier 1 while the CTA's other warps have left.
+template <bool NAMED>
+__device__ __forceinline__ void band_sync(int nt)
+{
+    if constexpr (NAMED) asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+    else __syncthreads();
+}
+
+// SROWS: the band's rows come from shared memory (srows, row r of the band at
+// srows + r N) instead of a.src, and the first N / CPT threads of the CTA run
+// the band (synchronising on barrier 1); float mode, CPT a multiple of 4.
+template <int MODE, int CPT, bool FINAL, bool COH = false, bool SROWS = false>
+__device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T, const float *srows = nullptr)
+{
+    static_assert(!SROWS || (MODE == MODE_FLOAT && CPT % 4 == 0), "shared-memory rows: float mode, CPT % 4 == 0");
     using Acc = typename ModeT<MODE>::Acc;
     const int N = 1 << log2N;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int nw = blockDim.x >> 5;
+    const int nthr = SROWS ? N / CPT : (int)blockDim.x;
+    const int nw = nthr >> 5;
     const int b = blockIdx.x;
     const int j0 = b * T;
     const int Tb = min(T, N - j0);  // rows of this band (the last one may be shorter)
@@ -399,14 +431,18 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
     }
 
     Acc vnext[CPT];
-    load_row<MODE, CPT>(a.src, log2N, j0, c0, a.mu, vnext);
+    if constexpr (SROWS) load_row_smem<CPT>(srows, c0, a.mu, vnext);
+    else load_row<MODE, CPT>(a.src, log2N, j0, c0, a.mu, vnext);
     for (int r = 0; r < Tb; ++r) {
         const int j = j0 + r;
         const int par = r & 1;
         Acc v[CPT];
 #pragma unroll
         for (int k = 0; k < CPT; ++k) v[k] = vnext[k];
-        if (r + 1 < Tb) load_row<MODE, CPT>(a.src, log2N, j + 1, c0, a.mu, vnext);  // prefetch
+        if (r + 1 < Tb) {  // prefetch
+            if constexpr (SROWS) load_row_smem<CPT>(srows + ((size_t)(r + 1) << log2N), c0, a.mu, vnext);
+            else load_row<MODE, CPT>(a.src, log2N, j + 1, c0, a.mu, vnext);
+        }
         if constexpr (!FINAL) {
             if (a.zero_out) {
                 uint32_t zz[CPT];
@@ -433,7 +469,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
             if (lane >= o) x = x + y;
         }
         if (lane == 31) s_wt[par][warp] = x;
-        __syncthreads();
+        band_sync<SROWS>(nthr);
         Acc wv = lane < nw ? s_wt[par][lane] : Acc(0);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -572,7 +608,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
         //   alpha, U, V: recurrence state at the band's last row;
         //   U0[r] = U(0, j0 + r); E[r] = V(N-1, j0 + r) + row totals below row r;
         //   S = band total.
-        __syncthreads();
+        band_sync<SROWS>(nthr);
         Acc *ag = static_cast<Acc *>(a.agg) + (size_t)b * a.agg_stride;
 #pragma unroll
         for (int k = 0; k < CPT; ++k) {
@@ -583,7 +619,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T)
                 ag[2 * N + c] = Vo[k];
             }
         }
-        for (int rr = t; rr < Tb; rr += blockDim.x) {
+        for (int rr = t; rr < Tb; rr += nthr) {
             Acc below = Acc(0);
             for (int q = rr + 1; q < Tb; ++q) below = below + s_RT[q];
             ag[3 * N + rr] = s_U0[rr];
@@ -604,6 +640,142 @@ template <int MODE, int CPT, bool FINAL>
 __device__ __noinline__ void band_body_wide(BandArgs a, int log2N, int T)
 {
     band_body<MODE, CPT, FINAL>(a, log2N, T);
+}
+
+// ------------------------------------------------------------------------
+// Smoothing fused into the aggregate pass (float mode, 128^2 .. 1024^2).
+// CTA b smooths the rows of its band from the counts (its rows plus r halo
+// rows on each side, reflected at the border), writes them to dens for the
+// final pass and aggregates the band from shared memory.  The taps are
+// summed as in smooth_win_body (vertical, then horizontal, one fused
+// multiply-add per tap in tap order), and band_body runs with the same CPT
+// as band_kernel, so the densities and aggregates are bit-identical to the
+// separate launches'.  The CTA has up to 4x the band's N / CPT threads: all
+// of them load and smooth, then the band's threads aggregate while the
+// others leave.  Windows of R outputs per thread in both passes; the
+// vertical pass's rows are stored at x + x / 32 so that the horizontal
+// pass's lanes (R columns apart) read distinct banks.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ int swz32(int x) { return x + (x >> 5); }
+
+template <int CPT, int R>
+__global__ void __launch_bounds__(1024) smooth_agg_kernel(BandArgs a, int log2N, int T, GaussW w,
+                                                         const uint32_t *__restrict__ counts,
+                                                         float *__restrict__ dens, uint32_t *__restrict__ zero_out)
+{
+    extern __shared__ __align__(16) float s_sa[];
+    const int N = 1 << log2N;
+    const int r = w.r;
+    const int W = N + 2 * r;
+    const int j0 = blockIdx.x * T;
+    const int Tb = min(T, N - j0);
+    const int nseg = (Tb + R - 1) / R;
+    const int H = Tb + 2 * r;          // input rows with the halo
+    const int Hal = nseg * R + 2 * r;  // rows the R-windows touch (>= H)
+    const int Ws = swz32(W - 1) + 1;
+    float *s_in = s_sa;                                                // Hal x W
+    float *s_mid = s_sa + (size_t)((T + R - 1) / R * R + 2 * r) * W;  // Tb x Ws, swizzled columns
+    float *s_rows = s_sa;  // Tb x N (reuses s_in after the vertical pass)
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    pdl_wait();
+    // input rows: the interior by 16-byte loads, eight in flight a thread,
+    // the r reflected columns on each side, zeros below row H
+    {
+        const int q4 = log2N - 2;  // uint4 a row = N / 4
+        const int total = Hal << q4;
+        for (int base = 0; base < total; base += 8 * nthr) {
+            uint4 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = base + k * nthr + tid;
+                const int yy = i >> q4;
+                v[k] = make_uint4(0u, 0u, 0u, 0u);
+                if (i < total && yy < H) {
+                    const uint4 *crow = reinterpret_cast<const uint4 *>(
+                        counts + ((size_t)reflect_index(j0 + yy - r, N) << log2N));
+                    v[k] = crow[i & ((1 << q4) - 1)];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = base + k * nthr + tid;
+                if (i < total) {
+                    float *d = s_in + (size_t)(i >> q4) * W + r + 4 * (i & ((1 << q4) - 1));
+                    d[0] = (float)v[k].x;
+                    d[1] = (float)v[k].y;
+                    d[2] = (float)v[k].z;
+                    d[3] = (float)v[k].w;
+                }
+            }
+        }
+        for (int i = tid; i < Hal * 2 * r; i += nthr) {
+            const int yy = i / (2 * r), e = i - yy * (2 * r);
+            const int xx = e < r ? e : N + e;  // halo columns [0, r) and [N + r, N + 2r)
+            float x = 0.0f;
+            if (yy < H)
+                x = (float)counts[((size_t)reflect_index(j0 + yy - r, N) << log2N) + reflect_index(xx - r, N)];
+            s_in[(size_t)yy * W + xx] = x;
+        }
+    }
+    if (zero_out) {
+        uint4 *z = reinterpret_cast<uint4 *>(zero_out + ((size_t)j0 << log2N));
+        for (int i = tid; i < (Tb << log2N) / 4; i += nthr) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncthreads();
+    // vertical: s_mid[y][xx] = sum_t g[t] s_in[y + t][xx]
+    for (int item = tid; item < nseg * W; item += blockDim.x) {
+        const int seg = item / W, xx = item - seg * W;
+        const int y0 = seg * R;
+        float acc[R], win[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k + 1 < R; ++k) win[k + 1] = s_in[(size_t)(y0 + k) * W + xx];
+#pragma unroll R
+        for (int t = 0; t <= 2 * r; ++t) {
+#pragma unroll
+            for (int k = 0; k + 1 < R; ++k) win[k] = win[k + 1];
+            win[R - 1] = s_in[(size_t)(y0 + t + R - 1) * W + xx];
+            const float g = w.g[t];
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] = fmaf(g, win[k], acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            if (y0 + k < Tb) s_mid[(size_t)(y0 + k) * Ws + swz32(xx)] = acc[k];
+    }
+    __syncthreads();
+    // horizontal: d_r[y][x] = sum_t g[t] s_mid[y][x + t]
+    const int segs = N / R;
+    for (int item = tid; item < Tb * segs; item += blockDim.x) {
+        const int y = item / segs, x0 = (item - y * segs) * R;
+        const float *row = s_mid + (size_t)y * Ws;
+        float acc[R], win[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k + 1 < R; ++k) win[k + 1] = row[swz32(x0 + k)];
+#pragma unroll R
+        for (int t = 0; t <= 2 * r; ++t) {
+#pragma unroll
+            for (int k = 0; k + 1 < R; ++k) win[k] = win[k + 1];
+            win[R - 1] = row[swz32(x0 + t + R - 1)];
+            const float g = w.g[t];
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] = fmaf(g, win[k], acc[k]);
+        }
+        float *o = dens + ((size_t)(j0 + y) << log2N) + x0;
+        float *so = s_rows + ((size_t)y << log2N) + x0;
+#pragma unroll
+        for (int k = 0; k < R; k += 4) {
+            const float4 v = make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
+            *reinterpret_cast<float4 *>(o + k) = v;
+            *reinterpret_cast<float4 *>(so + k) = v;
+        }
+    }
+    __syncthreads();
+    if (tid >= N / CPT) return;  // the band's N / CPT threads go on (barrier 1)
+    band_body<MODE_FLOAT, CPT, false, false, true>(a, log2N, T, s_rows);
 }
 
 // ------------------------------------------------------------------------
@@ -1724,9 +1896,16 @@ cudaError_t prepare_kernels()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(smooth_batched_kernel<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smooth_win_smem_bytes(32, 64));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(smooth_agg_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmoothAggSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(smooth_agg_kernel<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmoothAggSmemMax);
     if (e == cudaSuccess) e = allow_band2_smem_all<MODE_COUNT>();
     if (e == cudaSuccess) e = allow_band2_smem_all<MODE_FLOAT>();
     if (e == cudaSuccess) e = allow_band2_smem_all<MODE_GRID64>();
+    if (e == cudaSuccess) e = prepare_point_kernels();
     return e;
 }
 
@@ -1746,6 +1925,36 @@ cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, i
     const int bytes = smooth_smem_bytes(w.r);
     dim3 grid(N / TW, N / TW);
     return launch_kernel(smooth_kernel, grid, dim3(256), (size_t)bytes, s, counts, dens, log2N, w, zero_out);
+}
+
+// Smoothing fused into the aggregate pass: windows of 4 rows for bands of
+// up to 4 rows, else 8; shared memory for the input rows (with halo and the
+// windows' overrun) and the vertical pass's swizzled rows.
+static int smooth_agg_R(int T) { return T <= 4 ? 4 : 8; }
+static size_t smooth_agg_smem_bytes(const BandGeom &g, int r)
+{
+    const int R = smooth_agg_R(g.T);
+    const int W = g.N + 2 * r;
+    const int Ws = (W - 1) + ((W - 1) >> 5) + 1;
+    return 4 * ((size_t)((g.T + R - 1) / R * R + 2 * r) * W + (size_t)g.T * Ws);
+}
+bool smooth_agg_available(const BandGeom &g, const GaussW &w)
+{
+    return g.N >= 128 && g.log2N < interleaved_min_log2(MODE_FLOAT) && g.CPT == 4 && w.r >= 1 &&
+           smooth_agg_smem_bytes(g, w.r) <= kSmoothAggSmemMax;
+}
+
+cudaError_t launch_smooth_agg(cudaStream_t s, const BandGeom &g, const BandArgs &a, const GaussW &w,
+                              const uint32_t *counts, float *dens, uint32_t *zero_out)
+{
+    if (!smooth_agg_available(g, w)) return cudaErrorInvalidValue;
+    const size_t smem = smooth_agg_smem_bytes(g, w.r);
+    const int nt = 4 * g.NT < 1024 ? 4 * g.NT : 1024;  // g.NT = N / 4 band threads
+    if (smooth_agg_R(g.T) == 4)
+        return launch_kernel(smooth_agg_kernel<4, 4>, dim3(g.nb), dim3(nt), smem, s, a, g.log2N, g.T, w, counts,
+                             dens, zero_out);
+    return launch_kernel(smooth_agg_kernel<4, 8>, dim3(g.nb), dim3(nt), smem, s, a, g.log2N, g.T, w, counts, dens,
+                         zero_out);
 }
 
 // Ring slots of the interleaved kernels: up to 128 KB of rows for the

@@ -52,6 +52,7 @@ enum KernelKind {
     K_QUALITY = 6,
     K_REORDER = 7,  // counting sort of the samples by pixel, and the way back
     K_BAND_FUSED = 8,  // aggregate + carries + final pass in one cooperative launch
+    K_SMOOTH_AGG = 9,  // smoothing and the aggregate pass in one launch (float mode, 128^2 .. 1024^2)
 };
 
 // Accumulation mode of the integral-image kernels.
@@ -146,6 +147,11 @@ cudaError_t launch_reorder_back(cudaStream_t s, const float2 *spos, const uint32
 cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, int log2N, const GaussW &w,
                           uint32_t *zero_out);
 cudaError_t launch_band_agg(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a);
+// smoothing of counts into dens fused with the float-mode aggregate pass
+// (a.src = dens); zero_out as in launch_smooth
+bool smooth_agg_available(const BandGeom &g, const GaussW &w);
+cudaError_t launch_smooth_agg(cudaStream_t s, const BandGeom &g, const BandArgs &a, const GaussW &w,
+                              const uint32_t *counts, float *dens, uint32_t *zero_out);
 cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const void *agg,
                          void *carry);
 cudaError_t launch_band_final(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a);
@@ -171,6 +177,7 @@ cudaError_t launch_smooth_batched(cudaStream_t s, const PanelDesc *tab, int P, i
 cudaError_t launch_band_batched(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const PanelDesc *tab,
                                 int P, int cur, bool zero_next);
 cudaError_t prepare_kernels();  // per-device kernel attributes; call with the device current
+cudaError_t prepare_point_kernels();  // part of prepare_kernels: launch shapes of the sample kernels
 void set_last_error(const char *msg);  // message returned by declutter_last_error()
 // regularize() building blocks for the batched runtime: buffers for n samples
 // (outside any capture), the iteration sequence on stream s, and the
@@ -204,6 +211,7 @@ struct dc_ctx {
     void *carry = nullptr;
     unsigned *status = nullptr;         // [0] sticky status; [kBarWord, +2) grid barrier of the fused band kernel
     bool fused = false;                 // band phases as one cooperative launch (see band_fused_available)
+    bool smooth_agg = false;            // smoothing fused into the aggregate pass (see smooth_agg_available)
     unsigned *status_host = nullptr;    // pinned copy of the status word read by declutter_sync
     unsigned long long *qacc = nullptr; // [3 * (qslots)]
     int qslots = 0;

@@ -1,5 +1,7 @@
 // Per-sample kernels: splat (Sec. 4.1), advection (Sec. 4.2) and the
 // Sec. 6.2 quality reduction over the count grid.
+#include <atomic>
+
 #include "dc_internal.cuh"
 
 namespace dc {
@@ -467,7 +469,37 @@ int grid_for(int64_t n, int per_block, int max_blocks)
     return (int)b;
 }
 
+// CTAs of the advection kernel resident on the whole GPU at once, per device
+// (set by prepare_kernels): its grid is at most one wave, the grid-stride
+// loop with the next trip's samples prefetched covering the rest (1.6 waves
+// of one trip each measured slower at 1M samples).
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_advect_wave[kMaxDevices];
+
+int advect_wave()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return 152 * 4;
+    }
+    const int w = g_advect_wave[dev].load(std::memory_order_relaxed);
+    return w > 0 ? w : 152 * 4;
+}
+
 }  // namespace
+
+cudaError_t prepare_point_kernels()
+{
+    int dev = 0, sms = 0, p0 = 0, p1 = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p0, advect_kernel<false>, kThreads, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, advect_kernel<true>, kThreads, 0);
+    if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices && sms > 0 && p0 > 0 && p1 > 0)
+        g_advect_wave[dev].store((p0 < p1 ? p0 : p1) * sms, std::memory_order_relaxed);
+    return e;
+}
 
 cudaError_t launch_splat(cudaStream_t s, const float2 *pos, int64_t n, uint32_t *counts, int log2N)
 {
@@ -480,9 +512,10 @@ cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *
                           int pixel_center, int clamp, uint32_t *counts_next, bool sorted)
 {
     if (n <= 0) return cudaSuccess;
-    // two pairs (four samples) per thread and trip; run aggregation for
-    // samples in pixel order up to 1024^2 (measured faster there)
-    const dim3 grid(grid_for((n + 3) / 4, kThreads, 152 * 8));
+    // two pairs (four samples) per thread and trip, at most one wave; run
+    // aggregation for samples in pixel order up to 1024^2 (measured faster
+    // there)
+    const dim3 grid(grid_for((n + 3) / 4, kThreads, advect_wave()));
     if (sorted && log2N <= 10)
         return launch_kernel(advect_kernel<true>, grid, dim3(kThreads), 0, s, pos, n, disp, log2N,
                              pixel_center ? 0.5f : 0.0f, clamp, counts_next);

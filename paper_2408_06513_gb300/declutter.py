@@ -37,7 +37,7 @@ __all__ = [
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdeclutter.so")
-KERNEL_KINDS = 9
+KERNEL_KINDS = 10
 
 DC_CARRY_COMPENSATED = 0
 DC_CARRY_F64 = 1

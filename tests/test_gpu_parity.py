@@ -427,11 +427,13 @@ def test_regularize_host_matches_device(dc):
         dc.declutter_destroy(ctx)
 
 
-@pytest.mark.parametrize("fused", ["1", "0"])
-def test_profile_counts_launches(dc, monkeypatch, fused):
+@pytest.mark.parametrize("fused,fused_smooth", [("1", "1"), ("0", "1"), ("0", "0")])
+def test_profile_counts_launches(dc, monkeypatch, fused, fused_smooth):
     # the three band phases run as one cooperative launch on small grids,
-    # or as three launches (DECLUTTER_FUSED_BANDS=0)
+    # or as three launches (DECLUTTER_FUSED_BANDS=0); the smoothing runs
+    # inside the aggregate pass unless DECLUTTER_FUSED_SMOOTH=0
     monkeypatch.setenv("DECLUTTER_FUSED_BANDS", fused)
+    monkeypatch.setenv("DECLUTTER_FUSED_SMOOTH", fused_smooth)
     z, _ = synth.tiny_mixture()
     ctx = dc.declutter_create(7, kernel_r=2)
     try:
@@ -443,11 +445,44 @@ def test_profile_counts_launches(dc, monkeypatch, fused):
     k = prof["kernels"]
     assert prof["step_ms"] > 0
     assert k["splat"]["launches"] == 1
-    bands = ("band_fused",) if k["band_fused"]["launches"] else ("band_aggregate", "band_carry", "band_final")
+    if k["band_fused"]["launches"]:
+        names = ("smooth", "band_fused")
+    elif fused_smooth == "1":
+        names = ("smooth_aggregate", "band_carry", "band_final")
+    else:
+        names = ("smooth", "band_aggregate", "band_carry", "band_final")
     if fused == "0":
-        assert bands != ("band_fused",)
-    for name in ("smooth", "advect") + bands:
+        assert "band_fused" not in names
+    for name in ("advect",) + names:
         assert k[name]["launches"] == 3 and k[name]["ms"] >= 0
+    for name in set(k) - set(names) - {"advect", "splat", "reorder", "quality"}:
+        assert k[name]["launches"] == 0, name
+
+
+@pytest.mark.parametrize("log2,r,band_rows", [(7, 2, 0), (8, 2, 0), (8, 5, 3), (9, 4, 0), (9, 4, 5),
+                                               (9, 12, 7), (10, 8, 0), (10, 3, 16)])
+def test_fused_smoothing_matches_separate_launches(dc, monkeypatch, log2, r, band_rows):
+    # bitwise: smoothing inside the aggregate pass (windows of 4 or 8 rows,
+    # ragged last bands) against the smoothing kernel plus the aggregate pass
+    rng = np.random.default_rng(log2 * 100 + r)
+    z = rng.beta(2.0, 5.0, size=(60_000, 2)).astype(np.float32)
+    outs, us = [], []
+    for fs in ("1", "0"):
+        monkeypatch.setenv("DECLUTTER_FUSED_SMOOTH", fs)
+        ctx = dc.declutter_create(log2, kernel_r=r, band_rows=band_rows)
+        try:
+            pos = to_dev(z)
+            us.append(dc.regularize(ctx, pos, 3, uniformity=True))
+            dc.declutter_sync(ctx)
+            if fs == "1":
+                prof = dc.declutter_profile_regularize(ctx, to_dev(z), 1, reps=1)
+                assert prof["kernels"]["smooth_aggregate"]["launches"] == 1
+                assert prof["kernels"]["smooth"]["launches"] == 0
+            outs.append(pos.cpu())
+        finally:
+            dc.declutter_destroy(ctx)
+    assert torch.equal(outs[0], outs[1])
+    assert us[0] == us[1]
 
 
 @pytest.mark.parametrize("r", [0, 2])
