@@ -1512,26 +1512,40 @@ __global__ void __launch_bounds__(NT) agg_proj_kernel(BandArgs a, int log2N, int
 // [3N, 5N): diagonal v = lane - 3N - (N - 1).  Row b of the output holds
 // the sum over bands < b; row nb the total (the marginals).
 // ------------------------------------------------------------------------
+// Index in band b's compact aggregate of its contribution to line `lane`
+// (-1: none).  Selects rather than branches; the lane family (vertical,
+// anti-diagonal, diagonal) is uniform across a warp since N % 32 == 0.
+__device__ __forceinline__ int contrib_index(int b, int lane, int N, int T)
+{
+    const int j0 = b * T, Tb = min(T, N - j0), jl = j0 + Tb - 1;
+    const int S = 3 * N + 2 * T;  // band total
+    if (lane < N) return lane;
+    if (lane < 3 * N) {
+        const int u = lane - N;
+        return u < j0 ? -1 : (u < jl ? 3 * N + (u - j0) : (u <= jl + N - 1 ? N + (u - jl) : S));
+    }
+    const int v = lane - 3 * N - (N - 1);
+    const int m = v - (N - 1 - jl);
+    return v < -jl ? -1 : (m <= 0 ? 2 * N + (v + jl) : (m <= Tb - 1 ? 3 * N + T + (Tb - 1 - m) : S));
+}
+
+// Where band b's carry row keeps line `lane` (-1: outside its windows).
+__device__ __forceinline__ int carry_slot(int b, int lane, int N, int T)
+{
+    if (lane < N) return lane;
+    const int j0 = b * T, Tb = min(T, N - j0);
+    const int o = lane < 3 * N ? lane - N - j0 : lane - 3 * N - (N - j0 - Tb);
+    const int base = lane < 3 * N ? N : 2 * N + T - 1;
+    return (o >= 0 && o < N + Tb - 1) ? base + o : -1;
+}
+
 template <typename Acc, bool COH = false>
 __device__ __forceinline__ Acc band_contrib(const Acc *ab, int b, int lane, int N, int T)
 {
     // COH: L2 loads, for the fused kernel (records written by other CTAs of
     // the same launch)
-    const int j0 = b * T, Tb = min(T, N - j0), jl = j0 + Tb - 1;
-    if (lane < N) return ld_carry<COH>(ab + lane);
-    if (lane < 3 * N) {
-        const int u = lane - N;
-        if (u < j0) return Acc(0);
-        if (u < jl) return ld_carry<COH>(ab + 3 * N + (u - j0));
-        if (u <= jl + N - 1) return ld_carry<COH>(ab + N + (u - jl));
-        return ld_carry<COH>(ab + 3 * N + 2 * T);
-    }
-    const int v = lane - 3 * N - (N - 1);
-    if (v < -jl) return Acc(0);
-    if (v <= N - 1 - jl) return ld_carry<COH>(ab + 2 * N + (v + jl));
-    const int m = v - (N - 1 - jl);
-    if (m <= Tb - 1) return ld_carry<COH>(ab + 3 * N + T + (Tb - 1 - m));
-    return ld_carry<COH>(ab + 3 * N + 2 * T);
+    const int i = contrib_index(b, lane, N, T);
+    return i >= 0 ? ld_carry<COH>(ab + i) : Acc(0);
 }
 
 template <typename Acc> struct ScanSum {
@@ -1588,19 +1602,26 @@ __device__ __forceinline__ void carry_body(const Acc *__restrict__ agg, Acc *__r
     __shared__ Sum s_sum[32][33];
     pdl_wait();
 
+    // 32-bit element offsets (records and carries stay below 2^31 elements)
     Acc cache[kCarryCache];
     Sum s;
     s.zero();
     if (active) {
         if (bpg <= kCarryCache) {
 #pragma unroll
-            for (int k = 0; k < kCarryCache; ++k)
-                if (b_beg + k < b_end) cache[k] = band_contrib(agg + (size_t)(b_beg + k) * agg_stride, b_beg + k, lane, N, T);
+            for (int k = 0; k < kCarryCache; ++k) {
+                const int b = b_beg + k;
+                const int i = b < b_end ? contrib_index(b, lane, N, T) : -1;
+                cache[k] = i >= 0 ? agg[b * agg_stride + i] : Acc(0);
+            }
 #pragma unroll
             for (int k = 0; k < kCarryCache; ++k)
                 if (b_beg + k < b_end) s.add(cache[k]);
         } else {
-            for (int b = b_beg; b < b_end; ++b) s.add(band_contrib(agg + (size_t)b * agg_stride, b, lane, N, T));
+            for (int b = b_beg; b < b_end; ++b) {
+                const int i = contrib_index(b, lane, N, T);
+                s.add(i >= 0 ? agg[b * agg_stride + i] : Acc(0));
+            }
         }
     }
     s_sum[g][lx] = s;
@@ -1625,38 +1646,28 @@ __device__ __forceinline__ void carry_body(const Acc *__restrict__ agg, Acc *__r
     if (!active) return;
     Sum pre = s_sum[g][lx];
 
-    // where lane's value goes in band b's window (or -1)
-    auto slot = [&](int b) -> int {
-        if (lane < N) return lane;
-        const int j0 = b * T, Tb = min(T, N - j0);
-        if (lane < 3 * N) {
-            const int o = lane - N - j0;
-            return (o >= 0 && o < N + Tb - 1) ? N + o : -1;
-        }
-        const int o = lane - 3 * N - (N - j0 - Tb);
-        return (o >= 0 && o < N + Tb - 1) ? 2 * N + T - 1 + o : -1;
-    };
     if (bpg <= kCarryCache) {
 #pragma unroll
         for (int k = 0; k < kCarryCache; ++k) {
             const int b = b_beg + k;
             if (b < b_end) {
-                const int o = slot(b);
-                if (o >= 0) carry[(size_t)b * cs + o] = pre.value();
+                const int o = carry_slot(b, lane, N, T);
+                if (o >= 0) carry[b * cs + o] = pre.value();
                 pre.add(cache[k]);
             }
         }
     } else {
         for (int b = b_beg; b < b_end; ++b) {
-            const int o = slot(b);
-            if (o >= 0) carry[(size_t)b * cs + o] = pre.value();
-            pre.add(band_contrib(agg + (size_t)b * agg_stride, b, lane, N, T));
+            const int o = carry_slot(b, lane, N, T);
+            if (o >= 0) carry[b * cs + o] = pre.value();
+            const int i = contrib_index(b, lane, N, T);
+            pre.add(i >= 0 ? agg[b * agg_stride + i] : Acc(0));
         }
     }
-    if (b_beg < nb && b_end == nb) carry[(size_t)nb * cs + lane] = pre.value();
+    if (b_beg < nb && b_end == nb) carry[nb * cs + lane] = pre.value();
 }
 template <typename Acc, typename Sum>
-__global__ void __launch_bounds__(1024) carry_kernel(const Acc *__restrict__ agg, Acc *__restrict__ carry,
+__global__ void __launch_bounds__(1024, 1) carry_kernel(const Acc *__restrict__ agg, Acc *__restrict__ carry,
                                                      int log2N, int T, int nb, int agg_stride)
 {
     carry_body<Acc, Sum>(agg, carry, log2N, T, nb, agg_stride);
@@ -1816,7 +1827,7 @@ __global__ void __launch_bounds__(CPT == 1 ? 64 : 512) band_batched_kernel(const
 }
 
 template <typename Acc, typename Sum>
-__global__ void __launch_bounds__(1024) carry_batched_kernel(const PanelDesc *__restrict__ tab, int log2N, int T,
+__global__ void __launch_bounds__(1024, 1) carry_batched_kernel(const PanelDesc *__restrict__ tab, int log2N, int T,
                                                              int nb, int agg_stride)
 {
     const PanelDesc &d = tab[blockIdx.y];
