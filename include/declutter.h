@@ -83,7 +83,7 @@ typedef struct {
     int32_t band_rows;       /* rows per band of the integral-image kernels,
                                 1..64 (the last band may be shorter); 0 =
                                 automatic: one band per SM of a 152-SM GPU
-                                from 1024 x 1024, N / 128 below */
+                                from 1024 x 1024, N / 256 (at least 1) below */
     int32_t keep_order;      /* regularize(): 0 = iterate on an internal copy of the
                                 samples sorted by pixel (faster; results identical),
                                 1 = iterate in the caller's order */
