@@ -178,10 +178,14 @@ dc_status regularize(dc_ctx *ctx, float *pos_xy, int64_t n, int32_t iters, doubl
 dc_status regularize_tracers(dc_ctx *ctx, float *pos_xy, int64_t n, float *tracer_xy, int64_t n_tracers,
                              int32_t iters);
 
-/* regularize() on HOST samples: copies host float[2n] to a context-owned
- * device buffer, runs the iterations, copies the result back into the same
- * host array and synchronises.  Pinned host memory gives asynchronous
- * copies.  uniformity_out as for regularize(). */
+/* regularize() on HOST samples float[2n], updated in place; synchronises.
+ * Pinned or registered host memory (cudaHostAlloc, cudaHostRegister) with
+ * keep_order = 0: the iterations run on the host array directly, reading it
+ * over the host link in the first splat and the reordering and writing the
+ * result back in the final gather (no staging copies).  Otherwise the array
+ * is copied to a context-owned device buffer and back.  Setting the
+ * environment variable DECLUTTER_HOST_DIRECT=0 forces the copies.
+ * uniformity_out as for regularize(). */
 dc_status regularize_host(dc_ctx *ctx, float *host_pos_xy, int64_t n, int32_t iters,
                           double *uniformity_out);
 

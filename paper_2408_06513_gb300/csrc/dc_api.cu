@@ -711,12 +711,41 @@ dc_status regularize_tracers(dc_ctx *c, float *pos, int64_t n, float *tracer_xy,
     return DC_OK;
 }
 
+// Device address of host memory the device can reach directly (pinned or
+// registered under unified addressing), 8-byte aligned; else null.
+static float *device_alias(float *host_pos)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, host_pos) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    float *dp = static_cast<float *>(at.devicePointer);
+    return (reinterpret_cast<uintptr_t>(dp) & 7) ? nullptr : dp;
+}
+static bool host_direct_enabled()
+{
+    const char *e = getenv("DECLUTTER_HOST_DIRECT");
+    return !(e && e[0] == '0');
+}
+
 dc_status regularize_host(dc_ctx *c, float *host_pos, int64_t n, int32_t iters, double *uniformity_out)
 {
     if (dc_status st = check_ctx(c)) return st;
     if (n < 0 || n >= (int64_t(1) << 32)) return fail(DC_ERR_INVALID_ARG, "n");
     if (n > 0 && !host_pos) return fail(DC_ERR_INVALID_ARG, "null host pointer");
     DeviceGuard guard(c->device);
+    // Pinned (or registered) host memory is addressable by the device: with
+    // the samples reordered, the iterations touch the caller's array only in
+    // the first splat and the reordering (one read each) and in the way back
+    // (one write), so they run on it directly over the host link, without
+    // staging copies (DECLUTTER_HOST_DIRECT=0: always stage).
+    if (n > 0 && c->p.keep_order == 0 && host_direct_enabled())
+        if (float *dp = device_alias(host_pos)) {
+            if (dc_status st = regularize(c, dp, n, iters, uniformity_out)) return st;
+            return declutter_sync(c);
+        }
     if (n > c->hpos_cap) {
         DC_CUDA(cudaStreamSynchronize(c->stream));
         cudaFree(c->hpos);

@@ -413,16 +413,25 @@ def test_reordering_does_not_change_results(dc, r):
     assert out[0][1] == out[1][1]
 
 
-def test_regularize_host_matches_device(dc):
+@pytest.mark.parametrize("memory,direct", [("pinned", "1"), ("pinned", "0"), ("pageable", "1")])
+def test_regularize_host_matches_device(dc, monkeypatch, memory, direct):
+    # pinned host memory is used in place over the host link (or staged with
+    # DECLUTTER_HOST_DIRECT=0); pageable memory is always staged
+    monkeypatch.setenv("DECLUTTER_HOST_DIRECT", direct)
     z, _ = synth.tiny_mixture()
     ctx = dc.declutter_create(7, kernel_r=2)
     try:
         a = to_dev(z)
-        dc.regularize(ctx, a, 3)
+        ua = dc.regularize(ctx, a, 3, uniformity=True)
         dc.declutter_sync(ctx)
-        h = torch.from_numpy(z.copy()).pin_memory()
-        dc.regularize_host(ctx, h, 3)
-        assert torch.equal(a.cpu(), h)
+        h = torch.from_numpy(z.copy())
+        if memory == "pinned":
+            h = h.pin_memory()
+        for _ in range(2):  # the second call replays the cached graph
+            h.copy_(torch.from_numpy(z))
+            uh = dc.regularize_host(ctx, h, 3, uniformity=True)
+            assert torch.equal(a.cpu(), h)
+            assert ua == uh
     finally:
         dc.declutter_destroy(ctx)
 
