@@ -8,6 +8,7 @@ transposed operand in the oracle fails at least one of them.
 
 import itertools
 import math
+import os
 
 import numpy as np
 import pytest
@@ -294,6 +295,28 @@ def test_mapping_properties():
 # --------------------------------------------------------------------------
 # Sec. 4.2: eq. (map_res)
 # --------------------------------------------------------------------------
+
+def test_unit_mass_worked_example():
+    # hand-derived worked example (tests/golden/unit_mass_4x4.txt, Sec. 3.1,
+    # eq. (map), Sec. 4.1-4.2): one sample at pixel (1, 2) of a 4x4 grid;
+    # the constant texture's numerator X(1), t(.; c + d0) and D at four
+    # pixels, all exact binary fractions
+    path = os.path.join(os.path.dirname(__file__), "golden", "unit_mass_4x4.txt")
+    rows = np.loadtxt(path, comments="#")
+    N = 4
+    c = np.zeros((N, N))
+    c[2, 1] = 1.0  # [j][i]
+    d0 = 1.0 / 16
+    t1 = oracle.mapping(np.ones((N, N)))
+    td = oracle.mapping(c + d0)
+    D = oracle.displacement(c, d0)
+    assert rows.shape == (4, 8)
+    for i, j, x1x, x1y, tdx, tdy, dx, dy in rows:
+        i, j = int(i), int(j)
+        assert np.array_equal(t1[j, i] * (2 * N * N), [x1x, x1y]), (i, j)
+        assert np.array_equal(td[j, i], [tdx, tdy]), (i, j)
+        assert np.array_equal(D[j, i], [dx, dy]), (i, j)
+
 
 def test_displacement_uniform_is_zero_and_identities():
     N = 32
