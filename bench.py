@@ -628,6 +628,61 @@ def run_batched(args, dc, dev, stream, flush, seed_offset=0):
         dc.declutter_batch_destroy(batch)
 
 
+def surrogate_layer_flops(levels: int = 4, base: int = 32, in_ch: int = 3, log2_res: int = 8):
+    """Per-sample FLOPs (2 x MACs) of each 3x3 convolution of the network, in
+    the library's layer order: encoder levels (a: in -> c_l, b: c_l -> c_l),
+    decoder levels (up: c_(l+1) -> c_l on the upsampled input, c: c_l -> c_l),
+    the 2-channel head; true channel counts, no padding."""
+    ch = [base << l for l in range(levels)]
+    out, cin = [], in_ch
+    for l in range(levels):
+        hw = 1 << (2 * (log2_res - l))
+        out += [2 * hw * ch[l] * 9 * cin, 2 * hw * ch[l] * 9 * ch[l]]
+        cin = ch[l]
+    for l in range(levels - 2, -1, -1):
+        hw = 1 << (2 * (log2_res - l))
+        out += [2 * hw * ch[l] * 9 * ch[l + 1], 2 * hw * ch[l] * 9 * ch[l]]
+    out.append(2 * (1 << (2 * log2_res)) * 2 * 9 * ch[0])
+    return out
+
+
+def surrogate_tensor_rate(dc, sg, dens, scales, field, target, batch: int = 16, reps: int = 20):
+    """Tensor-core throughput of the surrogate: training steps and forward
+    passes at batch 16 on fixed inputs (learning rate 0 leaves the trained
+    weights unchanged), timed between device synchronisations (the network
+    runs on its own stream).  A training step is the forward, the data
+    gradient of every layer but the first, and every weight gradient."""
+    import torch
+
+    layers = surrogate_layer_flops()
+    fwd = float(sum(layers))
+    step = fwd + float(sum(layers[1:])) + fwd
+    xd, xs = dens[:batch].contiguous(), scales[:batch].contiguous()
+    xf, xt = field[:batch].contiguous(), target[:batch].contiguous()
+    out = torch.empty_like(xt)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps * 1e3
+
+    ms_train = timed(lambda: dc.surrogate_train_step(sg, xd, xs, xt, 0.0, want_loss=False, field=xf))
+    ms_fwd = timed(lambda: dc.surrogate_forward(sg, xd, xs, out, field=xf))
+    peaks, src = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    tf_train = step * batch / (ms_train * 1e-3) / 1e12
+    tf_fwd = fwd * batch / (ms_fwd * 1e-3) / 1e12
+    return {"bound": "tensor", "unit": "TFLOP/s", "batch": batch, "gflop_forward_per_sample": fwd / 1e9,
+            "gflop_train_step_per_sample": step / 1e9, "train_step_ms": ms_train, "train_tflops": tf_train,
+            "forward_ms": ms_fwd, "forward_tflops": tf_fwd, "peak": peak, "peak_source": src + " (bf16, sustained)",
+            "train_frac": tf_train / peak, "forward_frac": tf_fwd / peak}
+
+
 def run_surrogate(args, dc, dev):
     """Learned surrogate at 256^2: train the 4-level network (32..256 channels)
     on pairs the plain method generates, within a time budget, then compare
@@ -689,6 +744,7 @@ def run_surrogate(args, dc, dev):
                          "worth_plain_iters": worth, "ms_surrogate_pass": ms_sg, "ms_plain_equal_quality": ms_plain_eq,
                          "ms_plain8": ms_plain8, "ms_surrogate_to_plain8_quality": ms_fb, "fallback_plain_iters": used,
                          "cv_after_fallback": cv_fb})
+        tensor = surrogate_tensor_rate(dc, sg, dens, scales, field, target)
         avg = lambda k: float(np.mean([r[k] for r in rows]))  # noqa: E731
         return {"model": "conv encoder-decoder, 4 levels, 32/64/128/256 channels, 3x3, bf16 weights, fp32 accumulation; "
                          "input density + one iteration's field, output kappa * field + network",
@@ -701,7 +757,7 @@ def run_surrogate(args, dc, dev):
                 "ms_surrogate_pass": avg("ms_surrogate_pass"), "ms_plain_equal_quality": avg("ms_plain_equal_quality"),
                 "ms_plain8": avg("ms_plain8"), "ms_surrogate_to_plain8_quality": avg("ms_surrogate_to_plain8_quality"),
                 "fallback_plain_iters_mean": avg("fallback_plain_iters"),
-                "fixed_error": "bin std/mean within 1.05x of 8 plain iterations", "cases": rows}
+                "fixed_error": "bin std/mean within 1.05x of 8 plain iterations", "tensor": tensor, "cases": rows}
     finally:
         dc.declutter_destroy(ctx)
         dc.surrogate_destroy(sg)
