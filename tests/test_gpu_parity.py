@@ -468,11 +468,14 @@ def test_profile_counts_launches(dc, monkeypatch, fused, fused_smooth):
         assert k[name]["launches"] == 0, name
 
 
-@pytest.mark.parametrize("log2,r,band_rows", [(7, 2, 0), (8, 2, 0), (8, 5, 3), (9, 4, 0), (9, 4, 5),
-                                               (9, 12, 7), (10, 8, 0), (10, 3, 16)])
-def test_fused_smoothing_matches_separate_launches(dc, monkeypatch, log2, r, band_rows):
+@pytest.mark.parametrize("log2,r,band_rows,fused", [(7, 2, 0, 1), (8, 2, 0, 1), (8, 5, 3, 1), (9, 4, 0, 1),
+                                                     (9, 4, 5, 1), (9, 12, 7, 1), (10, 8, 0, 1), (10, 3, 16, 1),
+                                                     (7, 40, 0, 1), (10, 16, 0, 1), (10, 40, 0, 0)])
+def test_fused_smoothing_matches_separate_launches(dc, monkeypatch, log2, r, band_rows, fused):
     # bitwise: smoothing inside the aggregate pass (windows of 4 or 8 rows,
-    # ragged last bands) against the smoothing kernel plus the aggregate pass
+    # ragged last bands, radii up to the shared-memory limit) against the
+    # smoothing kernel plus the aggregate pass; r = 40 at 1024^2 does not fit
+    # and keeps the separate launches
     rng = np.random.default_rng(log2 * 100 + r)
     z = rng.beta(2.0, 5.0, size=(60_000, 2)).astype(np.float32)
     outs, us = [], []
@@ -485,8 +488,8 @@ def test_fused_smoothing_matches_separate_launches(dc, monkeypatch, log2, r, ban
             dc.declutter_sync(ctx)
             if fs == "1":
                 prof = dc.declutter_profile_regularize(ctx, to_dev(z), 1, reps=1)
-                assert prof["kernels"]["smooth_aggregate"]["launches"] == 1
-                assert prof["kernels"]["smooth"]["launches"] == 0
+                assert prof["kernels"]["smooth_aggregate"]["launches"] == fused
+                assert prof["kernels"]["smooth"]["launches"] == 1 - fused
             outs.append(pos.cpu())
         finally:
             dc.declutter_destroy(ctx)
