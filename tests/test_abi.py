@@ -87,3 +87,30 @@ def test_calls_on_null_context_fail_cleanly(lib):
     assert lib.regularize(None, None, 0, 1, None) == 1
     assert lib.declutter_sync(None) == 1
     assert lib.declutter_destroy(None) == 0
+
+
+def test_every_kernel_kind_has_algorithmic_bytes(lib):
+    # bench.py divides each kernel kind's algorithmic bytes by its time: every
+    # kind the library reports needs a formula, and no name is left over
+    import bench
+
+    names = [dc.declutter_kernel_name(k) for k in range(dc.KERNEL_KINDS)]
+    assert all(names) and dc.declutter_kernel_name(dc.KERNEL_KINDS) is None
+    info = type("Info", (), {"band_rows": 2})()
+    for name in names:
+        assert bench.algorithmic_bytes(name, 1_000_000, 512, info) > 0, name
+    assert set(bench.KERNELS_PER_UNIT) <= set(names)
+
+
+def test_surrogate_flop_count():
+    # the network of surrogate_create(8, 4, 32, in_channels=3): 8 encoder, 6
+    # decoder and one head convolution, 3x3; per 256^2 sample, counted by hand:
+    # 113.2M (3 -> 32) + seven c -> c convolutions of 1208.0M + three of
+    # 604.0M (c -> 2c encoder) + three of 2416.0M (2c -> c decoder, upsampled
+    # input) + 75.5M (head) = 17,704,157,184 FLOP
+    import bench
+
+    layers = bench.surrogate_layer_flops()
+    assert len(layers) == 15
+    assert sum(layers) == 17_704_157_184
+    assert layers[0] == 2 * 65536 * 32 * 27 and layers[-1] == 2 * 65536 * 2 * 288
