@@ -17,6 +17,9 @@ Also reported on the same JSON line:
   roofline     -- the dominant kernel's algorithmic bytes per launch over its
                   CUDA-event duration, against the measured HBM copy peak;
   cpu_baseline -- the CPU oracle timed on this host on a bounded sample;
+  inim_sweep, lens, batched, surrogate -- the standalone integral images,
+                  the virtual lens, the scatterplot matrix and the learned
+                  surrogate (skippable, see the flags);
   clocks       -- nvidia-smi samples taken during the timed region.
 
 ``--impl reference`` times the CPU oracle (the reference arm) instead.
@@ -455,6 +458,7 @@ def run_gpu(args, world, rank, local, pg):
 
     inim = None if args.no_inim_sweep else run_inim_sweep(args, dc, dev, stream, flush)
     batched = None if args.no_batched else run_batched(args, dc, dev, stream, flush, seed_offset=rank)
+    lens = None if args.no_inim_sweep else run_lens(args, dc, dev, stream, flush)
     surrogate = None if args.surrogate_budget <= 0 else run_surrogate(args, dc, dev)
 
     cpu = None
@@ -476,6 +480,7 @@ def run_gpu(args, world, rank, local, pg):
             "kernels": kernels,
             "cpu_baseline": cpu,
             "inim_sweep": inim,
+            "lens": lens,
             "batched": batched,
             "surrogate": surrogate,
             "clocks": clocks.summary(),
@@ -549,6 +554,50 @@ def run_ncu_inim(args):
             dc.integral_images_u32(ctx, g, a, at)
     dc.declutter_sync(ctx)
     dc.declutter_destroy(ctx)
+
+
+def run_lens(args, dc, dev, stream, flush, reps: int = 15):
+    """Virtual lens (end of Sec. 3.2): lens_field() on a painted density
+    (constant outside, rectangles of other constants inside) at 512^2 and
+    2048^2; the float band passes plus the final pass's lens epilogue.
+    Algorithmic bytes: the density read by the aggregate and final passes
+    (4 + 4 B/px) and the field written (8 B/px).  L2 flushed before every
+    call; CUDA events on the context's stream; median of ``reps``."""
+    import torch
+
+    peaks, src = measured_peaks()
+    rows = []
+    for k in (9, 11):
+        N = 1 << k
+        rng = np.random.default_rng(k)
+        d = np.ones((N, N), np.float32)
+        for _ in range(3):
+            i0, j0 = rng.integers(0, N - N // 4, size=2)
+            w, h = rng.integers(N // 16, N // 4, size=2)
+            d[j0:j0 + h, i0:i0 + w] = float(rng.choice([0.25, 2.0, 4.0, 8.0]))
+        dg = torch.from_numpy(d).to(dev)
+        ctx = dc.declutter_create(k, kernel_r=2, device=dev.index, stream=stream)
+        mean = float(d.mean())
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                dc.lens_field(ctx, dg, mean)
+            ts = []
+            for _ in range(reps):
+                flush()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                dc.lens_field(ctx, dg, mean)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        dc.declutter_sync(ctx)
+        dc.declutter_destroy(ctx)
+        us = statistics.median(ts) * 1e3
+        gbs = 16.0 * N * N / (us * 1e-6) / 1e9
+        rows.append({"grid": N, "us": us, "GBps": gbs, "frac": gbs / peaks["hbm_gbs"], "launches": 3})
+    return {"unit": "GB/s", "bytes_per_pixel": 16, "peak": peaks["hbm_gbs"], "peak_source": src, "sizes": rows,
+            "note": "t(x, y; d) - (x, y) of eq. (map) for a painted float density; L2 flushed before each call"}
 
 
 def run_batched(args, dc, dev, stream, flush, seed_offset=0):

@@ -156,8 +156,23 @@ dc_status integral_images_u32(dc_ctx *ctx, const uint32_t *grid, uint64_t *alpha
  * once, so an even count grid gives exactly zero. */
 dc_status displacement_field(dc_ctx *ctx, float *disp_xy_out);
 
+/* The virtual lens of Molchanov and Linsen (end of Sec. 3.2): the mapping of
+ * eq. (map) itself, t(x, y; d), for a caller's density d >= 0 (for the lens,
+ * constant inside and outside a selected area), without the defect term of
+ * eq. (map_res).  Writes the displacement t(x, y; d) - (x, y) of every pixel
+ * (domain units, interleaved x, y) into the context's field and, if
+ * disp_xy_out is not NULL, into device float[2*N*N]; advect_samples() then
+ * moves samples to the bilinearly interpolated mapping.
+ *   density     : device float[N*N], row-major [j][i], 16-byte aligned; not
+ *                 modified.
+ *   density_mean: a hint that centres the float sums (the density's mean,
+ *                 or 0); the mapping does not depend on it, only the
+ *                 rounding does.
+ * Float arithmetic as in displacement_field.  Asynchronous. */
+dc_status lens_field(dc_ctx *ctx, const float *density, float density_mean, float *disp_xy_out);
+
 /* Step (d), Sec. 4.2: in place, z <- z + bilinear(D)(z) for the n samples,
- * with the field of the last displacement_field call; corner indices are
+ * with the field of the last displacement_field (or lens_field) call; corner indices are
  * clamped to the grid, and with clamp_positions the result to [0, 1]^2. */
 dc_status advect_samples(dc_ctx *ctx, float *pos_xy, int64_t n);
 

@@ -16,6 +16,7 @@ Every function cites the passage it follows:
 * :func:`sat_u64`       -- Sec. 3.1, exact alpha and alpha_t of a uint32 grid
 * :func:`mapping`       -- Sec. 3.2, eq. (map) with anchors q1..q4
 * :func:`displacement`  -- Sec. 4.1-4.2, eqs. (d0) and (map_res)
+* :func:`lens_displacement` -- end of Sec. 3.2, eq. (map) as a virtual lens
 * :func:`advect`        -- Sec. 4.2 / 4.3 step 3, bilinear sample update
 * :func:`quality`       -- Sec. 6.2, 4x4-bin std and overplotting
 * :func:`iterate`       -- Sec. 4.3, one full iteration
@@ -150,6 +151,19 @@ def mapping(d: np.ndarray, pixel_center: bool = False) -> np.ndarray:
     stack = np.ascontiguousarray(np.stack([ims[k] for k in INIM_NAMES]))
     out = np.empty((N, N, 2), dtype=np.float64)
     _load().orc_mapping(_ptr(stack), N, int(bool(pixel_center)), _ptr(out))
+    return out
+
+
+def lens_displacement(d: np.ndarray, pixel_center: bool = False) -> np.ndarray:
+    """The virtual lens of Molchanov and Linsen (end of Sec. 3.2): eq. (map)
+    applied once, without the defect of eq. (map_res); t(x, y; d) - (x, y)
+    at every pixel, [N, N, 2], domain units."""
+    N = d.shape[0]
+    off = 0.5 if pixel_center else 0.0
+    pos = (np.arange(N, dtype=np.float64) + off) / N
+    out = mapping(d, pixel_center)
+    out[:, :, 0] -= pos[None, :]
+    out[:, :, 1] -= pos[:, None]
     return out
 
 

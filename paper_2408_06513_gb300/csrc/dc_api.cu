@@ -622,6 +622,31 @@ dc_status displacement_field(dc_ctx *c, float *disp_out)
     return DC_OK;
 }
 
+dc_status lens_field(dc_ctx *c, const float *density, float density_mean, float *disp_out)
+{
+    if (dc_status st = check_ctx(c)) return st;
+    if (!density) return fail(DC_ERR_INVALID_ARG, "null density");
+    if (!aligned(density, 16)) return fail(DC_ERR_INVALID_ARG, "density must be 16-byte aligned");
+    if (disp_out && !aligned(disp_out, 16)) return fail(DC_ERR_INVALID_ARG, "output must be 16-byte aligned");
+    if (!(density_mean >= 0.f) || !std::isfinite(density_mean))
+        return fail(DC_ERR_INVALID_ARG, "density_mean = %g", (double)density_mean);
+    DeviceGuard guard(c->device);
+    // float-mode band passes over the caller's grid; mu = the mean hint only
+    // centres the sums (any constant gives the same mapping), d0 = 0
+    BandArgs a = band_args(c, density, MODE_FLOAT, 0);
+    a.mu = density_mean;
+    a.d0 = 0.f;
+    a.lens = 1;
+    a.disp = c->disp;
+    Recorder rec;
+    DC_CUDA(enqueue_inims(c, c->stream, a, MODE_FLOAT, rec));
+    if (disp_out)
+        DC_CUDA(cudaMemcpyAsync(disp_out, c->disp, sizeof(float2) * (size_t)c->g.N * c->g.N,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    c->have_disp = true;
+    return DC_OK;
+}
+
 dc_status advect_samples(dc_ctx *c, float *pos, int64_t n)
 {
     if (dc_status st = check_ctx(c)) return st;

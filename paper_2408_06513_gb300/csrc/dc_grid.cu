@@ -424,7 +424,9 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T, c
         CVbN = ld_carry<COH>(cb + N - 1);
         if constexpr (MODE == MODE_FLOAT) {
             const float NN = (float)N * (float)N;
-            kappa = Ctot / NN;
+            // the defect's coefficient; the lens keeps t(x, y; d) itself:
+            // X(d) = X(d - mu) + mu X(1), so the coefficient becomes -mu
+            kappa = a.lens ? -a.mu : Ctot / NN;
             const float S = a.pixel_center ? 2.0f * N : (float)N;
             const float Call = Ctot + a.mu * NN + a.d0 * NN;
             scale = Call > 0.0f ? 1.0f / (2.0f * S * Call) : 0.0f;
@@ -558,6 +560,10 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T, c
                         }
                         dxy[2 * k] = fmaf(-kappa, nx0, nx) * scale;
                         dxy[2 * k + 1] = fmaf(-kappa, ny0, ny) * scale;
+                        if (a.lens) {  // displacement to the mapped position
+                            dxy[2 * k] -= (float)ai / (float)S;
+                            dxy[2 * k + 1] -= (float)bj / (float)S;
+                        }
                         const float muf = a.mu;
                         fal[k] = al + muf * (float)w0[0];
                         fat[k] = at + muf * (float)w0[4];
@@ -970,7 +976,7 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
         CVbN = cb[N - 1];
         if constexpr (MODE == MODE_FLOAT) {
             const float NN = (float)N * (float)N;
-            kappa = Ctot / NN;
+            kappa = a.lens ? -a.mu : Ctot / NN;  // as in band_body
             const float Sg = a.pixel_center ? 2.0f * N : (float)N;
             const float Call = Ctot + a.mu * NN + a.d0 * NN;
             scale = Call > 0.0f ? 1.0f / (2.0f * Sg * Call) : 0.0f;
@@ -1207,6 +1213,10 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
                             }
                             dxy[2 * e] = fmaf(-kappa, nx0, nx) * scale;
                             dxy[2 * e + 1] = fmaf(-kappa, ny0, ny) * scale;
+                            if (a.lens) {
+                                dxy[2 * e] -= (float)ai / (float)Sg;
+                                dxy[2 * e + 1] -= (float)bj / (float)Sg;
+                            }
                             oal[e] = al + a.mu * (float)w0[0];
                             oat[e] = at + a.mu * (float)w0[4];
                         } else {

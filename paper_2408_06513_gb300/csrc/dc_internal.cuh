@@ -97,6 +97,7 @@ struct BandArgs {
     int pixel_center;
     float d0;                 // regularising constant (>= 0)
     double inv_den_exact;     // COUNT: 1 / (2 S N^2 (n + d0 N^2))
+    int lens;                 // FLOAT final pass: t(x, y; d) - (x, y) (eq. (map) without the defect)
     unsigned *status;         // sticky device status word (DC_ERR_TIMEOUT), or null
 };
 

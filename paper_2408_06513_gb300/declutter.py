@@ -9,7 +9,7 @@ The function names are those of the C ABI:
 
     declutter_create, declutter_destroy, declutter_get_info,
     splat_density, integral_images, integral_images_u32,
-    displacement_field, advect_samples, regularize, regularize_host,
+    displacement_field, lens_field, advect_samples, regularize, regularize_host,
     quality_metrics, declutter_sync, declutter_profile_regularize,
     declutter_kernel_name, declutter_status_string, declutter_last_error
 """
@@ -25,7 +25,7 @@ import numpy as np
 __all__ = [
     "DeclutterError", "Context", "dc_params", "dc_info", "load_library", "exported_symbols",
     "declutter_create", "declutter_destroy", "declutter_get_info", "splat_density", "integral_images",
-    "integral_images_u32", "displacement_field", "advect_samples", "regularize", "regularize_host",
+    "integral_images_u32", "displacement_field", "lens_field", "advect_samples", "regularize", "regularize_host",
     "quality_metrics", "declutter_sync", "declutter_profile_regularize", "declutter_kernel_name",
     "declutter_status_string", "declutter_last_error", "DC_CARRY_COMPENSATED", "DC_CARRY_F64",
     "integral_images_u32_noalloc", "DC_NOALLOC_MAX_LOG2_RES", "Batch", "declutter_batch_create",
@@ -91,6 +91,7 @@ _SIGS = [
     ("integral_images", ctypes.c_int, [_P, _P, _P]),
     ("integral_images_u32", ctypes.c_int, [_P, _P, _P, _P]),
     ("displacement_field", ctypes.c_int, [_P, _P]),
+    ("lens_field", ctypes.c_int, [_P, _P, ctypes.c_float, _P]),
     ("advect_samples", ctypes.c_int, [_P, _P, ctypes.c_int64]),
     ("regularize", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
     ("regularize_host", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
@@ -310,6 +311,15 @@ def displacement_field(ctx: Context, disp_out=None) -> None:
     import torch
     _check(load_library().displacement_field(ctx.handle, _ptr(disp_out, torch.float32, 2 * ctx.N * ctx.N,
                                                               "disp_out")), "displacement_field")
+
+
+def lens_field(ctx: Context, density, density_mean: float = 0.0, disp_out=None) -> None:
+    """The lens mapping t(x, y; d) - (x, y) of a CUDA float32 density [N, N]
+    into the context's field (and ``disp_out``, float32 2*N*N, if given)."""
+    import torch
+    NN = ctx.N * ctx.N
+    _check(load_library().lens_field(ctx.handle, _ptr(density, torch.float32, NN, "density"), float(density_mean),
+                                     _ptr(disp_out, torch.float32, 2 * NN, "disp_out")), "lens_field")
 
 
 def advect_samples(ctx: Context, pos) -> None:

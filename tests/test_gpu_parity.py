@@ -581,3 +581,68 @@ def test_largest_grid_8192_one_iteration(dc, r):
         print(f"8192^2 r={r}: max |D - D_fp64| = {err:.3e} px")
     finally:
         dc.declutter_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
+# Virtual lens (end of Sec. 3.2): eq. (map) without the defect
+# --------------------------------------------------------------------------
+
+def painted_density(N, seed):
+    # constant outside, a few painted rectangles of other constant values
+    rng = np.random.default_rng(seed)
+    d = np.ones((N, N), np.float32)
+    for _ in range(3):
+        i0, j0 = rng.integers(0, N - N // 4, size=2)
+        w, h = rng.integers(N // 16, N // 4, size=2)
+        d[j0:j0 + h, i0:i0 + w] = float(rng.choice([0.25, 2.0, 4.0, 8.0]))
+    return d
+
+
+def lens_tol_px(N):
+    # t(x, y; d) is O(1) in domain units: a few float32 roundings of 1,
+    # i.e. of 2^-24 N pixel, on top of the displacement bound (measured:
+    # 9e-5 px at 512^2, 4.7e-4 px at 2048^2, about 4 such roundings)
+    return DISP_TOL_PX + 6 * N * 2.0 ** -24
+
+
+@pytest.mark.parametrize("k,r,pixel_center,hint", [(6, 2, 0, "mean"), (9, 0, 0, "mean"), (9, 4, 1, "zero"),
+                                                   (11, 16, 0, "mean"), (11, 16, 1, "zero")])
+def test_lens_field_matches_oracle(dc, k, r, pixel_center, hint):
+    N = 1 << k
+    d = painted_density(N, seed=k * 10 + pixel_center)
+    ref = oracle.lens_displacement(d.astype(np.float64), pixel_center=bool(pixel_center))
+    ctx = dc.declutter_create(k, kernel_r=r, pixel_center=pixel_center)
+    try:
+        dg = torch.from_numpy(d).to(DEV)
+        out = torch.empty(2 * N * N, dtype=torch.float32, device=DEV)
+        dc.lens_field(ctx, dg, float(d.mean()) if hint == "mean" else 0.0, out)
+        # samples on pixel positions move to the mapped positions
+        off = 0.5 if pixel_center else 0.0
+        jj, ii = np.meshgrid(np.arange(0, N, 7), np.arange(0, N, 5), indexing="ij")
+        z = np.stack([(ii.ravel() + off) / N, (jj.ravel() + off) / N], 1).astype(np.float32)
+        pos = to_dev(z)
+        dc.advect_samples(ctx, pos)
+        dc.declutter_sync(ctx)
+        assert torch.equal(dg, torch.from_numpy(d).to(DEV))  # the density is not modified
+    finally:
+        dc.declutter_destroy(ctx)
+    err = float(np.max(np.abs(out.cpu().numpy().reshape(N, N, 2).astype(np.float64) - ref))) * N
+    print(f"lens {N}^2 pc={pixel_center} hint={hint}: max error {err:.2e} px")
+    assert err <= lens_tol_px(N), err
+    want = z.astype(np.float64) + ref[jj.ravel(), ii.ravel()]
+    perr = float(np.max(np.abs(pos.cpu().numpy().astype(np.float64) - want))) * N
+    assert perr <= lens_tol_px(N) + N * float(np.spacing(np.float32(1.0))), perr
+
+
+def test_lens_field_rejects_bad_arguments(dc):
+    ctx = dc.declutter_create(7, kernel_r=2)
+    try:
+        d = torch.ones(128 * 128, dtype=torch.float32, device=DEV)
+        with pytest.raises(dc.DeclutterError):
+            dc.lens_field(ctx, d, -1.0)
+        with pytest.raises(dc.DeclutterError):
+            dc.lens_field(ctx, d, float("nan"))
+        with pytest.raises(dc.DeclutterError):  # not 16-byte aligned
+            dc.lens_field(ctx, torch.ones(128 * 128 + 1, dtype=torch.float32, device=DEV)[1:], 1.0)
+    finally:
+        dc.declutter_destroy(ctx)

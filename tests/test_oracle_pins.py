@@ -318,6 +318,37 @@ def test_unit_mass_worked_example():
         assert np.array_equal(D[j, i], [dx, dy]), (i, j)
 
 
+def test_lens_of_constant_density_from_worked_example():
+    # end of Sec. 3.2: eq. (map) is not the identity for a constant texture;
+    # its lens displacement is t(1) - p = X(1) / (2 N^2) - p, with X(1) from
+    # the hand-derived fixture (tests/golden/unit_mass_4x4.txt)
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "unit_mass_4x4.txt"), comments="#")
+    N = 4
+    L = oracle.lens_displacement(np.full((N, N), 3.0))
+    for i, j, x1x, x1y, *_ in rows:
+        i, j = int(i), int(j)
+        want = [x1x / (2 * N * N) - i / N, x1y / (2 * N * N) - j / N]
+        assert np.array_equal(L[j, i], want), (i, j)
+        assert np.any(L[j, i] != 0.0)
+
+
+def test_lens_magnifies_the_selected_area():
+    # end of Sec. 3.2: the density is constant inside and outside the
+    # selected area, and a larger value inside magnifies the area more
+    N = 32
+    spans = []
+    for inside in (1.0, 2.0, 4.0, 8.0):
+        d = np.ones((N, N))
+        d[12:20, 12:20] = inside
+        L = oracle.lens_displacement(d)
+        xs = (np.arange(N) / N)[None, :] + L[:, :, 0]
+        ys = (np.arange(N) / N)[:, None] + L[:, :, 1]
+        spans.append((xs[12:20, 12:20].max() - xs[12:20, 12:20].min(), ys[12:20, 12:20].max() - ys[12:20, 12:20].min()))
+        assert np.all(xs >= 0.0) and np.all(xs <= 1.0) and np.all(ys >= 0.0) and np.all(ys <= 1.0)
+    for a, b in zip(spans, spans[1:]):
+        assert b[0] > a[0] and b[1] > a[1], spans
+
+
 def test_displacement_uniform_is_zero_and_identities():
     N = 32
     D = oracle.displacement(np.full((N, N), 4.0), d0=4.0 / 1.0)
