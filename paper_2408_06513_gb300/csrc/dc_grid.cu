@@ -410,7 +410,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T, c
     const Acc *cb = nullptr, *ce = nullptr;
     Acc cvb[CPT], Rk[CPT];
     Acc Ctot = Acc(0), CVbN = Acc(0);
-    float kappa = 0.f, scale = 0.f;
+    float kappa = 0.f, scale = 0.f, lens_s = 0.f;
     if constexpr (FINAL) {
         cb = static_cast<const Acc *>(a.carry) + (size_t)b * carry_stride(N, T);
         ce = static_cast<const Acc *>(a.carry) + (size_t)((N + T - 1) / T) * carry_stride(N, T);
@@ -430,6 +430,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T, c
             const float S = a.pixel_center ? 2.0f * N : (float)N;
             const float Call = Ctot + a.mu * NN + a.d0 * NN;
             scale = Call > 0.0f ? 1.0f / (2.0f * S * Call) : 0.0f;
+            lens_s = a.lens ? 1.0f / S : 0.0f;  // the pixel position ai / S (exact: S = 2^k)
         }
     }
 
@@ -558,12 +559,9 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T, c
                             nx0 = fmaf((float)w0[q], (float)qx[q], nx0);
                             ny0 = fmaf((float)w0[q], (float)qy[q], ny0);
                         }
-                        dxy[2 * k] = fmaf(-kappa, nx0, nx) * scale;
-                        dxy[2 * k + 1] = fmaf(-kappa, ny0, ny) * scale;
-                        if (a.lens) {  // displacement to the mapped position
-                            dxy[2 * k] -= (float)ai / (float)S;
-                            dxy[2 * k + 1] -= (float)bj / (float)S;
-                        }
+                        // lens: minus the pixel position (lens_s = 0 otherwise: the same bits)
+                        dxy[2 * k] = fmaf(-lens_s, (float)ai, fmaf(-kappa, nx0, nx) * scale);
+                        dxy[2 * k + 1] = fmaf(-lens_s, (float)bj, fmaf(-kappa, ny0, ny) * scale);
                         const float muf = a.mu;
                         fal[k] = al + muf * (float)w0[0];
                         fat[k] = at + muf * (float)w0[4];
@@ -945,7 +943,7 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
     const int L4w = ((((N + T - 1 + 3) >> 2) + 23) >> 5 << 5) + 8;
     C *sA = nullptr, *sU = nullptr, *sV = nullptr, *sR = nullptr, *sAm = nullptr, *sBm = nullptr;
     C Ctot = C(0), CVbN = C(0);
-    float kappa = 0.f, scale = 0.f;
+    float kappa = 0.f, scale = 0.f, lens_s = 0.f;
     if constexpr (FINAL) {
         C *p = reinterpret_cast<C *>(s_dyn + (RING ? (size_t)ring * rowbytes : 0));
         sA = p; p += 4 * L4a;
@@ -980,6 +978,7 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
             const float Sg = a.pixel_center ? 2.0f * N : (float)N;
             const float Call = Ctot + a.mu * NN + a.d0 * NN;
             scale = Call > 0.0f ? 1.0f / (2.0f * Sg * Call) : 0.0f;
+            lens_s = a.lens ? 1.0f / Sg : 0.0f;
         }
         // the first row's barrier orders these writes before any read
     }
@@ -1211,12 +1210,8 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
                                 nx0 = fmaf((float)w0[k], (float)qx[k], nx0);
                                 ny0 = fmaf((float)w0[k], (float)qy[k], ny0);
                             }
-                            dxy[2 * e] = fmaf(-kappa, nx0, nx) * scale;
-                            dxy[2 * e + 1] = fmaf(-kappa, ny0, ny) * scale;
-                            if (a.lens) {
-                                dxy[2 * e] -= (float)ai / (float)Sg;
-                                dxy[2 * e + 1] -= (float)bj / (float)Sg;
-                            }
+                            dxy[2 * e] = fmaf(-lens_s, (float)ai, fmaf(-kappa, nx0, nx) * scale);
+                            dxy[2 * e + 1] = fmaf(-lens_s, (float)bj, fmaf(-kappa, ny0, ny) * scale);
                             oal[e] = al + a.mu * (float)w0[0];
                             oat[e] = at + a.mu * (float)w0[4];
                         } else {
