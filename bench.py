@@ -17,9 +17,10 @@ Also reported on the same JSON line:
   roofline     -- the dominant kernel's algorithmic bytes per launch over its
                   CUDA-event duration, against the measured HBM copy peak;
   cpu_baseline -- the CPU oracle timed on this host on a bounded sample;
-  inim_sweep, lens, batched, surrogate -- the standalone integral images,
-                  the virtual lens, the scatterplot matrix and the learned
-                  surrogate (skippable, see the flags);
+  inim_sweep, lens, contours, batched, surrogate -- the standalone
+                  integral images, the virtual lens, contour lines, the
+                  scatterplot matrix and the learned surrogate (skippable,
+                  see the flags);
   clocks       -- nvidia-smi samples taken during the timed region.
 
 ``--impl reference`` times the CPU oracle (the reference arm) instead.
@@ -459,6 +460,7 @@ def run_gpu(args, world, rank, local, pg):
     inim = None if args.no_inim_sweep else run_inim_sweep(args, dc, dev, stream, flush)
     batched = None if args.no_batched else run_batched(args, dc, dev, stream, flush, seed_offset=rank)
     lens = None if args.no_inim_sweep else run_lens(args, dc, dev, stream, flush)
+    contours = None if args.no_inim_sweep else run_contours(args, dc, dev, stream, flush)
     surrogate = None if args.surrogate_budget <= 0 else run_surrogate(args, dc, dev)
 
     cpu = None
@@ -481,6 +483,7 @@ def run_gpu(args, world, rank, local, pg):
             "cpu_baseline": cpu,
             "inim_sweep": inim,
             "lens": lens,
+            "contours": contours,
             "batched": batched,
             "surrogate": surrogate,
             "clocks": clocks.summary(),
@@ -598,6 +601,50 @@ def run_lens(args, dc, dev, stream, flush, reps: int = 15):
         rows.append({"grid": N, "us": us, "GBps": gbs, "frac": gbs / peaks["hbm_gbs"], "launches": 3})
     return {"unit": "GB/s", "bytes_per_pixel": 16, "peak": peaks["hbm_gbs"], "peak_source": src, "sizes": rows,
             "note": "t(x, y; d) - (x, y) of eq. (map) for a painted float density; L2 flushed before each call"}
+
+
+def run_contours(args, dc, dev, stream, flush, reps: int = 15):
+    """Contour lines (Sec. 5): contour_segments() of a smooth field at its
+    median, 512^2 and 2048^2.  Algorithmic bytes: the field read (4 B/px)
+    and two segment slots written a cell (32 B).  L2 flushed before every
+    call; CUDA events on the context's stream; median of ``reps``."""
+    import torch
+
+    peaks, src = measured_peaks()
+    rows = []
+    for k in (9, 11):
+        N = 1 << k
+        rng = np.random.default_rng(k)
+        jj, ii = np.meshgrid(np.arange(N, dtype=np.float32), np.arange(N, dtype=np.float32), indexing="ij")
+        f = np.zeros((N, N), np.float32)
+        for _ in range(12):
+            ci, cj = rng.uniform(0, N, size=2)
+            sg = rng.uniform(N / 30, N / 6)
+            f += np.float32(rng.uniform(0.5, 2.0)) * np.exp(-((ii - ci) ** 2 + (jj - cj) ** 2) / (2 * sg * sg))
+        fg = torch.from_numpy(f).to(dev)
+        out = torch.empty(8 * (N - 1) * (N - 1), dtype=torch.float32, device=dev)
+        level = float(np.median(f))
+        ctx = dc.declutter_create(k, kernel_r=2, device=dev.index, stream=stream)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                dc.contour_segments(ctx, fg, level, out)
+            ts = []
+            for _ in range(reps):
+                flush()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                dc.contour_segments(ctx, fg, level, out)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        dc.declutter_sync(ctx)
+        dc.declutter_destroy(ctx)
+        us = statistics.median(ts) * 1e3
+        gbs = (4.0 * N * N + 32.0 * (N - 1) ** 2) / (us * 1e-6) / 1e9
+        rows.append({"grid": N, "us": us, "GBps": gbs, "frac": gbs / peaks["hbm_gbs"], "launches": 1})
+    return {"unit": "GB/s", "bytes_per_cell": 36, "peak": peaks["hbm_gbs"], "peak_source": src, "sizes": rows,
+            "note": "marching squares at the median of a smooth field; L2 flushed before each call"}
 
 
 def run_batched(args, dc, dev, stream, flush, seed_offset=0):

@@ -171,6 +171,23 @@ dc_status displacement_field(dc_ctx *ctx, float *disp_xy_out);
  * Float arithmetic as in displacement_field.  Asynchronous. */
 dc_status lens_field(dc_ctx *ctx, const float *density, float density_mean, float *disp_xy_out);
 
+/* Contour lines of a density (Sec. 5: the original density's contours,
+ * shown again after the transformation by moving their vertices, e.g. as
+ * tracers of regularize_tracers).  Marching squares over the pixel nodes at
+ * the positions of the context's pixel convention: cell (i, j),
+ * 0 <= i, j < N - 1, has the corners f(i, j), f(i+1, j), f(i+1, j+1),
+ * f(i, j+1); a corner is inside when f >= level; a crossed edge holds the
+ * linearly interpolated vertex; the two saddle cases follow the cell
+ * centre, the mean of the four corners.
+ *   field   : device float[N*N], row-major [j][i] (e.g. d_r from
+ *             splat_density); not modified.
+ *   segs_out: device float[8 (N-1)^2], 16-byte aligned: for cell
+ *             c = j (N-1) + i, slots 2c and 2c+1 of (x0, y0, x1, y1) in domain
+ *             units; a cell with fewer than two segments writes NaN into the
+ *             unused slots (so the output order is the cell order).
+ * Asynchronous. */
+dc_status contour_segments(dc_ctx *ctx, const float *field, float level, float *segs_out);
+
 /* Step (d), Sec. 4.2: in place, z <- z + bilinear(D)(z) for the n samples,
  * with the field of the last displacement_field (or lens_field) call; corner indices are
  * clamped to the grid, and with clamp_positions the result to [0, 1]^2. */

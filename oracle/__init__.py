@@ -17,6 +17,7 @@ Every function cites the passage it follows:
 * :func:`mapping`       -- Sec. 3.2, eq. (map) with anchors q1..q4
 * :func:`displacement`  -- Sec. 4.1-4.2, eqs. (d0) and (map_res)
 * :func:`lens_displacement` -- end of Sec. 3.2, eq. (map) as a virtual lens
+* :func:`contour_cell`  -- Sec. 5, contour lines (marching squares)
 * :func:`advect`        -- Sec. 4.2 / 4.3 step 3, bilinear sample update
 * :func:`quality`       -- Sec. 6.2, 4x4-bin std and overplotting
 * :func:`iterate`       -- Sec. 4.3, one full iteration
@@ -165,6 +166,51 @@ def lens_displacement(d: np.ndarray, pixel_center: bool = False) -> np.ndarray:
     out[:, :, 0] -= pos[None, :]
     out[:, :, 1] -= pos[:, None]
     return out
+
+
+def contour_cell(f: np.ndarray, level: float, i: int, j: int, pixel_center: bool = False) -> list:
+    """Contour segments of cell (i, j) of the float32 field f at ``level``
+    (Sec. 5 contour lines; reading: marching squares over the pixel nodes).
+    Corners f[j, i], f[j, i+1], f[j+1, i+1], f[j+1, i] at the node positions
+    ((i + o) / N, (j + o) / N); a corner is inside when f >= level (compared
+    in float32); each edge whose ends differ holds the linearly interpolated
+    vertex.  Two crossed edges make one segment; four (a saddle) make two,
+    around the two corners on the other side of the cell centre, the float32
+    mean ((a + b) + (c + d)) / 4.  Returns [((x0, y0), (x1, y1)), ...] in
+    domain units, FP64."""
+    N = f.shape[0]
+    o = 0.5 if pixel_center else 0.0
+    lv = np.float32(level)
+    # corners counter-clockwise in (i, j): (i, j), (i+1, j), (i+1, j+1), (i, j+1)
+    ij = [(i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)]
+    val = [np.float32(f[b, a]) for a, b in ij]
+    ins = [v >= lv for v in val]
+
+    def cross(p, q):  # vertex on the edge from corner p to corner q
+        t = (float(lv) - float(val[p])) / (float(val[q]) - float(val[p]))
+        (ap, bp), (aq, bq) = ij[p], ij[q]
+        return ((ap + o + t * (aq - ap)) / N, (bp + o + t * (bq - bp)) / N)
+
+    sides = [(0, 1), (1, 2), (2, 3), (3, 0)]  # the four edges as corner pairs
+    hit = [s for s in sides if ins[s[0]] != ins[s[1]]]
+    if not hit:
+        return []
+    if len(hit) == 2:
+        return [(cross(*hit[0]), cross(*hit[1]))]
+    centre = ((val[0] + val[1]) + (val[2] + val[3])) * np.float32(0.25)
+    # the corners cut off: those whose side differs from the centre's
+    cut = [k for k in range(4) if ins[k] != (centre >= lv)]
+    segs = []
+    for k in cut:
+        a, b = (k + 3) % 4, (k + 1) % 4  # neighbours of corner k
+        segs.append((cross(a, k), cross(k, b)))
+    return segs
+
+
+def contour_segments(f: np.ndarray, level: float, pixel_center: bool = False) -> list:
+    """contour_cell of every cell, in cell order (j, then i); for small grids."""
+    N = f.shape[0]
+    return [contour_cell(f, level, i, j, pixel_center) for j in range(N - 1) for i in range(N - 1)]
 
 
 def displacement(d_r: np.ndarray, d0: float, pixel_center: bool = False) -> np.ndarray:

@@ -647,6 +647,19 @@ dc_status lens_field(dc_ctx *c, const float *density, float density_mean, float 
     return DC_OK;
 }
 
+dc_status contour_segments(dc_ctx *c, const float *field, float level, float *segs_out)
+{
+    if (dc_status st = check_ctx(c)) return st;
+    if (!field || !segs_out) return fail(DC_ERR_INVALID_ARG, "null field or output");
+    if (!aligned(field, 4)) return fail(DC_ERR_INVALID_ARG, "field must be 4-byte aligned");
+    if (!aligned(segs_out, 16)) return fail(DC_ERR_INVALID_ARG, "output must be 16-byte aligned");
+    if (!std::isfinite(level)) return fail(DC_ERR_INVALID_ARG, "level = %g", (double)level);
+    DeviceGuard guard(c->device);
+    DC_CUDA(launch_contour(c->stream, field, c->g.log2N, level, c->p.pixel_center,
+                           reinterpret_cast<float4 *>(segs_out)));
+    return DC_OK;
+}
+
 dc_status advect_samples(dc_ctx *c, float *pos, int64_t n)
 {
     if (dc_status st = check_ctx(c)) return st;

@@ -148,6 +148,10 @@ cudaError_t launch_reorder_back(cudaStream_t s, const float2 *spos, const uint32
 cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, int log2N, const GaussW &w,
                           uint32_t *zero_out);
 cudaError_t launch_band_agg(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a);
+// marching squares on a float N x N field: two float4 segment slots per cell
+// ((N-1)^2 cells, row-major), NaN for empty slots
+cudaError_t launch_contour(cudaStream_t s, const float *field, int log2N, float level, int pixel_center,
+                           float4 *segs);
 // smoothing of counts into dens fused with the float-mode aggregate pass
 // (a.src = dens); zero_out as in launch_smooth
 bool smooth_agg_available(const BandGeom &g, const GaussW &w);

@@ -9,7 +9,7 @@ The function names are those of the C ABI:
 
     declutter_create, declutter_destroy, declutter_get_info,
     splat_density, integral_images, integral_images_u32,
-    displacement_field, lens_field, advect_samples, regularize, regularize_host,
+    displacement_field, lens_field, contour_segments, advect_samples, regularize, regularize_host,
     quality_metrics, declutter_sync, declutter_profile_regularize,
     declutter_kernel_name, declutter_status_string, declutter_last_error
 """
@@ -25,7 +25,7 @@ import numpy as np
 __all__ = [
     "DeclutterError", "Context", "dc_params", "dc_info", "load_library", "exported_symbols",
     "declutter_create", "declutter_destroy", "declutter_get_info", "splat_density", "integral_images",
-    "integral_images_u32", "displacement_field", "lens_field", "advect_samples", "regularize", "regularize_host",
+    "integral_images_u32", "displacement_field", "lens_field", "contour_segments", "advect_samples", "regularize", "regularize_host",
     "quality_metrics", "declutter_sync", "declutter_profile_regularize", "declutter_kernel_name",
     "declutter_status_string", "declutter_last_error", "DC_CARRY_COMPENSATED", "DC_CARRY_F64",
     "integral_images_u32_noalloc", "DC_NOALLOC_MAX_LOG2_RES", "Batch", "declutter_batch_create",
@@ -92,6 +92,7 @@ _SIGS = [
     ("integral_images_u32", ctypes.c_int, [_P, _P, _P, _P]),
     ("displacement_field", ctypes.c_int, [_P, _P]),
     ("lens_field", ctypes.c_int, [_P, _P, ctypes.c_float, _P]),
+    ("contour_segments", ctypes.c_int, [_P, _P, ctypes.c_float, _P]),
     ("advect_samples", ctypes.c_int, [_P, _P, ctypes.c_int64]),
     ("regularize", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
     ("regularize_host", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
@@ -320,6 +321,17 @@ def lens_field(ctx: Context, density, density_mean: float = 0.0, disp_out=None) 
     NN = ctx.N * ctx.N
     _check(load_library().lens_field(ctx.handle, _ptr(density, torch.float32, NN, "density"), float(density_mean),
                                      _ptr(disp_out, torch.float32, 2 * NN, "disp_out")), "lens_field")
+
+
+def contour_segments(ctx: Context, field, level: float, segs_out) -> None:
+    """Marching squares of a CUDA float32 field [N, N] at ``level`` into
+    ``segs_out`` (CUDA float32, 8 (N-1)^2 values: two (x0, y0, x1, y1) slots a
+    cell, NaN when unused)."""
+    import torch
+    M = ctx.N - 1
+    _check(load_library().contour_segments(ctx.handle, _ptr(field, torch.float32, ctx.N * ctx.N, "field"),
+                                           float(level), _ptr(segs_out, torch.float32, 8 * M * M, "segs_out")),
+           "contour_segments")
 
 
 def advect_samples(ctx: Context, pos) -> None:

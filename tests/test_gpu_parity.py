@@ -682,3 +682,63 @@ def test_regularize_tracers_moves_nodes_by_the_field(dc, r):
         assert bool(torch.all(torch.isfinite(tr3))) and float(tr3.min()) >= 0.0 and float(tr3.max()) <= 1.0
     finally:
         dc.declutter_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
+# Contour lines (Sec. 5): marching squares
+# --------------------------------------------------------------------------
+
+CONTOUR_TOL = 2.0 ** -20  # domain units: a few float32 roundings of the interpolated vertex
+
+
+def smooth_field(N, seed):
+    rng = np.random.default_rng(seed)
+    jj, ii = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    f = np.zeros((N, N))
+    for _ in range(12):
+        ci, cj = rng.uniform(0, N, size=2)
+        s = rng.uniform(N / 30, N / 6)
+        f += rng.uniform(0.5, 2.0) * np.exp(-((ii - ci) ** 2 + (jj - cj) ** 2) / (2 * s * s))
+    return f.astype(np.float32)
+
+
+def check_contour_cells(out, f, level, cells, pixel_center):
+    N = f.shape[0]
+    M = N - 1
+    slots = out.reshape(M * M, 2, 4)
+    for c in cells:
+        j, i = divmod(int(c), M)
+        want = sorted(tuple(sorted(s)) for s in oracle.contour_cell(f, level, i, j, bool(pixel_center)))
+        got_slots = [s for s in slots[c] if not np.isnan(s[0])]
+        assert all(np.isnan(s).all() for s in slots[c] if np.isnan(s[0])), (i, j)
+        got = sorted(tuple(sorted([(float(s[0]), float(s[1])), (float(s[2]), float(s[3]))])) for s in got_slots)
+        assert len(got) == len(want), (i, j, got, want)
+        for g, w in zip(got, want):
+            assert np.max(np.abs(np.array(g) - np.array(w))) <= CONTOUR_TOL, (i, j, g, w)
+
+
+@pytest.mark.parametrize("k,kind,pixel_center", [(7, "smooth", 0), (7, "ties", 0), (7, "smooth", 1),
+                                                  (11, "smooth", 0)])
+def test_contour_segments_match_oracle(dc, k, kind, pixel_center):
+    N = 1 << k
+    if kind == "smooth":
+        f = smooth_field(N, seed=k)
+        levels = [float(np.float32(np.quantile(f, q))) for q in (0.3, 0.6, 0.9)]
+    else:  # integer values: corners and saddle centres equal to the level
+        jj, ii = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+        f = ((ii * 7 + jj * 13) % 5).astype(np.float32) * 2.0
+        levels = [4.0, 5.0]
+    M = N - 1
+    rng = np.random.default_rng(k)
+    cells = np.arange(M * M) if N <= 128 else np.unique(np.concatenate([
+        rng.integers(0, M * M, size=4000), np.arange(M * 700, M * 702)]))
+    ctx = dc.declutter_create(k, kernel_r=2, pixel_center=pixel_center)
+    try:
+        fg = torch.from_numpy(f).to(DEV)
+        for lv in levels:
+            out = torch.empty(8 * M * M, dtype=torch.float32, device=DEV)
+            dc.contour_segments(ctx, fg, lv, out)
+            dc.declutter_sync(ctx)
+            check_contour_cells(out.cpu().numpy(), f, lv, cells, pixel_center)
+    finally:
+        dc.declutter_destroy(ctx)

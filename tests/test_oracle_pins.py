@@ -349,6 +349,57 @@ def test_lens_magnifies_the_selected_area():
         assert b[0] > a[0] and b[1] > a[1], spans
 
 
+def _segset(segs):
+    return sorted(tuple(sorted(seg)) for seg in segs)
+
+
+def test_contour_saddle_cells_by_hand():
+    # Sec. 5 contour lines (marching squares): a 2x2 checkerboard, nodes at
+    # 0 and 1/2; the saddle follows the cell centre (mean 0.5)
+    f = np.array([[1.0, 0.0], [0.0, 1.0]], np.float32)
+    # level 0.5: centre inside, the outside corners (1/2, 0) and (0, 1/2) are cut off
+    assert _segset(oracle.contour_cell(f, 0.5, 0, 0)) == _segset(
+        [((0.25, 0.0), (0.5, 0.25)), ((0.25, 0.5), (0.0, 0.25))])
+    # level 0.625: centre outside, the inside corners (0, 0) and (1/2, 1/2) are cut off
+    assert _segset(oracle.contour_cell(f, 0.625, 0, 0)) == _segset(
+        [((0.1875, 0.0), (0.0, 0.1875)), ((0.5, 0.3125), (0.3125, 0.5))])
+
+
+def test_contour_of_a_ramp_is_straight():
+    # f(i, j) = i: the level 10.5 crosses only the cells of column 10, at
+    # x = 10.5 / N, each from row j to row j + 1
+    N = 32
+    f = np.tile(np.arange(N, dtype=np.float32), (N, 1))
+    cells = oracle.contour_segments(f, 10.5)
+    for c, segs in enumerate(cells):
+        j, i = divmod(c, N - 1)
+        if i == 10:
+            assert _segset(segs) == _segset([((10.5 / N, j / N), (10.5 / N, (j + 1) / N))])
+        else:
+            assert segs == []
+
+
+def test_contour_of_a_distance_field_is_a_closed_circle():
+    # f = distance (pixels) to the centre: the level R contour lies on the
+    # circle up to the chord error of linear interpolation (< 1 / (8 R) px),
+    # its length is 2 pi R within 1 %, and every vertex ends two segments
+    N, R = 64, 20.0
+    jj, ii = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    f = np.sqrt((ii - 31.3) ** 2 + (jj - 30.6) ** 2).astype(np.float32)
+    segs = [s for cell in oracle.contour_segments(f, R) for s in cell]
+    pts = np.array([p for s in segs for p in s]) * N
+    d = np.hypot(pts[:, 0] - 31.3, pts[:, 1] - 30.6)
+    assert np.all(np.abs(d - R) < 1.0 / (8 * R) + 1e-5)
+    length = sum(np.hypot((b[0] - a[0]) * N, (b[1] - a[1]) * N) for a, b in segs)
+    assert abs(length - 2 * np.pi * R) < 0.01 * 2 * np.pi * R
+    ends = {}
+    for s in segs:
+        for p in s:
+            k = (round(p[0], 9), round(p[1], 9))
+            ends[k] = ends.get(k, 0) + 1
+    assert set(ends.values()) == {2}
+
+
 def test_displacement_uniform_is_zero_and_identities():
     N = 32
     D = oracle.displacement(np.full((N, N), 4.0), d0=4.0 / 1.0)
