@@ -605,8 +605,8 @@ def lens_tol_px(N):
     return DISP_TOL_PX + 6 * N * 2.0 ** -24
 
 
-@pytest.mark.parametrize("k,r,pixel_center,hint", [(6, 2, 0, "mean"), (9, 0, 0, "mean"), (9, 4, 1, "zero"),
-                                                   (11, 16, 0, "mean"), (11, 16, 1, "zero")])
+@pytest.mark.parametrize("k,r,pixel_center,hint", [(4, 2, 0, "mean"), (6, 2, 0, "mean"), (9, 0, 0, "mean"),
+                                                   (9, 4, 1, "zero"), (11, 16, 0, "mean"), (11, 16, 1, "zero")])
 def test_lens_field_matches_oracle(dc, k, r, pixel_center, hint):
     N = 1 << k
     d = painted_density(N, seed=k * 10 + pixel_center)
@@ -717,8 +717,8 @@ def check_contour_cells(out, f, level, cells, pixel_center):
             assert np.max(np.abs(np.array(g) - np.array(w))) <= CONTOUR_TOL, (i, j, g, w)
 
 
-@pytest.mark.parametrize("k,kind,pixel_center", [(7, "smooth", 0), (7, "ties", 0), (7, "smooth", 1),
-                                                  (11, "smooth", 0)])
+@pytest.mark.parametrize("k,kind,pixel_center", [(4, "smooth", 0), (7, "smooth", 0), (7, "ties", 0),
+                                                  (7, "smooth", 1), (11, "smooth", 0), (13, "smooth", 0)])
 def test_contour_segments_match_oracle(dc, k, kind, pixel_center):
     N = 1 << k
     if kind == "smooth":
@@ -731,7 +731,7 @@ def test_contour_segments_match_oracle(dc, k, kind, pixel_center):
     M = N - 1
     rng = np.random.default_rng(k)
     cells = np.arange(M * M) if N <= 128 else np.unique(np.concatenate([
-        rng.integers(0, M * M, size=4000), np.arange(M * 700, M * 702)]))
+        rng.integers(0, M * M, size=4000), np.arange(M * 700, M * 702), np.arange(M * M - 2 * M, M * M)]))
     ctx = dc.declutter_create(k, kernel_r=2, pixel_center=pixel_center)
     try:
         fg = torch.from_numpy(f).to(DEV)
