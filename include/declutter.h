@@ -168,7 +168,10 @@ dc_status displacement_field(dc_ctx *ctx, float *disp_xy_out);
  *   density_mean: a hint that centres the float sums (the density's mean,
  *                 or 0); the mapping does not depend on it, only the
  *                 rounding does.
- * Float arithmetic as in displacement_field.  Asynchronous. */
+ * Float arithmetic as in displacement_field.  Asynchronous.  Errors:
+ * DC_ERR_INVALID_ARG for a null or misaligned pointer or a negative or
+ * non-finite density_mean (nothing is launched); DC_ERR_CUDA for a failed
+ * launch. */
 dc_status lens_field(dc_ctx *ctx, const float *density, float density_mean, float *disp_xy_out);
 
 /* Contour lines of a density (Sec. 5: the original density's contours,
@@ -185,7 +188,9 @@ dc_status lens_field(dc_ctx *ctx, const float *density, float density_mean, floa
  *             c = j (N-1) + i, slots 2c and 2c+1 of (x0, y0, x1, y1) in domain
  *             units; a cell with fewer than two segments writes NaN into the
  *             unused slots (so the output order is the cell order).
- * Asynchronous. */
+ * Asynchronous.  Errors: DC_ERR_INVALID_ARG for a null or misaligned
+ * pointer or a non-finite level (nothing is launched); DC_ERR_CUDA for a
+ * failed launch. */
 dc_status contour_segments(dc_ctx *ctx, const float *field, float level, float *segs_out);
 
 /* Step (d), Sec. 4.2: in place, z <- z + bilinear(D)(z) for the n samples,
