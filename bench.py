@@ -412,10 +412,9 @@ def run_gpu(args, world, rank, local, pg):
     # end-to-end through host buffers (pinned), transfers inside the timed
     # region.  regularize_host() runs on pinned memory in place (the first
     # splat and the reordering each read it over the host link, the way back
-    # writes it) unless DECLUTTER_HOST_DIRECT=0 or kept sample order, when it
-    # stages one copy each way.
+    # writes it) unless kept sample order, when it stages one copy each way.
     host = torch.from_numpy(z.copy()).pin_memory()
-    direct = os.environ.get("DECLUTTER_HOST_DIRECT", "1") != "0" and not args.keep_order
+    direct = not args.keep_order
     h2d_bytes = (2 if direct else 1) * 8 * n
     e2e_times = []
     for s in range(args.warmup + args.steps):

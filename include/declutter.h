@@ -82,13 +82,42 @@ typedef struct {
     int32_t carry_mode;      /* DC_CARRY_* (float mode only) */
     int32_t band_rows;       /* rows per band of the integral-image kernels,
                                 1..64 (the last band may be shorter); 0 =
-                                automatic: one band per SM of a 152-SM GPU
+                                automatic: one band per SM of the device
                                 from 1024 x 1024, N / 256 (at least 1) below */
     int32_t keep_order;      /* regularize(): 0 = iterate on an internal copy of the
                                 samples sorted by pixel (faster; results identical),
                                 1 = iterate in the caller's order */
-    int32_t reserved[3];     /* must be zero */
+    int32_t options;         /* OR of DC_OPT_* (0 = the default launch sequence) */
+    int32_t wait_limit_us;   /* bound of the grid-barrier waits of the
+                                DC_OPT_FUSED_BANDS launch, in microseconds,
+                                1..10^7; 0 = one second */
+    int32_t reserved[1];     /* must be zero */
 } dc_params;
+
+/* Launch-sequence options of dc_params.options.  Every option gives results
+ * bit-identical to the default sequence; the defaults are the measured
+ * fastest on a GB300. */
+enum {
+    /* float and exact mode below 2048 x 2048: the aggregate pass, the
+     * carries and the final pass of the integral images as one cooperative
+     * launch with two grid barriers (where all band CTAs fit on the GPU at
+     * once), instead of three launches */
+    DC_OPT_FUSED_BANDS = 1,
+    /* float mode: the Gaussian smoothing as its own launch instead of inside
+     * the aggregate pass (128^2 .. 1024^2) */
+    DC_OPT_SEPARATE_SMOOTH = 2,
+    /* regularize_host(): always stage pinned host samples through a device
+     * copy instead of iterating on them over the host link */
+    DC_OPT_STAGE_HOST = 4,
+    /* declutter_batch_create(): one launch per step over all panels of a
+     * resolution instead of per-panel graph branches */
+    DC_OPT_BATCHED_LAUNCHES = 8,
+    /* For testing the timeout path only: the grid barrier of the
+     * DC_OPT_FUSED_BANDS launch waits for one CTA more than the grid holds,
+     * so every wait runs to wait_limit_us, the call's results are undefined
+     * and declutter_sync() returns DC_ERR_TIMEOUT. */
+    DC_OPT_TEST_UNREACHED_BARRIER = 1 << 30
+};
 
 /* Read-back of the configuration a context settled on. */
 typedef struct {
@@ -220,11 +249,24 @@ dc_status regularize_tracers(dc_ctx *ctx, float *pos_xy, int64_t n, float *trace
  * keep_order = 0: the iterations run on the host array directly, reading it
  * over the host link in the first splat and the reordering and writing the
  * result back in the final gather (no staging copies).  Otherwise the array
- * is copied to a context-owned device buffer and back.  Setting the
- * environment variable DECLUTTER_HOST_DIRECT=0 forces the copies.
+ * is copied to a context-owned device buffer and back.  The context option
+ * DC_OPT_STAGE_HOST forces the copies.
  * uniformity_out as for regularize(). */
 dc_status regularize_host(dc_ctx *ctx, float *host_pos_xy, int64_t n, int32_t iters,
                           double *uniformity_out);
+
+/* The count grid c(i, j) of Sec. 4.1 (Sec. 4.3 step 1) that the context
+ * holds: that of the last splat_density() call or, after regularize(),
+ * that of the last splat the iterations performed.  Inside regularize()
+ * the advection of every iteration but the last splats the moved samples
+ * into the next iteration's grid; with uniformity_out given, the last
+ * iteration does too, so the grid is that of the returned positions;
+ * without it, the grid is the input of the last iteration.
+ *   counts_out: device uint32[N*N], 4-byte aligned, row-major [j][i].
+ * Asynchronous (a device-to-device copy on the context's stream).  Errors:
+ * DC_ERR_INVALID_ARG for a null or misaligned pointer, DC_ERR_STATE before
+ * any splat. */
+dc_status declutter_counts(dc_ctx *ctx, uint32_t *counts_out);
 
 /* Sec. 6.2 quality measures of the count grid of the last splat_density
  * call; synchronises.  out (host double[3]): [0] std of the 4x4-bin counts,
@@ -332,6 +374,13 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
                            int32_t max_batch, uint64_t seed, int device, void *cuda_stream, dc_surrogate **out);
 /* kappa of the output skip kappa * field (in_channels = 3). */
 dc_status surrogate_set_skip(dc_surrogate *sg, float kappa);
+
+/* Tensor-core path of the forward convolutions with 64..256 output
+ * channels: DC_SG_MMA_SYNC (default; warp-level mma.sync) or DC_SG_TCGEN05
+ * (fifth-generation tcgen05.mma with the accumulator in tensor memory).
+ * The two sum in different orders (results within FP32 rounding). */
+enum { DC_SG_MMA_SYNC = 0, DC_SG_TCGEN05 = 1 };
+dc_status surrogate_set_tensor_path(dc_surrogate *sg, int32_t path);
 dc_status surrogate_destroy(dc_surrogate *sg);
 
 /* Parameter counts in the unpadded layout used by get/set: for every layer
@@ -369,17 +418,20 @@ dc_status surrogate_apply(dc_ctx *ctx, dc_surrogate *sg, float *pos_xy, int64_t 
                           int32_t max_plain_iters, int32_t *plain_iters_out, double *cv_out);
 
 /* No-allocation variant of integral_images_u32(), for callers that cannot
- * allocate device memory when they need the result: code running while a
- * stream is captured into a CUDA graph (where cudaMalloc and cudaFree are not
- * allowed), loops that cannot afford the synchronisation an allocation may
- * imply, and hosts whose device memory comes from their own pool.  The paper
- * has no counterpart; it is a deployment variant of the same computation.
+ * allocate device memory when they need the result: applications that hand
+ * out all device memory from their own pool or budget and do not let a
+ * library allocate behind their back, and latency-bound loops that cannot
+ * afford the device-wide synchronisation cudaMalloc and cudaFree may imply.
+ * The paper has no counterpart; it is a deployment variant of the same
+ * computation.
  *
  * Needs no context.  Writes the exact uint64 alpha and alpha_t of the device
  * uint32[N*N] array grid, N = 2^log2_res, into alpha_out / alpha_t_out
  * (device, 16-byte aligned, either may be NULL), on cuda_stream (NULL = the
  * legacy default stream), asynchronously, on the calling thread's current
- * device.  Results are bit-identical to integral_images_u32().
+ * device; grid and the outputs must be memory of that device (checked with
+ * cudaPointerGetAttributes before anything is launched: DC_ERR_INVALID_ARG
+ * otherwise).  Results are bit-identical to integral_images_u32().
  *
  * Scratch: one fixed device array inside the library,
  * DC_NOALLOC_SCRATCH_BYTES long, held by every GPU that loads the library
@@ -389,10 +441,14 @@ dc_status surrogate_apply(dc_ctx *ctx, dc_surrogate *sg, float *pos_xy, int64_t 
  * DC_ERR_NOT_POW2; declutter_last_error() gives the reason.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) and sets the kernels' shared-memory attributes with
- * that device current; make that first call before any stream capture.  All calls share the one array and it keeps
- * the last call's contents (none of it needs to start at zero): calls that
- * overlap on the GPU, for instance on two streams, race and must not be
- * issued. */
+ * that device current; make that first call before any stream capture.  All
+ * calls share the one array and it keeps the last call's contents (none of
+ * it needs to start at zero): calls that overlap on the GPU, for instance on
+ * two streams, race and must not be issued.
+ * There is no status word on this path: from 1024 x 1024 the kernels' bulk
+ * copies are waited for with a bounded wait, and if such a wait expired the
+ * results would be wrong with nothing reported (the context path reports it
+ * as DC_ERR_TIMEOUT from declutter_sync). */
 #define DC_NOALLOC_MAX_LOG2_RES 10
 #define DC_NOALLOC_SCRATCH_BYTES 8912896
 dc_status integral_images_u32_noalloc(const uint32_t *grid, uint32_t log2_res, uint64_t *alpha_out,

@@ -1,5 +1,6 @@
 // C ABI and runtime of libdeclutter: context, buffers, streams, CUDA-graph
 // capture of the iteration, instrumentation, error reporting.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -112,8 +113,11 @@ cudaError_t enqueue_inims(dc_ctx *c, cudaStream_t s, const BandArgs &a, int mode
         BandArgs f = a;
         f.zero_out = nullptr;
         rec.count(K_BAND_FUSED);
+        const unsigned long long limit_ns =
+            (c->p.wait_limit_us > 0 ? (unsigned long long)c->p.wait_limit_us : 1000000ull) * 1000ull;
+        const unsigned extra = (c->p.options & DC_OPT_TEST_UNREACHED_BARRIER) ? 1u : 0u;
         for (int t = 0; t < rec.times(K_BAND_FUSED) && e == cudaSuccess; ++t)
-            e = launch_band_fused(s, c->g, mode, c->p.carry_mode, a, f, c->status + kBarWord);
+            e = launch_band_fused(s, c->g, mode, c->p.carry_mode, a, f, c->status + kBarWord, limit_ns, extra);
         return e;
     }
     if (smooth_counts) {
@@ -368,13 +372,23 @@ PanelDesc dc::panel_desc(const dc_ctx *c, float *pos, int64_t n)
     return d;
 }
 
-bool dc::pdl_enabled()
+int dc::device_sms()
 {
-    static const bool on = [] {
-        const char *e = std::getenv("DECLUTTER_PDL");
-        return !(e && e[0] == '0');
-    }();
-    return on;
+    constexpr int kMaxDev = 256;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 1;
+    }
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
 }
 
 extern "C" {
@@ -407,8 +421,12 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
     *out = nullptr;
     const dc_params p = *params;
     if (p.log2_res < 4 || p.log2_res > 13) return fail(DC_ERR_NOT_POW2, "log2_res = %u", p.log2_res);
-    for (int k = 0; k < 3; ++k)
-        if (p.reserved[k] != 0) return fail(DC_ERR_INVALID_ARG, "reserved fields must be zero");
+    if (p.reserved[0] != 0) return fail(DC_ERR_INVALID_ARG, "reserved fields must be zero");
+    constexpr int kKnownOpts = DC_OPT_FUSED_BANDS | DC_OPT_SEPARATE_SMOOTH | DC_OPT_STAGE_HOST |
+                               DC_OPT_BATCHED_LAUNCHES | DC_OPT_TEST_UNREACHED_BARRIER;
+    if (p.options & ~kKnownOpts) return fail(DC_ERR_INVALID_ARG, "unknown options 0x%x", p.options & ~kKnownOpts);
+    if (p.wait_limit_us < 0 || p.wait_limit_us > 10000000)
+        return fail(DC_ERR_INVALID_ARG, "wait_limit_us = %d (0..10^7)", p.wait_limit_us);
     if (p.keep_order != 0 && p.keep_order != 1) return fail(DC_ERR_INVALID_ARG, "keep_order");
     const int N = 1 << p.log2_res;
     int r = p.kernel_r;
@@ -437,7 +455,7 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
     c->device = device;
     c->r = r;
     c->mode = r > 0 ? MODE_FLOAT : MODE_COUNT;
-    c->g = make_band_geom((int)p.log2_res, p.band_rows);
+    c->g = make_band_geom((int)p.log2_res, p.band_rows, device_sms());
     c->sigma = r > 0 ? (p.sigma > 0.f ? p.sigma : (float)r / 3.0f) : 0.f;
     if (r > 0) {
         double g[129], s = 0.0;
@@ -499,14 +517,13 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
         return bail(fail(DC_ERR_OOM, "pinned status word"));
     }
     if (prepare_kernels() != cudaSuccess) return bail(fail(DC_ERR_CUDA, "kernel attributes"));
-    // DECLUTTER_FUSED_BANDS=1: the three band phases as one cooperative
-    // launch on small grids (measured slower than three launches at 512^2)
-    const char *fz = getenv("DECLUTTER_FUSED_BANDS");
-    c->fused = fz && fz[0] == '1' && band_fused_available(c->g, c->mode, c->p.carry_mode, c->device);
+    // DC_OPT_FUSED_BANDS: the three band phases as one cooperative launch on
+    // small grids (measured slower than three launches at 512^2)
+    c->fused = (p.options & DC_OPT_FUSED_BANDS) && band_fused_available(c->g, c->mode, c->p.carry_mode, c->device);
     // the smoothing runs inside the aggregate pass where it fits
-    // (DECLUTTER_FUSED_SMOOTH=0: separate launches, the same bits)
-    const char *fs = getenv("DECLUTTER_FUSED_SMOOTH");
-    c->smooth_agg = !(fs && fs[0] == '0') && !c->fused && c->mode == MODE_FLOAT && smooth_agg_available(c->g, c->w);
+    // (DC_OPT_SEPARATE_SMOOTH: separate launches, the same bits)
+    c->smooth_agg = !(p.options & DC_OPT_SEPARATE_SMOOTH) && !c->fused && c->mode == MODE_FLOAT &&
+                    smooth_agg_available(c->g, c->w);
     *out = c;
     return DC_OK;
 }
@@ -762,11 +779,6 @@ static float *device_alias(float *host_pos)
     float *dp = static_cast<float *>(at.devicePointer);
     return (reinterpret_cast<uintptr_t>(dp) & 7) ? nullptr : dp;
 }
-static bool host_direct_enabled()
-{
-    const char *e = getenv("DECLUTTER_HOST_DIRECT");
-    return !(e && e[0] == '0');
-}
 
 dc_status regularize_host(dc_ctx *c, float *host_pos, int64_t n, int32_t iters, double *uniformity_out)
 {
@@ -778,8 +790,8 @@ dc_status regularize_host(dc_ctx *c, float *host_pos, int64_t n, int32_t iters, 
     // the samples reordered, the iterations touch the caller's array only in
     // the first splat and the reordering (one read each) and in the way back
     // (one write), so they run on it directly over the host link, without
-    // staging copies (DECLUTTER_HOST_DIRECT=0: always stage).
-    if (n > 0 && c->p.keep_order == 0 && host_direct_enabled())
+    // staging copies (DC_OPT_STAGE_HOST: always stage).
+    if (n > 0 && c->p.keep_order == 0 && !(c->p.options & DC_OPT_STAGE_HOST))
         if (float *dp = device_alias(host_pos)) {
             if (dc_status st = regularize(c, dp, n, iters, uniformity_out)) return st;
             return declutter_sync(c);
@@ -800,6 +812,17 @@ dc_status regularize_host(dc_ctx *c, float *host_pos, int64_t n, int32_t iters, 
     if (dc_status st = regularize(c, c->hpos, n, iters, uniformity_out)) return st;
     if (n > 0) DC_CUDA(cudaMemcpyAsync(host_pos, c->hpos, bytes, cudaMemcpyDeviceToHost, c->stream));
     return declutter_sync(c);
+}
+
+dc_status declutter_counts(dc_ctx *c, uint32_t *counts_out)
+{
+    if (dc_status st = check_ctx(c)) return st;
+    if (!counts_out || !aligned(counts_out, 4)) return fail(DC_ERR_INVALID_ARG, "counts_out null or misaligned");
+    if (c->n_last < 0) return fail(DC_ERR_STATE, "declutter_counts before any splat");
+    DeviceGuard guard(c->device);
+    DC_CUDA(cudaMemcpyAsync(counts_out, c->counts_buf[c->cur_counts], sizeof(uint32_t) * (size_t)c->g.N * c->g.N,
+                            cudaMemcpyDeviceToDevice, c->stream));
+    return DC_OK;
 }
 
 dc_status quality_metrics(dc_ctx *c, double *out)

@@ -4,7 +4,7 @@
 // Each panel has its own context (resolution, buffers) and runs as one branch
 // of one CUDA graph (a fork from the capture stream to one stream per branch
 // and a join back), so that the phases of different panels overlap.  With
-// DECLUTTER_BATCHED_LAUNCHES=1 the panels of one resolution instead form a
+// DC_OPT_BATCHED_LAUNCHES the panels of one resolution instead form a
 // class whose every step is one launch over all its panels (the kernels take
 // a table of the panels' buffers and index it with blockIdx.y); the results
 // are bit-identical, but at 120 panels of 256^2..1024^2 the per-panel
@@ -40,7 +40,7 @@ struct dc_batch {
     std::vector<cudaStream_t> branch;
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> join;
-    bool batched = false;  // batched launches per resolution class (DECLUTTER_BATCHED_LAUNCHES=1)
+    bool batched = false;  // batched launches per resolution class (DC_OPT_BATCHED_LAUNCHES)
     struct Entry {
         std::vector<const void *> pos;
         std::vector<int64_t> n;
@@ -172,7 +172,7 @@ dc_status declutter_autotune_band_rows(const dc_params *params, int device, void
     float best_ms = 0.f;
     dc_status st = DC_OK;
     // powers of two, then the automatic height (one band per SM)
-    const int T_auto = make_band_geom(params->log2_res, 0).T;
+    const int T_auto = make_band_geom(params->log2_res, 0, device_sms()).T;
     for (int Tk = 1; Tk <= 128 && st == DC_OK; Tk *= 2) {
         const int T = Tk <= 64 ? Tk : T_auto;
         if (Tk > 64 && (T_auto & (T_auto - 1)) == 0) continue;  // already timed
@@ -227,8 +227,7 @@ dc_status declutter_batch_create(const dc_params *base, const uint32_t *log2_res
     dc_batch *b = new dc_batch();
     b->device = device;
     b->base = *base;
-    const char *bl = getenv("DECLUTTER_BATCHED_LAUNCHES");
-    b->batched = bl && bl[0] == '1';
+    b->batched = (base->options & DC_OPT_BATCHED_LAUNCHES) != 0;
     auto bail = [&](dc_status st) {
         declutter_batch_destroy(b);
         return st;

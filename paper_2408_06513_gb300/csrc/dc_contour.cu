@@ -94,7 +94,7 @@ cudaError_t launch_contour(cudaStream_t s, const float *field, int log2N, float 
     const int64_t M = ((int64_t)1 << log2N) - 1;
     const int64_t cells = M * M;
     int64_t blocks = (cells + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > device_sms() * 16) blocks = device_sms() * 16;
     if (blocks < 1) blocks = 1;
     return launch_kernel(contour_kernel, dim3((unsigned)blocks), dim3(256), 0, s, field, log2N, level,
                          pixel_center ? 0.5f : 0.0f, segs);

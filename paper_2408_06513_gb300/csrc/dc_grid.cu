@@ -26,16 +26,17 @@
 
 namespace dc {
 
-BandGeom make_band_geom(int log2N, int band_rows)
+BandGeom make_band_geom(int log2N, int band_rows, int sms)
 {
     BandGeom g;
     g.log2N = log2N;
     g.N = 1 << log2N;
+    g.sms = sms > 0 ? sms : 1;
     int T = band_rows;
     if (T <= 0) {
-        // from 1024^2 one band for each of the 152 SMs (the last one shorter);
-        // below, N / 256 rows (2 at 512^2: measured 2.6 % faster than 4)
-        T = g.N >= 1024 ? (g.N + 151) / 152 : g.N / 256;
+        // from 1024^2 one band for each SM (the last one shorter); below,
+        // N / 256 rows (2 at 512^2: measured 2.6 % faster than 4)
+        T = g.N >= 1024 ? (g.N + g.sms - 1) / g.sms : g.N / 256;
         if (T < 1) T = 1;
         if (T > 64) T = 64;
     }
@@ -311,6 +312,21 @@ __device__ __forceinline__ float exact_component(long long A1, long long A0, int
     return (float)((neg ? -dm : dm) * inv_den);
 }
 
+// Virtual-lens component t - x of eq. (map) at pixel numerator ai (scale S):
+// t - x = (X(d - mu) + mu X(1) - 2 Call ai) / (2 S Call) with
+// Call = C(d - mu) + mu N^2, i.e. (nx + mu E1 - 2 C(d - mu) ai) * scale where
+// E1 = X(1) - 2 N^2 ai = sum_k w0_k q_k - 2 N^2 ai is formed exactly in
+// integers: the O(1) pixel position cancels before any float rounding.
+__device__ __forceinline__ float lens_component(float nx, const int (&w0)[8], const int (&q)[8], int ai, int log2NN,
+                                                float mu, float Cex, float scale)
+{
+    long long x1 = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x1 += (long long)w0[k] * q[k];
+    const long long e1 = x1 - ((long long)ai << (log2NN + 1));
+    return fmaf(-2.0f * Cex, (float)ai, fmaf(mu, (float)e1, nx)) * scale;
+}
+
 __device__ __forceinline__ unsigned bits32(float x) { return __float_as_uint(x); }
 __device__ __forceinline__ unsigned bits32(uint32_t x) { return x; }
 
@@ -410,7 +426,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T, c
     const Acc *cb = nullptr, *ce = nullptr;
     Acc cvb[CPT], Rk[CPT];
     Acc Ctot = Acc(0), CVbN = Acc(0);
-    float kappa = 0.f, scale = 0.f, lens_s = 0.f;
+    float kappa = 0.f, scale = 0.f;
     if constexpr (FINAL) {
         cb = static_cast<const Acc *>(a.carry) + (size_t)b * carry_stride(N, T);
         ce = static_cast<const Acc *>(a.carry) + (size_t)((N + T - 1) / T) * carry_stride(N, T);
@@ -424,13 +440,15 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T, c
         CVbN = ld_carry<COH>(cb + N - 1);
         if constexpr (MODE == MODE_FLOAT) {
             const float NN = (float)N * (float)N;
-            // the defect's coefficient; the lens keeps t(x, y; d) itself:
-            // X(d) = X(d - mu) + mu X(1), so the coefficient becomes -mu
-            kappa = a.lens ? -a.mu : Ctot / NN;
+            // the defect's coefficient (the lens keeps t(x, y; d) itself and
+            // uses lens_component instead)
+            kappa = Ctot / NN;
             const float S = a.pixel_center ? 2.0f * N : (float)N;
             const float Call = Ctot + a.mu * NN + a.d0 * NN;
             scale = Call > 0.0f ? 1.0f / (2.0f * S * Call) : 0.0f;
-            lens_s = a.lens ? 1.0f / S : 0.0f;  // the pixel position ai / S (exact: S = 2^k)
+            // eq. (map) has no value for a density without mass: the lens
+            // then writes zero and reports an invalid argument
+            if (a.lens && !(Call > 0.0f) && t == 0 && a.status) atomicOr(a.status, (unsigned)DC_ERR_INVALID_ARG);
         }
     }
 
@@ -559,9 +577,13 @@ __device__ __forceinline__ void band_body(const BandArgs &a, int log2N, int T, c
                             nx0 = fmaf((float)w0[q], (float)qx[q], nx0);
                             ny0 = fmaf((float)w0[q], (float)qy[q], ny0);
                         }
-                        // lens: minus the pixel position (lens_s = 0 otherwise: the same bits)
-                        dxy[2 * k] = fmaf(-lens_s, (float)ai, fmaf(-kappa, nx0, nx) * scale);
-                        dxy[2 * k + 1] = fmaf(-lens_s, (float)bj, fmaf(-kappa, ny0, ny) * scale);
+                        if (a.lens) {  // uniform: a launch parameter
+                            dxy[2 * k] = lens_component(nx, w0, qx, ai, 2 * log2N, a.mu, Ctot, scale);
+                            dxy[2 * k + 1] = lens_component(ny, w0, qy, bj, 2 * log2N, a.mu, Ctot, scale);
+                        } else {
+                            dxy[2 * k] = fmaf(-kappa, nx0, nx) * scale;
+                            dxy[2 * k + 1] = fmaf(-kappa, ny0, ny) * scale;
+                        }
                         const float muf = a.mu;
                         fal[k] = al + muf * (float)w0[0];
                         fat[k] = at + muf * (float)w0[4];
@@ -943,7 +965,7 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
     const int L4w = ((((N + T - 1 + 3) >> 2) + 23) >> 5 << 5) + 8;
     C *sA = nullptr, *sU = nullptr, *sV = nullptr, *sR = nullptr, *sAm = nullptr, *sBm = nullptr;
     C Ctot = C(0), CVbN = C(0);
-    float kappa = 0.f, scale = 0.f, lens_s = 0.f;
+    float kappa = 0.f, scale = 0.f;
     if constexpr (FINAL) {
         C *p = reinterpret_cast<C *>(s_dyn + (RING ? (size_t)ring * rowbytes : 0));
         sA = p; p += 4 * L4a;
@@ -974,11 +996,11 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
         CVbN = cb[N - 1];
         if constexpr (MODE == MODE_FLOAT) {
             const float NN = (float)N * (float)N;
-            kappa = a.lens ? -a.mu : Ctot / NN;  // as in band_body
+            kappa = Ctot / NN;  // as in band_body
             const float Sg = a.pixel_center ? 2.0f * N : (float)N;
             const float Call = Ctot + a.mu * NN + a.d0 * NN;
             scale = Call > 0.0f ? 1.0f / (2.0f * Sg * Call) : 0.0f;
-            lens_s = a.lens ? 1.0f / Sg : 0.0f;
+            if (a.lens && !(Call > 0.0f) && t == 0 && a.status) atomicOr(a.status, (unsigned)DC_ERR_INVALID_ARG);
         }
         // the first row's barrier orders these writes before any read
     }
@@ -1210,8 +1232,13 @@ __global__ void __launch_bounds__(NT) band2_kernel(BandArgs a, int log2N, int T,
                                 nx0 = fmaf((float)w0[k], (float)qx[k], nx0);
                                 ny0 = fmaf((float)w0[k], (float)qy[k], ny0);
                             }
-                            dxy[2 * e] = fmaf(-lens_s, (float)ai, fmaf(-kappa, nx0, nx) * scale);
-                            dxy[2 * e + 1] = fmaf(-lens_s, (float)bj, fmaf(-kappa, ny0, ny) * scale);
+                            if (a.lens) {  // uniform: a launch parameter
+                                dxy[2 * e] = lens_component(nx, w0, qx, ai, 2 * log2N, a.mu, Ctot, scale);
+                                dxy[2 * e + 1] = lens_component(ny, w0, qy, bj, 2 * log2N, a.mu, Ctot, scale);
+                            } else {
+                                dxy[2 * e] = fmaf(-kappa, nx0, nx) * scale;
+                                dxy[2 * e + 1] = fmaf(-kappa, ny0, ny) * scale;
+                            }
                             oal[e] = al + a.mu * (float)w0[0];
                             oat[e] = at + a.mu * (float)w0[4];
                         } else {
@@ -1688,9 +1715,13 @@ __global__ void __launch_bounds__(1024, 1) carry_kernel(const Acc *__restrict__ 
 // ------------------------------------------------------------------------
 
 // Sense-reversing grid barrier on bar[0] (arrivals) and bar[1] (generation);
-// reusable across barriers and launches without a reset.  Waits at most one
-// second (then DC_ERR_TIMEOUT in status, and the CTA goes on).
-__device__ __noinline__ void grid_barrier(unsigned *bar, unsigned nblocks, unsigned *status)
+// reusable across barriers and launches without a reset.  Waits at most
+// limit_ns (then DC_ERR_TIMEOUT in status, and the CTA goes on; the status
+// reset of declutter_sync also clears both words).  nblocks is the number of
+// arrivals that completes the barrier: the grid size, or more when a test
+// makes every wait run to its limit.
+__device__ __noinline__ void grid_barrier(unsigned *bar, unsigned nblocks, unsigned *status,
+                                          unsigned long long limit_ns)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1704,7 +1735,7 @@ __device__ __noinline__ void grid_barrier(unsigned *bar, unsigned nblocks, unsig
         } else {
             const unsigned long long t0 = global_ns();
             while (*gen == g0) {
-                if (global_ns() - t0 > 1000000000ull) {
+                if (global_ns() - t0 > limit_ns) {
                     if (status) atomicOr(status, (unsigned)DC_ERR_TIMEOUT);
                     break;
                 }
@@ -1790,16 +1821,17 @@ __device__ void carry_phase(const Acc *agg, Acc *carry, int N, int T, int nb, in
 
 template <int MODE, int CPT, typename Sum>
 __global__ void __launch_bounds__(CPT == 1 ? 64 : 512) band_fused_kernel(BandArgs aagg, BandArgs afin, int log2N, int T,
-                                                                        unsigned *bar)
+                                                                        unsigned *bar, unsigned long long limit_ns,
+                                                                        unsigned extra_arrivals)
 {
     using Acc = typename ModeT<MODE>::Acc;
     __shared__ Sum s_part[CPT == 1 ? 64 : 512];
     band_body<MODE, CPT, false>(aagg, log2N, T);
-    grid_barrier(bar, gridDim.x, afin.status);
+    grid_barrier(bar, gridDim.x + extra_arrivals, afin.status, limit_ns);
     const int N = 1 << log2N;
     carry_phase<Acc, Sum>(static_cast<const Acc *>(aagg.agg), static_cast<Acc *>(const_cast<void *>(afin.carry)), N,
                           T, (N + T - 1) / T, aagg.agg_stride, s_part);
-    grid_barrier(bar, gridDim.x, afin.status);
+    grid_barrier(bar, gridDim.x + extra_arrivals, afin.status, limit_ns);
     band_body<MODE, CPT, true, true>(afin, log2N, T);
 }
 
@@ -2078,14 +2110,15 @@ cudaError_t launch_band_final(cudaStream_t s, const BandGeom &g, int mode, const
     return cudaErrorInvalidValue;
 }
 
+using FusedFn = void (*)(BandArgs, BandArgs, int, int, unsigned *, unsigned long long, unsigned);
 template <int MODE, typename Sum>
-static void (*fused_ptr(int CPT))(BandArgs, BandArgs, int, int, unsigned *)
+static FusedFn fused_ptr(int CPT)
 {
     if (CPT == 1) return band_fused_kernel<MODE, 1, Sum>;
     if (CPT == 4) return band_fused_kernel<MODE, 4, Sum>;
     return nullptr;
 }
-static void (*fused_kernel_for(const BandGeom &g, int mode, int carry_mode))(BandArgs, BandArgs, int, int, unsigned *)
+static FusedFn fused_kernel_for(const BandGeom &g, int mode, int carry_mode)
 {
     if (g.log2N >= interleaved_min_log2(mode) || (mode != MODE_COUNT && mode != MODE_FLOAT)) return nullptr;
     if (5 * g.T > g.NT) return nullptr;  // carry lanes of a CTA: at most one per thread
@@ -2109,7 +2142,8 @@ bool band_fused_available(const BandGeom &g, int mode, int carry_mode, int devic
 }
 
 cudaError_t launch_band_fused(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const BandArgs &aagg,
-                              const BandArgs &afin, unsigned *bar)
+                              const BandArgs &afin, unsigned *bar, unsigned long long limit_ns,
+                              unsigned extra_arrivals)
 {
     auto k = fused_kernel_for(g, mode, carry_mode);
     if (!k) return cudaErrorInvalidValue;
@@ -2122,15 +2156,15 @@ cudaError_t launch_band_fused(cudaStream_t s, const BandGeom &g, int mode, int c
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, aagg, afin, g.log2N, g.T, bar);
+    return cudaLaunchKernelEx(&cfg, k, aagg, afin, g.log2N, g.T, bar, limit_ns, extra_arrivals);
 }
 
 cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const void *agg, void *carry)
 {
     // groups of bands per block (one warp each): as many as keep all blocks
-    // resident at once on 152 SMs of 2048 threads, at most 32 and nb
+    // resident at once on the device's SMs of 2048 threads, at most 32 and nb
     const int nblk = (g.lanes + 31) / 32;
-    int cap = 152 * 64 / nblk;
+    int cap = g.sms * 64 / nblk;
     if (cap > 32) cap = 32;
     if (cap > g.nb) cap = g.nb;
     int ng = 1;
@@ -2184,7 +2218,7 @@ static cudaError_t band_batched_mode(cudaStream_t s, const BandGeom &g, int carr
     int ng = 32;  // groups of bands per carry block: as launch_carry, so that
     {             // float carries are summed in the same order as for one panel
         const int nblk = (g.lanes + 31) / 32;
-        int cap = 152 * 64 / nblk;
+        int cap = g.sms * 64 / nblk;
         if (cap > 32) cap = 32;
         if (cap > g.nb) cap = g.nb;
         ng = 1;

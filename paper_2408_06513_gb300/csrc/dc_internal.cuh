@@ -18,8 +18,6 @@ namespace dc {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-bool pdl_enabled();  // DECLUTTER_PDL=0 in the environment turns it off
-
 template <typename... KArgs, typename... Args>
 cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                           Args... args)
@@ -33,7 +31,7 @@ cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
@@ -71,9 +69,14 @@ struct BandGeom {
     int NT = 0, CPT = 0;
     int agg_stride = 0; // elements per band in the compact aggregate array
     int lanes = 0;      // 5N absolute carry lanes
+    int sms = 0;        // SMs of the device (band and carry launch shapes)
 };
 
-BandGeom make_band_geom(int log2N, int band_rows);
+// band_rows = 0: automatic height for a device of `sms` SMs
+BandGeom make_band_geom(int log2N, int band_rows, int sms);
+// SM count of the calling thread's current device (cached per device; 1 if
+// it cannot be queried)
+int device_sms();
 
 // Gaussian weights passed by value (kernel parameter space).
 struct GaussW {
@@ -162,9 +165,13 @@ cudaError_t launch_carry(cudaStream_t s, const BandGeom &g, int mode, int carry_
 cudaError_t launch_band_final(cudaStream_t s, const BandGeom &g, int mode, const BandArgs &a);
 // one cooperative launch of the three band phases (grids below 2048^2);
 // available when all CTAs fit on the device at once; bar: two device words
+// bar: two device words; each grid-barrier wait gives up after limit_ns
+// (DC_ERR_TIMEOUT); extra_arrivals > 0 makes the barrier wait for that many
+// CTAs more than the grid holds (testing the timeout path)
 bool band_fused_available(const BandGeom &g, int mode, int carry_mode, int device);
 cudaError_t launch_band_fused(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const BandArgs &aagg,
-                              const BandArgs &afin, unsigned *bar);
+                              const BandArgs &afin, unsigned *bar, unsigned long long limit_ns,
+                              unsigned extra_arrivals);
 int smooth_smem_bytes(int r);
 // batched launches over P same-resolution panels (tab: device PanelDesc[P]);
 // max_n: the largest n; which / cur: count grid index; nxt: grid to splat the

@@ -2,13 +2,12 @@
 // uint32 grid without a context and without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need
-// the integral images: code that runs while a stream is being captured into
-// a CUDA graph (cudaMalloc and cudaFree are not allowed there), latency-bound
-// loops that cannot afford the device-wide synchronisation cudaMalloc and
-// cudaFree may imply, and hosts whose device memory is handed out by their
-// own pool and must not be bypassed.  This entry point keeps its band
-// aggregates and carries in one fixed array that the library declares at
-// file scope; the caller passes only the grid and the outputs.
+// the integral images: applications that hand out all device memory from
+// their own pool or budget and do not let a library allocate behind their
+// back, and latency-bound loops that cannot afford the device-wide
+// synchronisation that cudaMalloc and cudaFree may imply.  This entry point
+// keeps its band aggregates and carries in one fixed array that the library
+// declares at file scope; the caller passes only the grid and the outputs.
 #include <cstdio>
 #include <mutex>
 
@@ -19,7 +18,8 @@ using namespace dc;
 namespace {
 
 // 8.5 MiB: room for the aggregates and carries of the largest supported
-// grid, 1024 x 1024 with the default band height (7,299,360 bytes).  Every GPU
+// grid, 1024 x 1024 (7,299,360 bytes with one band per SM of a 152-SM GPU; on
+// a GPU with more SMs the bands are made taller until they fit).  Every GPU
 // that loads the library holds this array until the process exits.
 constexpr size_t kNoallocScratchBytes = DC_NOALLOC_SCRATCH_BYTES;
 constexpr uint32_t kNoallocMaxLog2Res = DC_NOALLOC_MAX_LOG2_RES;
@@ -64,6 +64,26 @@ extern "C" dc_status integral_images_u32_noalloc(const uint32_t *grid, uint32_t 
         snprintf(g_noalloc_msg, sizeof(g_noalloc_msg), "no current CUDA device");
         return noalloc_fail(DC_ERR_CUDA);
     }
+    // the grid and the outputs must be device memory of the current device:
+    // the kernels run there and the scratch array is that device's copy
+    {
+        const void *ptrs[3] = {grid, alpha_out, alpha_t_out};
+        const char *names[3] = {"grid", "alpha_out", "alpha_t_out"};
+        for (int k = 0; k < 3; ++k) {
+            if (!ptrs[k]) continue;
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, ptrs[k]) != cudaSuccess) {
+                cudaGetLastError();
+                at.type = cudaMemoryTypeUnregistered;
+            }
+            if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev) {
+                snprintf(g_noalloc_msg, sizeof(g_noalloc_msg),
+                         "%s is not device memory of the current device %d (memory type %d, device %d)", names[k],
+                         dev, (int)at.type, at.device);
+                return noalloc_fail(DC_ERR_INVALID_ARG);
+            }
+        }
+    }
     void *scratch = nullptr;
     {
         // once per device, with that device current: the array's device address
@@ -86,11 +106,21 @@ extern "C" dc_status integral_images_u32_noalloc(const uint32_t *grid, uint32_t 
         scratch = g_noalloc_ptr[dev];
     }
 
-    const BandGeom g = make_band_geom((int)log2_res, 0);
-    const size_t agg_bytes = ((size_t)g.nb * g.agg_stride * sizeof(unsigned long long) + 255) & ~size_t(255);
+    // the automatic band height, made taller while the bands' aggregates and
+    // carries do not fit the array (the sums are exact for any height)
+    const int sms = device_sms();
+    BandGeom g = make_band_geom((int)log2_res, 0, sms);
+    auto agg_size = [](const BandGeom &q) {
+        return ((size_t)q.nb * q.agg_stride * sizeof(unsigned long long) + 255) & ~size_t(255);
+    };
     // per band the lanes its final pass reads, then the 5N totals
-    const size_t carry_bytes =
-        ((size_t)g.nb * ((3 * g.N + 2 * g.T - 2 + 3) & ~3) + (size_t)g.lanes) * sizeof(unsigned long long);
+    auto carry_size = [](const BandGeom &q) {
+        return ((size_t)q.nb * ((3 * q.N + 2 * q.T - 2 + 3) & ~3) + (size_t)q.lanes) * sizeof(unsigned long long);
+    };
+    while (agg_size(g) + carry_size(g) > kNoallocScratchBytes && g.T < 64 && g.T < g.N)
+        g = make_band_geom((int)log2_res, g.T + 1, sms);
+    const size_t agg_bytes = agg_size(g);
+    const size_t carry_bytes = carry_size(g);
     if (agg_bytes + carry_bytes > kNoallocScratchBytes) {
         snprintf(g_noalloc_msg, sizeof(g_noalloc_msg), "grid needs %zu scratch bytes, limit %zu",
                  agg_bytes + carry_bytes, kNoallocScratchBytes);

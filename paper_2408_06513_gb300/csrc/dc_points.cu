@@ -481,10 +481,10 @@ int advect_wave()
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
-        return 152 * 4;
+        return device_sms() * 4;
     }
     const int w = g_advect_wave[dev].load(std::memory_order_relaxed);
-    return w > 0 ? w : 152 * 4;
+    return w > 0 ? w : device_sms() * 4;
 }
 
 }  // namespace
@@ -504,7 +504,7 @@ cudaError_t prepare_point_kernels()
 cudaError_t launch_splat(cudaStream_t s, const float2 *pos, int64_t n, uint32_t *counts, int log2N)
 {
     if (n <= 0) return cudaSuccess;
-    return launch_kernel(splat_kernel, dim3(grid_for(n, kThreads, 152 * 16)), dim3(kThreads), 0, s, pos, n, counts,
+    return launch_kernel(splat_kernel, dim3(grid_for(n, kThreads, device_sms() * 16)), dim3(kThreads), 0, s, pos, n, counts,
                          log2N);
 }
 
@@ -548,7 +548,7 @@ cudaError_t launch_splat_rank(cudaStream_t s, const float2 *pos, int64_t n, uint
                               uint32_t *rank)
 {
     if (n <= 0) return cudaSuccess;
-    return launch_kernel(splat_rank_kernel, dim3(grid_for(n, kThreads, 152 * 16)), dim3(kThreads), 0, s, pos, n,
+    return launch_kernel(splat_rank_kernel, dim3(grid_for(n, kThreads, device_sms() * 16)), dim3(kThreads), 0, s, pos, n,
                          counts, log2N, rank);
 }
 
@@ -556,7 +556,7 @@ cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n,
                                    const uint32_t *rank, float2 *spos, uint32_t *inv, unsigned *status)
 {
     if (n <= 0) return cudaSuccess;
-    return launch_kernel(reorder_scatter_kernel, dim3(grid_for(n, kThreads, 152 * 8)), dim3(kThreads), 0, s, pos, n,
+    return launch_kernel(reorder_scatter_kernel, dim3(grid_for(n, kThreads, device_sms() * 8)), dim3(kThreads), 0, s, pos, n,
                          log2N, cursor, rank, spos, inv, status);
 }
 
@@ -564,14 +564,14 @@ cudaError_t launch_reorder_back(cudaStream_t s, const float2 *spos, const uint32
                                 unsigned *status)
 {
     if (n <= 0) return cudaSuccess;
-    return launch_kernel(reorder_gather_back_kernel, dim3(grid_for(n, kThreads, 152 * 8)), dim3(kThreads), 0, s,
+    return launch_kernel(reorder_gather_back_kernel, dim3(grid_for(n, kThreads, device_sms() * 8)), dim3(kThreads), 0, s,
                          spos, inv, n, pos, status);
 }
 
 cudaError_t launch_quality(cudaStream_t s, const uint32_t *counts, int log2N, unsigned long long *acc)
 {
     const int B = (1 << log2N) >> 2;
-    return launch_kernel(quality_kernel, dim3(grid_for((int64_t)B * B, kThreads, 152 * 4)), dim3(kThreads), 0, s,
+    return launch_kernel(quality_kernel, dim3(grid_for((int64_t)B * B, kThreads, device_sms() * 4)), dim3(kThreads), 0, s,
                          counts, log2N, acc);
 }
 
@@ -645,7 +645,7 @@ cudaError_t launch_zero_batched(cudaStream_t s, const PanelDesc *tab, int P, int
 cudaError_t launch_splat_rank_batched(cudaStream_t s, const PanelDesc *tab, int P, int64_t max_n, int log2N)
 {
     if (max_n <= 0) return cudaSuccess;
-    return launch_kernel(splat_rank_batched_kernel, dim3(grid_for(max_n, kThreads, 152 * 16), P), dim3(kThreads), 0,
+    return launch_kernel(splat_rank_batched_kernel, dim3(grid_for(max_n, kThreads, device_sms() * 16), P), dim3(kThreads), 0,
                          s, tab, log2N);
 }
 
@@ -659,7 +659,7 @@ cudaError_t launch_reorder_batched(cudaStream_t s, const PanelDesc *tab, int P, 
     if (e == cudaSuccess)
         e = launch_kernel(scan_apply_batched_kernel, dim3(nch, P), dim3(kScanThreads), 0, s, tab, M, chunk);
     if (e == cudaSuccess)
-        e = launch_kernel(scatter_batched_kernel, dim3(grid_for(max_n, kThreads, 152 * 8), P), dim3(kThreads), 0, s,
+        e = launch_kernel(scatter_batched_kernel, dim3(grid_for(max_n, kThreads, device_sms() * 8), P), dim3(kThreads), 0, s,
                           tab, log2N);
     return e;
 }
@@ -668,7 +668,7 @@ cudaError_t launch_advect_batched(cudaStream_t s, const PanelDesc *tab, int P, i
                                   int pixel_center, int clamp, int nxt, bool sorted)
 {
     if (max_n <= 0) return cudaSuccess;
-    const dim3 grid(grid_for((max_n + 3) / 4, kThreads, 152 * 8), P);
+    const dim3 grid(grid_for((max_n + 3) / 4, kThreads, device_sms() * 8), P);
     if (sorted && log2N <= 10)
         return launch_kernel(advect_batched_kernel<true>, grid, dim3(kThreads), 0, s, tab, log2N,
                              pixel_center ? 0.5f : 0.0f, clamp, nxt);
@@ -679,14 +679,14 @@ cudaError_t launch_advect_batched(cudaStream_t s, const PanelDesc *tab, int P, i
 cudaError_t launch_quality_batched(cudaStream_t s, const PanelDesc *tab, int P, int log2N, int which, int slot)
 {
     const int B = 1 << (log2N - 2);
-    return launch_kernel(quality_batched_kernel, dim3(grid_for((int64_t)B * B, kThreads, 152 * 4), P), dim3(kThreads),
+    return launch_kernel(quality_batched_kernel, dim3(grid_for((int64_t)B * B, kThreads, device_sms() * 4), P), dim3(kThreads),
                          0, s, tab, log2N, which, slot);
 }
 
 cudaError_t launch_back_batched(cudaStream_t s, const PanelDesc *tab, int P, int64_t max_n)
 {
     if (max_n <= 0) return cudaSuccess;
-    return launch_kernel(back_batched_kernel, dim3(grid_for(max_n, kThreads, 152 * 8), P), dim3(kThreads), 0, s, tab);
+    return launch_kernel(back_batched_kernel, dim3(grid_for(max_n, kThreads, device_sms() * 8), P), dim3(kThreads), 0, s, tab);
 }
 
 }  // namespace dc

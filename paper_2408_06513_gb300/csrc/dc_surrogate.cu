@@ -370,7 +370,7 @@ __global__ void field_to_disp_kernel(const float *__restrict__ F, int64_t P, flo
     GRID_STRIDE(i, P) disp[i] = make_float2(F[2 * i] * invN, F[2 * i + 1] * invN);
 }
 
-int eb(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
+int eb(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, (int64_t)device_sms() * 16); }
 
 // host-side normal deviates (splitmix64 + Box-Muller), deterministic by seed
 struct HostRng {
@@ -413,7 +413,7 @@ struct dc_surrogate {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     bool tcgen05 = false;               // forward convolutions of 64..256 channels on tcgen05
-                                        // (DECLUTTER_SG_TCGEN05=1; measured slower at these sizes)
+                                        // (surrogate_set_tensor_path; measured slower at these sizes)
     unsigned *status = nullptr;         // DC_ERR_TIMEOUT from a bounded wait in a kernel
     cudaEvent_t ev[2] = {nullptr, nullptr};  // stream ordering with a context in surrogate_apply
     // surrogate_apply's forward pass + field conversion as one CUDA graph,
@@ -452,8 +452,9 @@ int find_layer(const dc_surrogate *s, const std::string &name)
     return -1;
 }
 
-// Split-K workspace of the forward convolutions (fp32 partial sums).
-constexpr size_t kSplitAccElems = (size_t)2 * 152 * BM * BN;
+// Split-K workspace of the forward convolutions (fp32 partial sums): layers
+// whose output has at most this many elements may split K.
+constexpr size_t kSplitAccElems = (size_t)320 * BM * BN;
 
 // y = act(conv(x) + bias) (bf16), optionally the decoder skip sum
 // sadd = bf16(y + skip) and the fp32 head output yf.  up: x at half
@@ -490,8 +491,9 @@ cudaError_t conv_forward(dc_surrogate *s, const Layer &L, const bf16 *x, int B, 
     const int ksteps = (p.K + tk - 1) / tk;
     const int min_steps = um ? 2 : 8;  // k-steps a split at least
     int splits = 1;
-    if (tiles < 2 * 152 && (size_t)p.M * p.N <= kSplitAccElems) {
-        splits = (2 * 152 + tiles - 1) / tiles;
+    const int sms = device_sms();
+    if (tiles < 2 * sms && (size_t)p.M * p.N <= kSplitAccElems) {
+        splits = (2 * sms + tiles - 1) / tiles;
         if (splits > ksteps / min_steps) splits = ksteps / min_steps;
         if (splits < 1) splits = 1;
     }
@@ -535,7 +537,7 @@ cudaError_t conv_backward(dc_surrogate *s, const Layer &L, const bf16 *x, const 
     // registers and 18 KB): the tiles are few and each k-step is latency-bound
     // (2 a SM measured 8.97 ms a training step at batch 16, 8 a SM 7.55 ms)
     const int tiles = ((w.M + BM - 1) / BM) * ((w.N + BN - 1) / BN);
-    int splits = (int)std::max<int64_t>(1, std::min<int64_t>((8 * 152 + tiles - 1) / tiles, P / (4 * BK)));
+    int splits = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)8 * device_sms() + tiles - 1) / tiles, P / (4 * BK)));
     cudaError_t e = run_gemm(s->stream, w, splits);
     if (e != cudaSuccess) return e;
     const int64_t chunk = 256;
@@ -680,7 +682,6 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
     if (!out) return sfail(DC_ERR_INVALID_ARG, "null out");
     *out = nullptr;
     if (in_channels != 1 && in_channels != 3) return sfail(DC_ERR_INVALID_ARG, "in_channels = %d", in_channels);
-    const char *tc = getenv("DECLUTTER_SG_TCGEN05");
     if (levels < 1 || levels > 6 || base_channels < 8 || base_channels > 256 || (base_channels & 7))
         return sfail(DC_ERR_INVALID_ARG, "levels = %d, base_channels = %d", levels, base_channels);
     if (log2_res < levels + 2 || log2_res > 11) return sfail(DC_ERR_INVALID_ARG, "log2_res = %d", log2_res);
@@ -690,7 +691,7 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
     s->levels = levels;
     s->c0 = base_channels;
     s->in_channels = in_channels;
-    s->tcgen05 = tc && tc[0] == '1';
+    s->tcgen05 = false;
     s->log2H = log2_res;
     s->max_batch = max_batch;
     s->device = device;
@@ -935,6 +936,21 @@ dc_status surrogate_set_skip(dc_surrogate *s, float kappa)
         s->apply_exec = nullptr;
     }
     s->kappa = kappa;
+    return DC_OK;
+}
+
+dc_status surrogate_set_tensor_path(dc_surrogate *sg, int32_t path)
+{
+    if (dc_status st = check_sg(sg)) return st;
+    if (path != DC_SG_MMA_SYNC && path != DC_SG_TCGEN05) return sfail(DC_ERR_INVALID_ARG, "path = %d", path);
+    const bool tc = path == DC_SG_TCGEN05;
+    if (tc != sg->tcgen05 && sg->apply_exec) {  // the captured forward holds the old kernels
+        SgGuard guard(sg->device);
+        cudaStreamSynchronize(sg->stream);
+        cudaGraphExecDestroy(sg->apply_exec);
+        sg->apply_exec = nullptr;
+    }
+    sg->tcgen05 = tc;
     return DC_OK;
 }
 

@@ -26,13 +26,15 @@ __all__ = [
     "DeclutterError", "Context", "dc_params", "dc_info", "load_library", "exported_symbols",
     "declutter_create", "declutter_destroy", "declutter_get_info", "splat_density", "integral_images",
     "integral_images_u32", "displacement_field", "lens_field", "contour_segments", "advect_samples", "regularize", "regularize_host",
-    "quality_metrics", "declutter_sync", "declutter_profile_regularize", "declutter_kernel_name",
+    "quality_metrics", "declutter_counts", "declutter_sync", "declutter_profile_regularize", "declutter_kernel_name",
     "declutter_status_string", "declutter_last_error", "DC_CARRY_COMPENSATED", "DC_CARRY_F64",
+    "DC_OPT_FUSED_BANDS", "DC_OPT_SEPARATE_SMOOTH", "DC_OPT_STAGE_HOST", "DC_OPT_BATCHED_LAUNCHES",
+    "DC_OPT_TEST_UNREACHED_BARRIER", "DC_SG_MMA_SYNC", "DC_SG_TCGEN05",
     "integral_images_u32_noalloc", "DC_NOALLOC_MAX_LOG2_RES", "Batch", "declutter_batch_create",
     "declutter_batch_destroy", "declutter_batch_regularize", "declutter_batch_sync",
     "declutter_autotune_band_rows", "declutter_batch_autotune", "regularize_tracers", "Surrogate",
     "surrogate_create", "surrogate_destroy", "surrogate_num_params", "surrogate_get_params", "surrogate_set_params",
-    "surrogate_get_grads", "surrogate_set_skip", "surrogate_forward", "surrogate_loss_grad", "surrogate_train_step", "surrogate_apply",
+    "surrogate_get_grads", "surrogate_set_skip", "surrogate_set_tensor_path", "surrogate_forward", "surrogate_loss_grad", "surrogate_train_step", "surrogate_apply",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -42,6 +44,15 @@ KERNEL_KINDS = 10
 DC_CARRY_COMPENSATED = 0
 DC_CARRY_F64 = 1
 DC_NOALLOC_MAX_LOG2_RES = 10
+# dc_params.options
+DC_OPT_FUSED_BANDS = 1
+DC_OPT_SEPARATE_SMOOTH = 2
+DC_OPT_STAGE_HOST = 4
+DC_OPT_BATCHED_LAUNCHES = 8
+DC_OPT_TEST_UNREACHED_BARRIER = 1 << 30
+# surrogate_set_tensor_path
+DC_SG_MMA_SYNC = 0
+DC_SG_TCGEN05 = 1
 
 
 class DeclutterError(RuntimeError):
@@ -61,7 +72,9 @@ class dc_params(ctypes.Structure):
         ("carry_mode", ctypes.c_int32),
         ("band_rows", ctypes.c_int32),
         ("keep_order", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("options", ctypes.c_int32),
+        ("wait_limit_us", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
 
@@ -97,6 +110,7 @@ _SIGS = [
     ("regularize", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
     ("regularize_host", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
     ("quality_metrics", ctypes.c_int, [_P, _P]),
+    ("declutter_counts", ctypes.c_int, [_P, _P]),
     ("declutter_sync", ctypes.c_int, [_P]),
     ("declutter_profile_regularize", ctypes.c_int,
      [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
@@ -113,6 +127,7 @@ _SIGS = [
     ("surrogate_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_uint64, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     ("surrogate_set_skip", ctypes.c_int, [_P, ctypes.c_float]),
+    ("surrogate_set_tensor_path", ctypes.c_int, [_P, ctypes.c_int32]),
     ("surrogate_destroy", ctypes.c_int, [_P]),
     ("surrogate_num_params", ctypes.c_int, [_P, _P, _P]),
     ("surrogate_get_params", ctypes.c_int, [_P, _P, _P]),
@@ -168,13 +183,16 @@ def _check(status: int, where: str):
         raise DeclutterError(status, where, f"{declutter_status_string(status)}: {declutter_last_error()}")
 
 
-def _ptr(t, dtype=None, numel=None, name="tensor"):
-    """Device pointer of a CUDA tensor (or None -> NULL)."""
+def _ptr(t, dtype=None, numel=None, name="tensor", device=None):
+    """Device pointer of a CUDA tensor (or None -> NULL); with ``device``,
+    the tensor must live on that CUDA device."""
     if t is None:
         return None
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
+    if device is not None and t.device.index != int(device):
+        raise ValueError(f"{name} is on {t.device}, expected cuda:{int(device)}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if dtype is not None and t.dtype != dtype:
@@ -207,7 +225,8 @@ class Context:
 
 def make_params(log2_res: int, kernel_r: int = -1, sigma: float = 0.0, d0: float = -1.0,
                 pixel_center: bool = False, clamp_positions: bool = True,
-                carry_mode: int = DC_CARRY_COMPENSATED, band_rows: int = 0, keep_order: bool = False) -> dc_params:
+                carry_mode: int = DC_CARRY_COMPENSATED, band_rows: int = 0, keep_order: bool = False,
+                options: int = 0, wait_limit_us: int = 0) -> dc_params:
     p = dc_params()
     p.log2_res = int(log2_res)
     p.kernel_r = int(kernel_r)
@@ -218,6 +237,8 @@ def make_params(log2_res: int, kernel_r: int = -1, sigma: float = 0.0, d0: float
     p.carry_mode = int(carry_mode)
     p.band_rows = int(band_rows)
     p.keep_order = int(bool(keep_order))
+    p.options = int(options)
+    p.wait_limit_us = int(wait_limit_us)
     return p
 
 
@@ -232,7 +253,7 @@ def _stream_ptr(stream, device):
 def declutter_create(log2_res: int, kernel_r: int = -1, sigma: float = 0.0, d0: float = -1.0,
                      pixel_center: bool = False, clamp_positions: bool = True,
                      carry_mode: int = DC_CARRY_COMPENSATED, band_rows: int = 0, keep_order: bool = False,
-                     device: int | None = None, stream=None) -> Context:
+                     options: int = 0, wait_limit_us: int = 0, device: int | None = None, stream=None) -> Context:
     """Create a context.  ``stream``: a ``torch.cuda.Stream`` or None for the
     current torch stream (the library makes its own stream, ordered with the
     legacy default stream, when that is the default stream)."""
@@ -243,7 +264,8 @@ def declutter_create(log2_res: int, kernel_r: int = -1, sigma: float = 0.0, d0: 
     if stream is None:
         stream = torch.cuda.current_stream(device)
     sp = getattr(stream, "cuda_stream", stream) or 0
-    p = make_params(log2_res, kernel_r, sigma, d0, pixel_center, clamp_positions, carry_mode, band_rows, keep_order)
+    p = make_params(log2_res, kernel_r, sigma, d0, pixel_center, clamp_positions, carry_mode, band_rows, keep_order,
+                    options, wait_limit_us)
     h = ctypes.c_void_p()
     _check(lib.declutter_create(ctypes.byref(p), int(device), ctypes.c_void_p(sp) if sp else None,
                                 ctypes.byref(h)), "declutter_create")
@@ -262,29 +284,29 @@ def declutter_get_info(ctx: Context) -> dc_info:
     return out
 
 
-def _pos_args(pos):
+def _pos_args(pos, device=None, name="pos"):
     import torch
     if pos.dim() != 2 or pos.shape[1] != 2:
-        raise ValueError("pos must have shape [n, 2]")
-    return _ptr(pos, torch.float32, name="pos"), int(pos.shape[0])
+        raise ValueError(f"{name} must have shape [n, 2]")
+    return _ptr(pos, torch.float32, name=name, device=device), int(pos.shape[0])
 
 
 def splat_density(ctx: Context, pos, counts_out=None, density_out=None) -> None:
     import torch
-    pp, n = _pos_args(pos)
+    pp, n = _pos_args(pos, ctx.device)
     NN = ctx.N * ctx.N
     _check(load_library().splat_density(ctx.handle, pp, n,
-                                        _ptr(counts_out, torch.int32, NN, "counts_out"),
-                                        _ptr(density_out, torch.float32, NN, "density_out")), "splat_density")
+                                        _ptr(counts_out, torch.int32, NN, "counts_out", ctx.device),
+                                        _ptr(density_out, torch.float32, NN, "density_out", ctx.device)), "splat_density")
 
 
-def _u64(t, NN, name):
+def _u64(t, NN, name, device=None):
     import torch
     if t is None:
         return None
     if t.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)):
         raise TypeError(f"{name} must be a 64-bit integer tensor")
-    return _ptr(t, None, NN, name)
+    return _ptr(t, None, NN, name, device)
 
 
 def integral_images(ctx: Context, alpha_out=None, alpha_t_out=None) -> None:
@@ -292,10 +314,10 @@ def integral_images(ctx: Context, alpha_out=None, alpha_t_out=None) -> None:
     import torch
     NN = ctx.N * ctx.N
     if int(ctx.params.kernel_r) == 0:
-        a, b = _u64(alpha_out, NN, "alpha_out"), _u64(alpha_t_out, NN, "alpha_t_out")
+        a, b = _u64(alpha_out, NN, "alpha_out", ctx.device), _u64(alpha_t_out, NN, "alpha_t_out", ctx.device)
     else:
-        a = _ptr(alpha_out, torch.float32, NN, "alpha_out")
-        b = _ptr(alpha_t_out, torch.float32, NN, "alpha_t_out")
+        a = _ptr(alpha_out, torch.float32, NN, "alpha_out", ctx.device)
+        b = _ptr(alpha_t_out, torch.float32, NN, "alpha_t_out", ctx.device)
     _check(load_library().integral_images(ctx.handle, a, b), "integral_images")
 
 
@@ -303,15 +325,15 @@ def integral_images_u32(ctx: Context, grid, alpha_out=None, alpha_t_out=None) ->
     """``grid``: CUDA int32 tensor holding uint32 bit patterns, N*N."""
     import torch
     NN = ctx.N * ctx.N
-    g = _ptr(grid, torch.int32, NN, "grid")
-    _check(load_library().integral_images_u32(ctx.handle, g, _u64(alpha_out, NN, "alpha_out"),
-                                              _u64(alpha_t_out, NN, "alpha_t_out")), "integral_images_u32")
+    g = _ptr(grid, torch.int32, NN, "grid", ctx.device)
+    _check(load_library().integral_images_u32(ctx.handle, g, _u64(alpha_out, NN, "alpha_out", ctx.device),
+                                              _u64(alpha_t_out, NN, "alpha_t_out", ctx.device)), "integral_images_u32")
 
 
 def displacement_field(ctx: Context, disp_out=None) -> None:
     import torch
     _check(load_library().displacement_field(ctx.handle, _ptr(disp_out, torch.float32, 2 * ctx.N * ctx.N,
-                                                              "disp_out")), "displacement_field")
+                                                              "disp_out", ctx.device)), "displacement_field")
 
 
 def lens_field(ctx: Context, density, density_mean: float = 0.0, disp_out=None) -> None:
@@ -319,8 +341,8 @@ def lens_field(ctx: Context, density, density_mean: float = 0.0, disp_out=None) 
     into the context's field (and ``disp_out``, float32 2*N*N, if given)."""
     import torch
     NN = ctx.N * ctx.N
-    _check(load_library().lens_field(ctx.handle, _ptr(density, torch.float32, NN, "density"), float(density_mean),
-                                     _ptr(disp_out, torch.float32, 2 * NN, "disp_out")), "lens_field")
+    _check(load_library().lens_field(ctx.handle, _ptr(density, torch.float32, NN, "density", ctx.device), float(density_mean),
+                                     _ptr(disp_out, torch.float32, 2 * NN, "disp_out", ctx.device)), "lens_field")
 
 
 def contour_segments(ctx: Context, field, level: float, segs_out) -> None:
@@ -329,18 +351,18 @@ def contour_segments(ctx: Context, field, level: float, segs_out) -> None:
     cell, NaN when unused)."""
     import torch
     M = ctx.N - 1
-    _check(load_library().contour_segments(ctx.handle, _ptr(field, torch.float32, ctx.N * ctx.N, "field"),
-                                           float(level), _ptr(segs_out, torch.float32, 8 * M * M, "segs_out")),
+    _check(load_library().contour_segments(ctx.handle, _ptr(field, torch.float32, ctx.N * ctx.N, "field", ctx.device),
+                                           float(level), _ptr(segs_out, torch.float32, 8 * M * M, "segs_out", ctx.device)),
            "contour_segments")
 
 
 def advect_samples(ctx: Context, pos) -> None:
-    pp, n = _pos_args(pos)
+    pp, n = _pos_args(pos, ctx.device)
     _check(load_library().advect_samples(ctx.handle, pp, n), "advect_samples")
 
 
 def regularize(ctx: Context, pos, iters: int, uniformity: bool = False):
-    pp, n = _pos_args(pos)
+    pp, n = _pos_args(pos, ctx.device)
     out = (ctypes.c_double * max(int(iters), 1))() if uniformity else None
     _check(load_library().regularize(ctx.handle, pp, n, int(iters), out), "regularize")
     return list(out)[:iters] if uniformity else None
@@ -363,6 +385,14 @@ def regularize_host(ctx: Context, host_pos, iters: int, uniformity: bool = False
     return list(out)[:iters] if uniformity else None
 
 
+def declutter_counts(ctx: Context, counts_out) -> None:
+    """Copy the context's current count grid (uint32 bit patterns) into the
+    CUDA int32 tensor ``counts_out`` of N*N elements."""
+    import torch
+    _check(load_library().declutter_counts(ctx.handle, _ptr(counts_out, torch.int32, ctx.N * ctx.N, "counts_out",
+                                                            ctx.device)), "declutter_counts")
+
+
 def quality_metrics(ctx: Context) -> dict:
     out = (ctypes.c_double * 3)()
     _check(load_library().quality_metrics(ctx.handle, out), "quality_metrics")
@@ -377,10 +407,10 @@ def declutter_profile_regularize(ctx: Context, pos, iters: int, reps: int = 10, 
     """In-graph device time of regularize(iters) and of each kernel kind in
     it (see the C header).  Returns ``{"step_ms": t, "kernels": {name:
     {"ms": per call, "launches": per call}}}``."""
-    pp, n = _pos_args(pos)
+    pp, n = _pos_args(pos, ctx.device)
     src = None
     if reset_src is not None:
-        src, n2 = _pos_args(reset_src)
+        src, n2 = _pos_args(reset_src, ctx.device)
         if n2 != n:
             raise ValueError("reset_src must have the shape of pos")
     step = ctypes.c_float()
@@ -402,13 +432,17 @@ def integral_images_u32_noalloc(grid, log2_res: int, alpha_out=None, alpha_t_out
     import torch
     NN = 1 << (2 * int(log2_res))
     g = _ptr(grid, torch.int32, NN, "grid")
-    if stream is None:
-        stream = torch.cuda.current_stream(grid.device)
-    sp = getattr(stream, "cuda_stream", stream) or 0
-    _check(load_library().integral_images_u32_noalloc(g, int(log2_res), _u64(alpha_out, NN, "alpha_out"),
-                                                      _u64(alpha_t_out, NN, "alpha_t_out"),
-                                                      ctypes.c_void_p(sp) if sp else None),
-           "integral_images_u32_noalloc")
+    dev = grid.device.index
+    a = _u64(alpha_out, NN, "alpha_out", dev)
+    at = _u64(alpha_t_out, NN, "alpha_t_out", dev)
+    # the C call runs on the calling thread's current device: make it the grid's
+    with torch.cuda.device(grid.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(grid.device)
+        sp = getattr(stream, "cuda_stream", stream) or 0
+        _check(load_library().integral_images_u32_noalloc(g, int(log2_res), a, at,
+                                                          ctypes.c_void_p(sp) if sp else None),
+               "integral_images_u32_noalloc")
 
 
 @dataclass
@@ -507,8 +541,8 @@ def declutter_batch_autotune(batch: Batch, positions, iters: int):
 def regularize_tracers(ctx: Context, pos, tracers, iters: int) -> None:
     """``regularize`` that also moves ``tracers`` (CUDA float32 [m, 2]) by each
     iteration's field without splatting them."""
-    pp, n = _pos_args(pos)
-    tp, nt = _pos_args(tracers)
+    pp, n = _pos_args(pos, ctx.device)
+    tp, nt = _pos_args(tracers, ctx.device)
     _check(load_library().regularize_tracers(ctx.handle, pp, n, tp, nt, int(iters)), "regularize_tracers")
 
 
@@ -545,6 +579,12 @@ def surrogate_create(log2_res: int, levels: int = 4, base_channels: int = 32, ma
 
 def surrogate_set_skip(sg: Surrogate, kappa: float) -> None:
     _check(load_library().surrogate_set_skip(sg.handle, float(kappa)), "surrogate_set_skip")
+
+
+def surrogate_set_tensor_path(sg: Surrogate, path: int) -> None:
+    """``DC_SG_MMA_SYNC`` (default) or ``DC_SG_TCGEN05`` for the forward
+    convolutions of 64..256 output channels."""
+    _check(load_library().surrogate_set_tensor_path(sg.handle, int(path)), "surrogate_set_tensor_path")
 
 
 def surrogate_destroy(sg: Surrogate) -> None:
@@ -634,7 +674,7 @@ def surrogate_train_step(sg: Surrogate, density, scales, target, lr: float, want
 
 
 def surrogate_apply(ctx: Context, sg: Surrogate, pos, target_cv: float, max_plain_iters: int):
-    pp, n = _pos_args(pos)
+    pp, n = _pos_args(pos, ctx.device)
     used = ctypes.c_int32()
     cv = ctypes.c_double()
     _check(load_library().surrogate_apply(ctx.handle, sg.handle, pp, n, float(target_cv), int(max_plain_iters),

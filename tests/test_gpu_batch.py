@@ -30,13 +30,13 @@ def panels():
 
 
 @pytest.mark.parametrize("r,launches", [(0, "1"), (-1, "1"), (-1, "0"), (0, "0")])
-def test_batch_matches_panels_alone(dc, panels, monkeypatch, r, launches):
+def test_batch_matches_panels_alone(dc, panels, r, launches):
     # batched launches per resolution class ("1") or one branch per panel
     # ("0"): bit-identical to every panel regularised on its own
-    monkeypatch.setenv("DECLUTTER_BATCHED_LAUNCHES", launches)
     iters = 3
     pos_b = [torch.from_numpy(z).cuda() for z, _ in panels]
-    batch = dc.declutter_batch_create([k for _, k in panels], [z.shape[0] for z, _ in panels], kernel_r=r)
+    batch = dc.declutter_batch_create([k for _, k in panels], [z.shape[0] for z, _ in panels], kernel_r=r,
+                                      options=dc.DC_OPT_BATCHED_LAUNCHES if launches == "1" else 0)
     try:
         u_b = dc.declutter_batch_regularize(batch, pos_b, iters, uniformity=True)
         # second call replays the cached graph
@@ -117,15 +117,15 @@ def test_batch_autotune_keeps_results(dc, panels):
 
 
 @pytest.mark.parametrize("launches", ["0", "1"])
-def test_batch_with_empty_and_tiny_panels(dc, monkeypatch, launches):
+def test_batch_with_empty_and_tiny_panels(dc, launches):
     # a class with an empty panel, a one-sample panel and a full one
-    monkeypatch.setenv("DECLUTTER_BATCHED_LAUNCHES", launches)
     rng = np.random.default_rng(3)
     zs = [np.zeros((0, 2), np.float32), rng.random((1, 2)).astype(np.float32),
           rng.random((5000, 2)).astype(np.float32), rng.random((700, 2)).astype(np.float32)]
     log2s = [8, 8, 8, 9]
     pos_b = [torch.from_numpy(z).cuda() for z in zs]
-    batch = dc.declutter_batch_create(log2s, [max(1, z.shape[0]) for z in zs])
+    batch = dc.declutter_batch_create(log2s, [max(1, z.shape[0]) for z in zs],
+                                      options=dc.DC_OPT_BATCHED_LAUNCHES if launches == "1" else 0)
     try:
         u_b = dc.declutter_batch_regularize(batch, pos_b, 2, uniformity=True)
         dc.declutter_batch_sync(batch)

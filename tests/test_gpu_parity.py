@@ -413,13 +413,12 @@ def test_reordering_does_not_change_results(dc, r):
     assert out[0][1] == out[1][1]
 
 
-@pytest.mark.parametrize("memory,direct", [("pinned", "1"), ("pinned", "0"), ("pageable", "1")])
-def test_regularize_host_matches_device(dc, monkeypatch, memory, direct):
+@pytest.mark.parametrize("memory,direct", [("pinned", True), ("pinned", False), ("pageable", True)])
+def test_regularize_host_matches_device(dc, memory, direct):
     # pinned host memory is used in place over the host link (or staged with
-    # DECLUTTER_HOST_DIRECT=0); pageable memory is always staged
-    monkeypatch.setenv("DECLUTTER_HOST_DIRECT", direct)
+    # the DC_OPT_STAGE_HOST option); pageable memory is always staged
     z, _ = synth.tiny_mixture()
-    ctx = dc.declutter_create(7, kernel_r=2)
+    ctx = dc.declutter_create(7, kernel_r=2, options=0 if direct else dc.DC_OPT_STAGE_HOST)
     try:
         a = to_dev(z)
         ua = dc.regularize(ctx, a, 3, uniformity=True)
@@ -437,14 +436,13 @@ def test_regularize_host_matches_device(dc, monkeypatch, memory, direct):
 
 
 @pytest.mark.parametrize("fused,fused_smooth", [("1", "1"), ("0", "1"), ("0", "0")])
-def test_profile_counts_launches(dc, monkeypatch, fused, fused_smooth):
-    # the three band phases run as one cooperative launch on small grids,
-    # or as three launches (DECLUTTER_FUSED_BANDS=0); the smoothing runs
-    # inside the aggregate pass unless DECLUTTER_FUSED_SMOOTH=0
-    monkeypatch.setenv("DECLUTTER_FUSED_BANDS", fused)
-    monkeypatch.setenv("DECLUTTER_FUSED_SMOOTH", fused_smooth)
+def test_profile_counts_launches(dc, fused, fused_smooth):
+    # the three band phases run as one cooperative launch on small grids
+    # (DC_OPT_FUSED_BANDS) or as three launches; the smoothing runs inside
+    # the aggregate pass unless DC_OPT_SEPARATE_SMOOTH
+    opts = (dc.DC_OPT_FUSED_BANDS if fused == "1" else 0) | (dc.DC_OPT_SEPARATE_SMOOTH if fused_smooth == "0" else 0)
     z, _ = synth.tiny_mixture()
-    ctx = dc.declutter_create(7, kernel_r=2)
+    ctx = dc.declutter_create(7, kernel_r=2, options=opts)
     try:
         pos = to_dev(z)
         src = to_dev(z)
@@ -471,7 +469,7 @@ def test_profile_counts_launches(dc, monkeypatch, fused, fused_smooth):
 @pytest.mark.parametrize("log2,r,band_rows,fused", [(7, 2, 0, 1), (8, 2, 0, 1), (8, 5, 3, 1), (9, 4, 0, 1),
                                                      (9, 4, 5, 1), (9, 12, 7, 1), (10, 8, 0, 1), (10, 3, 16, 1),
                                                      (7, 40, 0, 1), (10, 16, 0, 1), (10, 40, 0, 0)])
-def test_fused_smoothing_matches_separate_launches(dc, monkeypatch, log2, r, band_rows, fused):
+def test_fused_smoothing_matches_separate_launches(dc, log2, r, band_rows, fused):
     # bitwise: smoothing inside the aggregate pass (windows of 4 or 8 rows,
     # ragged last bands, radii up to the shared-memory limit) against the
     # smoothing kernel plus the aggregate pass; r = 40 at 1024^2 does not fit
@@ -480,8 +478,8 @@ def test_fused_smoothing_matches_separate_launches(dc, monkeypatch, log2, r, ban
     z = rng.beta(2.0, 5.0, size=(60_000, 2)).astype(np.float32)
     outs, us = [], []
     for fs in ("1", "0"):
-        monkeypatch.setenv("DECLUTTER_FUSED_SMOOTH", fs)
-        ctx = dc.declutter_create(log2, kernel_r=r, band_rows=band_rows)
+        ctx = dc.declutter_create(log2, kernel_r=r, band_rows=band_rows,
+                                  options=0 if fs == "1" else dc.DC_OPT_SEPARATE_SMOOTH)
         try:
             pos = to_dev(z)
             us.append(dc.regularize(ctx, pos, 3, uniformity=True))
@@ -498,13 +496,12 @@ def test_fused_smoothing_matches_separate_launches(dc, monkeypatch, log2, r, ban
 
 
 @pytest.mark.parametrize("r", [0, 2])
-def test_fused_and_separate_band_launches_agree(dc, monkeypatch, r):
+def test_fused_and_separate_band_launches_agree(dc, r):
     # bitwise: the fused launch runs the same code as the three launches
     z, _ = synth.tiny_mixture()
     outs = []
     for fused in ("1", "0"):
-        monkeypatch.setenv("DECLUTTER_FUSED_BANDS", fused)
-        ctx = dc.declutter_create(9, kernel_r=r)
+        ctx = dc.declutter_create(9, kernel_r=r, options=dc.DC_OPT_FUSED_BANDS if fused == "1" else 0)
         try:
             pos = to_dev(z)
             dc.regularize(ctx, pos, 4)
@@ -513,6 +510,60 @@ def test_fused_and_separate_band_launches_agree(dc, monkeypatch, r):
         finally:
             dc.declutter_destroy(ctx)
     assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("r", [0, 2])
+def test_grid_barrier_timeout_is_reported_and_recovers(dc, r):
+    # The one wait between CTAs (the grid barrier of the cooperative band
+    # launch) is bounded.  A test option makes it wait for one CTA more than
+    # the grid holds, so that every wait runs to its limit (2 ms here): the
+    # kernel ends, the status says DC_ERR_TIMEOUT, and the context stays
+    # usable.  A fresh context with the default limit then gives the
+    # oracle's result and the bits of the three separate launches.
+    z, _ = synth.tiny_mixture()
+    k = 9
+    N = 1 << k
+    bad = dc.declutter_create(k, kernel_r=r, options=dc.DC_OPT_FUSED_BANDS | dc.DC_OPT_TEST_UNREACHED_BARRIER,
+                              wait_limit_us=2000)
+    try:
+        pos = to_dev(z)
+        dc.regularize(bad, pos, 2)
+        with pytest.raises(dc.DeclutterError) as ei:
+            dc.declutter_sync(bad)
+        assert ei.value.status == 5
+        dc.declutter_sync(bad)  # cleared: the context is usable again
+        assert declutter_info_ok(dc, bad)
+    finally:
+        dc.declutter_destroy(bad)
+    p = oracle.Params(log2_res=k, kernel_r=r)
+    ref = oracle.iterate(z, p)
+    outs = []
+    for opts in (dc.DC_OPT_FUSED_BANDS, 0):
+        ctx = dc.declutter_create(k, kernel_r=r, options=opts)
+        try:
+            pos = to_dev(z)
+            dc.regularize(ctx, pos, 1)
+            dc.declutter_sync(ctx)
+            outs.append(pos.cpu())
+            if opts:
+                prof = dc.declutter_profile_regularize(ctx, to_dev(z), 1, reps=1)
+                assert prof["kernels"]["band_fused"]["launches"] == 1
+        finally:
+            dc.declutter_destroy(ctx)
+    assert torch.equal(outs[0], outs[1])
+    err = float(np.max(np.abs(outs[0].numpy().astype(np.float64) - ref))) * N
+    assert err <= pos_tol_px(N), err
+
+
+def declutter_info_ok(dc, ctx):
+    info = dc.declutter_get_info(ctx)
+    return info.N == ctx.N
+
+
+def test_options_and_limits_are_validated(dc):
+    for kw in ({"options": 1 << 20}, {"wait_limit_us": -1}, {"wait_limit_us": 10_000_001}):
+        with pytest.raises(dc.DeclutterError):
+            dc.declutter_create(7, kernel_r=2, **kw)
 
 
 def test_bad_arguments_are_rejected(dc):
@@ -584,6 +635,90 @@ def test_largest_grid_8192_one_iteration(dc, r):
 
 
 # --------------------------------------------------------------------------
+# The splat fused into the advection inside regularize() (Sec. 4.3 step 1 of
+# every iteration after the first), compared with the oracle's splat
+# --------------------------------------------------------------------------
+
+FUSED_CASES = {
+    # name: (generator, log2 N, r)
+    "gmm20_512": (lambda: synth.gmm20()[0], 9, 4),
+    "student_t_2048": (lambda: synth.student_t_clusters()[0], 11, 16),
+}
+
+
+@pytest.mark.parametrize("case,keep_order,k", [("gmm20_512", False, 2), ("gmm20_512", False, 3),
+                                               ("gmm20_512", True, 2), ("student_t_2048", False, 2),
+                                               ("student_t_2048", False, 3)])
+def test_fused_splat_inside_regularize_matches_oracle(dc, case, keep_order, k):
+    # Inside regularize(k) the advection of iteration m splats the moved
+    # samples into the count grid of iteration m + 1 (run-aggregated atomics
+    # on pixel-ordered samples up to 1024^2, __match_any_sync otherwise and
+    # in the caller's order).  Three checks:
+    #  (1) regularize(k) without metrics leaves the input grid of its last
+    #      iteration, i.e. the in-graph splat of the positions after k - 1
+    #      iterations (regularize(k - 1) on a copy gives those bits):
+    #      bit-exact against oracle.splat;
+    #  (2) regularize(k) with metrics also splats the final positions:
+    #      bit-exact against oracle.splat of the returned positions;
+    #  (3) the last in-graph iteration, which ran on those counts, against
+    #      oracle.iterate of the positions it started from (teacher-forced).
+    gen, log2, r = FUSED_CASES[case]
+    z = gen()
+    N = 1 << log2
+    p = oracle.Params(log2_res=log2, kernel_r=r)
+    ctx = dc.declutter_create(log2, kernel_r=r, keep_order=keep_order)
+    try:
+        prev = to_dev(z)
+        dc.regularize(ctx, prev, k - 1)
+        dc.declutter_sync(ctx)
+        prev_np = prev.cpu().numpy()
+        del prev
+        counts = torch.empty(N * N, dtype=torch.int32, device=DEV)
+        pos = to_dev(z)
+        dc.regularize(ctx, pos, k)
+        dc.declutter_counts(ctx, counts)
+        dc.declutter_sync(ctx)
+        c_in = u32(counts, N).astype(np.uint64)
+        assert np.array_equal(c_in, oracle.splat(prev_np, log2)), "in-graph splat of the input of iteration k"
+        got = pos.cpu().numpy()
+        ref = oracle.iterate(prev_np, p)
+        perr = float(np.max(np.abs(got.astype(np.float64) - ref))) * N
+        assert perr <= pos_tol_px(N), perr
+        pos.copy_(to_dev(z))
+        u = dc.regularize(ctx, pos, k, uniformity=True)
+        dc.declutter_counts(ctx, counts)
+        dc.declutter_sync(ctx)
+        fin = pos.cpu().numpy()
+        assert np.array_equal(fin, got), "metrics must not change the positions"
+        c_out = u32(counts, N).astype(np.uint64)
+        ref_c = oracle.splat(fin, log2)
+        assert np.array_equal(c_out, ref_c), "in-graph splat of the final positions"
+        assert abs(u[-1] - oracle.quality(ref_c)["bin_std"]) <= 1e-9 * max(1.0, u[-1])
+        print(f"{case} keep_order={keep_order} k={k}: counts bit-exact, last iteration {perr:.3e} px")
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+def test_declutter_counts_state_and_arguments(dc):
+    ctx = dc.declutter_create(6, kernel_r=0)
+    try:
+        out = torch.empty(64 * 64, dtype=torch.int32, device=DEV)
+        with pytest.raises(dc.DeclutterError):
+            dc.declutter_counts(ctx, out)         # before any splat
+        z, _ = synth.tiny_mixture(3000, seed=9)
+        dc.splat_density(ctx, to_dev(z))
+        dc.declutter_counts(ctx, out)
+        dc.declutter_sync(ctx)
+        assert np.array_equal(u32(out, 64).astype(np.uint64), oracle.splat(z, 6))
+        lib = dc.load_library()
+        import ctypes
+        assert lib.declutter_counts(ctx.handle, None) == 1
+        assert lib.declutter_counts(ctx.handle, ctypes.c_void_p(out.data_ptr() + 2)) == 1
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
 # Virtual lens (end of Sec. 3.2): eq. (map) without the defect
 # --------------------------------------------------------------------------
 
@@ -598,10 +733,15 @@ def painted_density(N, seed):
     return d
 
 
-def lens_tol_px(N):
-    # t(x, y; d) is O(1) in domain units: a few float32 roundings of 1,
-    # i.e. of 2^-24 N pixel, on top of the displacement bound (measured:
-    # 9e-5 px at 512^2, 4.7e-4 px at 2048^2, about 4 such roundings)
+def lens_tol_px(N, hint="zero"):
+    # With the density's mean as the hint the pixel position cancels in
+    # exact integers before any rounding (t - x from excess sums), so the
+    # displacement bound holds.  With hint 0 the sums are not centred and
+    # t(x, y; d) is formed as an O(1) float32 value before the position is
+    # taken off: a few float32 roundings of 1, i.e. of 2^-24 N pixel, on
+    # top of the displacement bound.
+    if hint == "mean":
+        return DISP_TOL_PX
     return DISP_TOL_PX + 6 * N * 2.0 ** -24
 
 
@@ -628,10 +768,28 @@ def test_lens_field_matches_oracle(dc, k, r, pixel_center, hint):
         dc.declutter_destroy(ctx)
     err = float(np.max(np.abs(out.cpu().numpy().reshape(N, N, 2).astype(np.float64) - ref))) * N
     print(f"lens {N}^2 pc={pixel_center} hint={hint}: max error {err:.2e} px")
-    assert err <= lens_tol_px(N), err
+    assert err <= lens_tol_px(N, hint), err
     want = z.astype(np.float64) + ref[jj.ravel(), ii.ravel()]
     perr = float(np.max(np.abs(pos.cpu().numpy().astype(np.float64) - want))) * N
-    assert perr <= lens_tol_px(N) + N * float(np.spacing(np.float32(1.0))), perr
+    assert perr <= lens_tol_px(N, hint) + N * float(np.spacing(np.float32(1.0))), perr
+
+
+@pytest.mark.parametrize("k", [7, 11])
+def test_lens_field_without_mass_writes_zero_and_reports(dc, k):
+    # eq. (map) divides by the total mass: for an all-zero density the lens
+    # writes a zero field and the status reports an invalid argument
+    N = 1 << k
+    ctx = dc.declutter_create(k, kernel_r=2)
+    try:
+        out = torch.full((2 * N * N,), 7.0, dtype=torch.float32, device=DEV)
+        dc.lens_field(ctx, torch.zeros(N * N, dtype=torch.float32, device=DEV), 0.0, out)
+        with pytest.raises(dc.DeclutterError) as ei:
+            dc.declutter_sync(ctx)
+        assert ei.value.status == 1
+        assert bool(torch.all(out == 0))
+        dc.declutter_sync(ctx)  # the status was cleared
+    finally:
+        dc.declutter_destroy(ctx)
 
 
 def test_lens_field_rejects_bad_arguments(dc):

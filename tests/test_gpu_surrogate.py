@@ -55,8 +55,7 @@ def split_params(w, b, levels, c0, c_in=1):
     (2, 8, 4, 2, 3, 1.7, "0"), (4, 32, 6, 1, 3, 3.0, "0"),
     # the tcgen05 path of the forward convolutions (64..256 output channels)
     (4, 32, 7, 1, 3, 3.0, "1"), (3, 64, 7, 2, 1, 0.0, "1")])
-def test_forward_and_gradients_match_oracle(dc, monkeypatch, levels, c0, log2, batch, c_in, kappa, tc):
-    monkeypatch.setenv("DECLUTTER_SG_TCGEN05", tc)
+def test_forward_and_gradients_match_oracle(dc, levels, c0, log2, batch, c_in, kappa, tc):
     H = 1 << log2
     rng = np.random.default_rng(levels * 10 + c0 + c_in)
     P = S.init_params(levels, c0, seed=levels + c0, c_in=c_in)
@@ -68,6 +67,7 @@ def test_forward_and_gradients_match_oracle(dc, monkeypatch, levels, c0, log2, b
     t = rng.normal(size=(batch, H, H, 2))
     sg = dc.surrogate_create(log2, levels, c0, max_batch=batch, seed=0, in_channels=c_in)
     try:
+        dc.surrogate_set_tensor_path(sg, dc.DC_SG_TCGEN05 if tc == "1" else dc.DC_SG_MMA_SYNC)
         dc.surrogate_set_skip(sg, kappa)
         w, b = flat_params(P, levels, c0, c_in)
         dc.surrogate_set_params(sg, w, b)
