@@ -255,6 +255,102 @@ dc_status regularize_tracers(dc_ctx *ctx, float *pos_xy, int64_t n, float *trace
 dc_status regularize_host(dc_ctx *ctx, float *host_pos_xy, int64_t n, int32_t iters,
                           double *uniformity_out);
 
+/* Sec. 4.3 step 4: iterations of regularize() until a stopping criterion
+ * holds, decided on the GPU after every iteration, in one CUDA graph launch
+ * (captured on the first call for this (pos_xy, n, max_iters) and replayed
+ * afterwards; the criteria are read at launch time).  After iteration k the
+ * run stops when
+ *   - k = max_iters (1..1024), or
+ *   - target_cv > 0 and the Sec. 6.2 bin std over the mean bin count of the
+ *     moved samples is <= target_cv (a regularity measure), or
+ *   - min_move_px > 0 and the largest distance a sample moved in iteration k
+ *     is <= min_move_px pixels (the impact of the last iteration), or
+ *   - max_ms > 0 and the device time since the graph started is >= max_ms.
+ * Iterations 2..max_iters sit in conditional graph nodes whose condition
+ * the previous iteration's check sets, so at most max_iters iterations run
+ * whatever the data.  The positions are those of regularize() with the
+ * same number of iterations, bit for bit.
+ *   iters_out  : host int32, iterations done (or NULL).
+ *   cv_out, move_px_out: host double[max_iters] (or NULL): the measure and
+ *                the largest move of every iteration done.
+ * Synchronises.  Errors: DC_ERR_INVALID_ARG for n = 0, max_iters outside
+ * 1..1024 or a negative or non-finite criterion. */
+dc_status regularize_adaptive(dc_ctx *ctx, float *pos_xy, int64_t n, int32_t max_iters, double target_cv,
+                              double min_move_px, double max_ms, int32_t *iters_out, double *cv_out,
+                              double *move_px_out);
+
+/* Sec. 1: the continuous transition between the original and the
+ * regularised scatterplot, as a per-sample blend of the two positions:
+ * out = (1 - s) from + s to, rounded to float32 after each operation in
+ * that order, so s = 0 gives from and s = 1 gives to exactly.
+ *   from_xy, to_xy, out_xy: device float[2n] (out may alias either input).
+ *   s: 0 <= s <= 1.
+ * Asynchronous.  Errors: DC_ERR_INVALID_ARG for s outside [0, 1], a null or
+ * misaligned pointer. */
+dc_status transition_positions(dc_ctx *ctx, const float *from_xy, const float *to_xy, int64_t n, float s,
+                               float *out_xy);
+
+/* Sec. 6.2: how well the regularised layout keeps the original's local
+ * structure, by the two measures the paper reports: trustworthiness
+ * (Venna and Kaski) and orthogonal ordering (Misue et al.).  Positions are
+ * taken on the lattice X = rint(float32(x * 65535)) (x clamped to [0, 1]);
+ * distances are squared lattice distances, ties broken by sample index.
+ * Over the query samples Q (m of them):
+ *   out[0] = T = 1 - 2 / (m k (2n - 3k - 1)) * sum_{i in Q} sum_{j in U_k(i)} (r(i, j) - k),
+ *            U_k(i) = the k nearest neighbours of i in reg that are not
+ *            among its k nearest in orig, r(i, j) = the rank of j by
+ *            distance from i in orig (nearest = 1);
+ *   out[1] = O = 1 - (sum_{i in Q} #{j : sign(X_i - X_j) or sign(Y_i - Y_j)
+ *            differs between orig and reg}) / (m (n - 1)).
+ * With every sample a query these are the exact measures; a random subset
+ * estimates them at O(m n) cost.
+ *   orig_xy, reg_xy: device float[2n], n < 2^31.
+ *   queries: device uint32[n_queries] sample indices, or NULL for
+ *            0 .. n_queries - 1 (n_queries <= n).
+ *   k: 1..32, k < n / 2.
+ *   out: host double[2]; terms_out: host int64[2 n_queries] or NULL, the
+ *        per-query integer sums (T's inner sum, O's count).
+ * Synchronises.  Errors: DC_ERR_INVALID_ARG for bad sizes or pointers,
+ * DC_ERR_RANGE for a query index outside [0, n). */
+dc_status layout_metrics(dc_ctx *ctx, const float *orig_xy, const float *reg_xy, int64_t n,
+                         const uint32_t *queries, int32_t n_queries, int32_t k, double *out, int64_t *terms_out);
+
+/* Sec. 5, the density background texture: a texture given at the N x N
+ * pixel nodes (e.g. d_r from splat_density), drawn on the mesh of those
+ * nodes after they moved to nodes_xy (e.g. the tracers of
+ * regularize_tracers started at the pixel positions), into an M x M raster,
+ * M = 2^out_log2.  Every cell (i, j) of the node mesh is split into the
+ * triangles 2c = (i, j), (i+1, j), (i+1, j+1) and 2c + 1 = (i, j),
+ * (i+1, j+1), (i, j+1), c = j (N - 1) + i.  Output pixel (p, q) has its
+ * centre at ((p + 1/2) / M, (q + 1/2) / M); it is covered by the triangles
+ * whose interior holds the centre, or whose edge holds it under a fill rule
+ * that gives points on a shared edge or vertex to exactly one of the
+ * triangles (vertices snapped to 1/256 pixel; exact integer tests); where
+ * triangles overlap, the lowest index wins.  A covered pixel takes the
+ * texture at the source point with the same barycentric coordinates in the
+ * undeformed triangle (bilinear lookup between nodes); uncovered pixels are
+ * 0.  DC_WARP_MASS multiplies by the undeformed over the deformed triangle
+ * area, the push-forward density, whose sum is the texture's mass.
+ *   nodes_xy: device float[2 N N] (domain units; clamped to [-1, 2]).
+ *   texture : device float[N N], row-major [j][i].
+ *   out     : device float[M M]; tri_out: device int32[M M] receiving the
+ *             winning triangle (-1: none), or NULL (context scratch).
+ * Asynchronous.  Errors: DC_ERR_INVALID_ARG for null or misaligned pointers,
+ * out_log2 outside 4..13 or an unknown mode. */
+enum { DC_WARP_VALUE = 0, DC_WARP_MASS = 1 };
+dc_status warp_texture(dc_ctx *ctx, const float *nodes_xy, const float *texture, int32_t out_log2, int32_t mode,
+                       float *out, int32_t *tri_out);
+
+/* Sec. 5 transfer function: rgba_out[k] = lut[i] with
+ * i = rint((values[k] - lo) * s), s = 255 / (hi - lo), clamped to 0..255
+ * (float32, each operation rounded in that order; NaN -> 0).
+ *   values: device float[count]; lut: device uint32[256] (RGBA8);
+ *   rgba_out: device uint32[count].
+ * Asynchronous.  Errors: DC_ERR_INVALID_ARG for null or misaligned pointers
+ * or unless lo < hi, both finite. */
+dc_status transfer_function(dc_ctx *ctx, const float *values, int64_t count, float lo, float hi,
+                            const uint32_t *lut, uint32_t *rgba_out);
+
 /* The count grid c(i, j) of Sec. 4.1 (Sec. 4.3 step 1) that the context
  * holds: that of the last splat_density() call or, after regularize(),
  * that of the last splat the iterations performed.  Inside regularize()

@@ -13,6 +13,7 @@ it, and it shares no code with the CUDA library).
 * :func:`regularize_until`  -- Sec. 4.3 step 4, the stopping criteria
 * :func:`warp_texture`      -- Sec. 5, the density background texture
   deformed by the mesh mapping, and its push-forward (mass) variant
+* :func:`transfer`          -- Sec. 5, the transfer function to colours
 
 Plain numpy; slow on purpose.  Every function is pinned in
 ``tests/test_oracle_layout.py``.
@@ -178,8 +179,10 @@ def _tri_vertices(N: int):
 
 
 def _fixed(xy: np.ndarray, log2M: int) -> np.ndarray:
-    """Fixed-point vertex coordinates: rint(float32(x * 2^(log2M + SUB)))."""
+    """Fixed-point vertex coordinates: rint(float32(x * 2^(log2M + SUB))) of
+    x clamped to [-1, 2] (NaN -> -1); nodes are expected in [0, 1]."""
     z = np.asarray(xy, dtype=np.float32)
+    z = np.clip(np.where(np.isnan(z), np.float32(-1.0), z), np.float32(-1.0), np.float32(2.0))
     return np.rint(z * np.float32(2.0 ** (log2M + SUB))).astype(np.int64)
 
 
@@ -277,6 +280,17 @@ def warp_texture(nodes_xy: np.ndarray, texture: np.ndarray, log2M: int, mass: bo
                 v *= cross0 / abs(area)
             out[q, p] = v
     return out, cov
+
+
+def transfer(values: np.ndarray, lo: float, hi: float, lut: np.ndarray) -> np.ndarray:
+    """Transfer function of the background texture (Sec. 5): lut[i] with
+    i = rint((v - lo) * (255 / (hi - lo))) clamped to 0..255, in float32
+    with each operation rounded in that order (NaN -> 0)."""
+    v = np.asarray(values, dtype=np.float32)
+    scale = np.float32(255.0) / (np.float32(hi) - np.float32(lo))
+    x = ((v - np.float32(lo)).astype(np.float32) * scale).astype(np.float32)
+    i = np.clip(np.rint(np.where(np.isnan(x), np.float32(0.0), x)), 0, 255).astype(np.int64)
+    return np.asarray(lut, dtype=np.uint32)[i]
 
 
 def identity_nodes(N: int, pixel_center: bool = False) -> np.ndarray:

@@ -140,17 +140,85 @@ cudaError_t enqueue_inims(dc_ctx *c, cudaStream_t s, const BandArgs &a, int mode
     return e;
 }
 
-// The iteration of Sec. 4.3, `iters` times.  Counts alternate between two
-// grids: the advection of iteration it also splats the moved samples into
-// the other grid, which the smoothing (float mode) or the aggregate kernel
-// (exact mode) of iteration it has zeroed.  Only the first iteration has its
-// own memset and splat.  With metrics, the quality of the counts after
-// iteration it goes to accumulator slot it.
+// Pieces of the iteration sequence of Sec. 4.3.  Counts alternate between
+// two grids: the advection of iteration it also splats the moved samples
+// into the other grid, which the smoothing (float mode) or the aggregate
+// kernel (exact mode) of iteration it has zeroed.  Only the first iteration
+// has its own memset and splat.
+
+// The first splat, in the caller's order, into grid 0; with the reordering,
+// its counts key the counting sort of the samples into c->spos.
+cudaError_t enqueue_first_splat(dc_ctx *c, cudaStream_t s, const float *pos, int64_t n, bool reorder, Recorder &rec)
+{
+    uint32_t *cb[2] = {c->counts_buf[0], c->counts_buf[1]};
+    cudaError_t e = cudaMemsetAsync(cb[0], 0, sizeof(uint32_t) * (size_t)c->g.N * c->g.N, s);
+    if (e != cudaSuccess) return e;
+    rec.count(K_SPLAT);
+    const float2 *p2 = reinterpret_cast<const float2 *>(pos);
+    e = reorder ? launch_splat_rank(s, p2, n, cb[0], c->g.log2N, c->rank) : launch_splat(s, p2, n, cb[0], c->g.log2N);
+    // a profiling duplicate goes to the other grid, which is zeroed before
+    // its next use, so that these counts stay those of pos
+    if (e == cudaSuccess && rec.times(K_SPLAT) > 1) e = launch_splat(s, p2, n, cb[1], c->g.log2N);
+    if (e != cudaSuccess || !reorder) return e;
+    rec.count(K_REORDER);
+    for (int t = 0; t < rec.times(K_REORDER) && e == cudaSuccess; ++t) {
+        e = launch_reorder_scan(s, cb[0], c->g.log2N, c->partials, c->cursor);
+        if (e == cudaSuccess)
+            e = launch_reorder_scatter(s, p2, n, c->g.log2N, c->cursor, c->rank, c->spos, c->inv, c->status);
+    }
+    return e;
+}
+
+// Iteration it on count grid `cur`: smoothing (float mode), integral images
+// and displacement, advection of the samples ipos (pixel order when they
+// are not the caller's pos).  need_next: the moved samples are splatted into
+// grid cur ^ 1; qacc (or null): the Sec. 6.2 accumulators of that grid;
+// dmax (or null): the largest squared move of the iteration.
+cudaError_t enqueue_iteration(dc_ctx *c, cudaStream_t s, const float *pos, float *ipos, int64_t n, int cur,
+                              bool need_next, unsigned long long *qacc, unsigned *dmax, Recorder &rec,
+                              float *tracers = nullptr, int64_t n_tracers = 0)
+{
+    cudaError_t e = cudaSuccess;
+    uint32_t *cb[2] = {c->counts_buf[0], c->counts_buf[1]};
+    const int nxt = cur ^ 1;
+    const bool smooth_fused = c->mode == MODE_FLOAT && c->smooth_agg;
+    if (c->mode == MODE_FLOAT && !smooth_fused) {
+        rec.count(K_SMOOTH);
+        for (int t = 0; t < rec.times(K_SMOOTH) && e == cudaSuccess; ++t)
+            e = launch_smooth(s, cb[cur], c->dens, c->g.log2N, c->w, need_next ? cb[nxt] : nullptr);
+        if (e != cudaSuccess) return e;
+    }
+    const void *src = c->mode == MODE_FLOAT ? (const void *)c->dens : (const void *)cb[cur];
+    BandArgs a = band_args(c, src, c->mode, n);
+    a.disp = c->disp;
+    a.zero_out = (c->mode != MODE_FLOAT && need_next) ? cb[nxt] : nullptr;
+    e = smooth_fused ? enqueue_inims(c, s, a, c->mode, rec, cb[cur], need_next ? cb[nxt] : nullptr)
+                     : enqueue_inims(c, s, a, c->mode, rec);
+    if (e != cudaSuccess) return e;
+    rec.count(K_ADVECT);
+    for (int t = 0; t < rec.times(K_ADVECT) && e == cudaSuccess; ++t)
+        e = launch_advect(s, reinterpret_cast<float2 *>(ipos), n, c->disp, c->g.log2N, c->p.pixel_center,
+                          c->p.clamp_positions, need_next ? cb[nxt] : nullptr, ipos != pos, dmax);
+    if (e != cudaSuccess) return e;
+    if (n_tracers > 0) {
+        // massless tracers: moved by the same field, not splatted
+        e = launch_advect(s, reinterpret_cast<float2 *>(tracers), n_tracers, c->disp, c->g.log2N, c->p.pixel_center,
+                          c->p.clamp_positions, nullptr);
+        if (e != cudaSuccess) return e;
+    }
+    if (qacc) {
+        rec.count(K_QUALITY);
+        e = launch_quality(s, cb[nxt], c->g.log2N, qacc);
+    }
+    return e;
+}
+
+// The iteration of Sec. 4.3, `iters` times.  With metrics, the quality of
+// the counts after iteration it goes to accumulator slot it.
 cudaError_t enqueue_iterations(dc_ctx *c, cudaStream_t s, float *pos, int64_t n, int iters, int metrics,
                                Recorder &rec, float *tracers = nullptr, int64_t n_tracers = 0)
 {
     cudaError_t e = cudaSuccess;
-    uint32_t *cb[2] = {c->counts_buf[0], c->counts_buf[1]};
     const bool reorder = c->p.keep_order == 0 && n > 0;
     float *ipos = reorder ? reinterpret_cast<float *>(c->spos) : pos;  // samples the iterations move
     if (metrics) {
@@ -159,62 +227,12 @@ cudaError_t enqueue_iterations(dc_ctx *c, cudaStream_t s, float *pos, int64_t n,
     }
     int cur = 0;
     for (int it = 0; it < iters; ++it) {
-        const int nxt = cur ^ 1;
         const bool need_next = (it + 1 < iters) || metrics;
-        if (it == 0) {
-            // first splat in the caller's order; its counts key the reordering
-            e = cudaMemsetAsync(cb[cur], 0, sizeof(uint32_t) * (size_t)c->g.N * c->g.N, s);
-            if (e != cudaSuccess) return e;
-            rec.count(K_SPLAT);
-            const float2 *p2 = reinterpret_cast<const float2 *>(pos);
-            e = reorder ? launch_splat_rank(s, p2, n, cb[cur], c->g.log2N, c->rank)
-                        : launch_splat(s, p2, n, cb[cur], c->g.log2N);
-            // a profiling duplicate goes to the other grid, which is zeroed
-            // before its next use, so that these counts stay those of pos
-            if (e == cudaSuccess && rec.times(K_SPLAT) > 1) e = launch_splat(s, p2, n, cb[nxt], c->g.log2N);
-            if (e != cudaSuccess) return e;
-            if (reorder) {
-                rec.count(K_REORDER);
-                for (int t = 0; t < rec.times(K_REORDER) && e == cudaSuccess; ++t) {
-                    e = launch_reorder_scan(s, cb[cur], c->g.log2N, c->partials, c->cursor);
-                    if (e == cudaSuccess)
-                        e = launch_reorder_scatter(s, p2, n, c->g.log2N, c->cursor, c->rank, c->spos, c->inv,
-                                                   c->status);
-                }
-                if (e != cudaSuccess) return e;
-            }
-        }
-        const bool smooth_fused = c->mode == MODE_FLOAT && c->smooth_agg;
-        if (c->mode == MODE_FLOAT && !smooth_fused) {
-            rec.count(K_SMOOTH);
-            for (int t = 0; t < rec.times(K_SMOOTH) && e == cudaSuccess; ++t)
-                e = launch_smooth(s, cb[cur], c->dens, c->g.log2N, c->w, need_next ? cb[nxt] : nullptr);
-            if (e != cudaSuccess) return e;
-        }
-        const void *src = c->mode == MODE_FLOAT ? (const void *)c->dens : (const void *)cb[cur];
-        BandArgs a = band_args(c, src, c->mode, n);
-        a.disp = c->disp;
-        a.zero_out = (c->mode != MODE_FLOAT && need_next) ? cb[nxt] : nullptr;
-        e = smooth_fused ? enqueue_inims(c, s, a, c->mode, rec, cb[cur], need_next ? cb[nxt] : nullptr)
-                         : enqueue_inims(c, s, a, c->mode, rec);
+        if (it == 0 && (e = enqueue_first_splat(c, s, pos, n, reorder, rec)) != cudaSuccess) return e;
+        e = enqueue_iteration(c, s, pos, ipos, n, cur, need_next, metrics ? c->qacc + 3 * it : nullptr, nullptr, rec,
+                              tracers, n_tracers);
         if (e != cudaSuccess) return e;
-        rec.count(K_ADVECT);
-        for (int t = 0; t < rec.times(K_ADVECT) && e == cudaSuccess; ++t)
-            e = launch_advect(s, reinterpret_cast<float2 *>(ipos), n, c->disp, c->g.log2N, c->p.pixel_center,
-                              c->p.clamp_positions, need_next ? cb[nxt] : nullptr, ipos != pos);
-        if (e != cudaSuccess) return e;
-        if (n_tracers > 0) {
-            // massless tracers: moved by the same field, not splatted
-            e = launch_advect(s, reinterpret_cast<float2 *>(tracers), n_tracers, c->disp, c->g.log2N,
-                              c->p.pixel_center, c->p.clamp_positions, nullptr);
-            if (e != cudaSuccess) return e;
-        }
-        if (metrics) {
-            rec.count(K_QUALITY);
-            e = launch_quality(s, cb[nxt], c->g.log2N, c->qacc + 3 * it);
-            if (e != cudaSuccess) return e;
-        }
-        if (need_next) cur = nxt;
+        if (need_next) cur ^= 1;
     }
     if (reorder && iters > 0) {
         for (int t = 0; t < rec.times(K_REORDER) && e == cudaSuccess; ++t)
@@ -266,6 +284,108 @@ dc_status capture_iterations(dc_ctx *c, float *pos, int64_t n, int iters, int me
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(DC_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
     if (rec_out) *rec_out = rec;
+    return DC_OK;
+}
+
+// regularize_adaptive's device state for up to `cap` iterations (AdaptState,
+// cv[cap], move_px[cap], dmax[cap]); graphs that point at an old buffer are
+// dropped when it moves.
+constexpr size_t kAdaptHead = 64;
+size_t adapt_bytes(int cap) { return kAdaptHead + (size_t)cap * (2 * sizeof(double) + sizeof(unsigned)); }
+double *adapt_cv(const dc_ctx *c) { return reinterpret_cast<double *>(static_cast<char *>(c->adapt) + kAdaptHead); }
+double *adapt_move(const dc_ctx *c) { return adapt_cv(c) + c->adapt_cap; }
+unsigned *adapt_dmax(const dc_ctx *c) { return reinterpret_cast<unsigned *>(adapt_move(c) + c->adapt_cap); }
+
+dc_status ensure_adapt(dc_ctx *c, int cap)
+{
+    if (cap <= c->adapt_cap) return DC_OK;
+    DC_CUDA(cudaStreamSynchronize(c->stream));
+    for (auto it = c->graphs.begin(); it != c->graphs.end();) {
+        if (it->adaptive) {
+            cudaGraphExecDestroy(it->exec);
+            it = c->graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    cudaFree(c->adapt);
+    c->adapt = nullptr;
+    c->adapt_cap = 0;
+    if (cudaMalloc(&c->adapt, adapt_bytes(cap)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DC_ERR_OOM, "adaptive state for %d iterations", cap);
+    }
+    c->adapt_cap = cap;
+    return DC_OK;
+}
+
+// regularize_adaptive's graph: the first iteration, then iterations 1 ..
+// max_iters - 1 each inside an IF conditional node whose condition the
+// previous iteration's check kernel sets (default 0 at every launch), so the
+// number of iterations is bounded by construction; the way back to the
+// caller's order runs after them in any case.
+dc_status capture_adaptive(dc_ctx *c, float *pos, int64_t n, int max_iters, cudaGraphExec_t *out)
+{
+    const bool reorder = c->p.keep_order == 0 && n > 0;
+    float *ipos = reorder ? reinterpret_cast<float *>(c->spos) : pos;
+    AdaptState *st = static_cast<AdaptState *>(c->adapt);
+    double *cv = adapt_cv(c), *mv = adapt_move(c);
+    unsigned *dmax = adapt_dmax(c);
+    Recorder rec;
+    DC_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t s = c->cap_stream;
+    cudaGraph_t cg = nullptr;
+    cudaStreamCaptureStatus cs;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr);
+    std::vector<cudaGraphConditionalHandle> h((size_t)max_iters + 1, 0);
+    for (int it = 1; it < max_iters && e == cudaSuccess; ++it)
+        e = cudaGraphConditionalHandleCreate(&h[it], cg, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->qacc, 0, sizeof(unsigned long long) * 3 * (size_t)max_iters, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, sizeof(unsigned) * (size_t)max_iters, s);
+    if (e == cudaSuccess) e = launch_adapt_start(s, st);
+    if (e == cudaSuccess) e = enqueue_first_splat(c, s, pos, n, reorder, rec);
+    if (e == cudaSuccess) e = enqueue_iteration(c, s, pos, ipos, n, 0, true, c->qacc, dmax, rec);
+    if (e == cudaSuccess)
+        e = launch_adapt_check(s, c->qacc, dmax, st, cv, mv, 0, c->g.log2N, h[1], max_iters > 1 ? 1 : 0);
+    for (int it = 1; it < max_iters && e == cudaSuccess; ++it) {
+        const cudaGraphNode_t *deps = nullptr;
+        const cudaGraphEdgeData *edges = nullptr;
+        size_t nd = 0;
+        e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, &edges, &nd);
+        if (e != cudaSuccess) break;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h[it];
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        e = cudaGraphAddNode(&node, cg, deps, edges, nd, &np);
+        if (e != cudaSuccess) break;
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(c->cap_stream2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        cudaError_t eb = enqueue_iteration(c, c->cap_stream2, pos, ipos, n, it & 1, true, c->qacc + 3 * it,
+                                           dmax + it, rec);
+        if (eb == cudaSuccess)
+            eb = launch_adapt_check(c->cap_stream2, c->qacc + 3 * it, dmax, st, cv, mv, it, c->g.log2N, h[it + 1],
+                                    it + 1 < max_iters ? 1 : 0);
+        cudaGraph_t body_out = nullptr;
+        e = cudaStreamEndCapture(c->cap_stream2, &body_out);
+        if (eb != cudaSuccess) e = eb;
+        if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    }
+    if (e == cudaSuccess && reorder)
+        e = launch_reorder_back(s, c->spos, c->inv, n, reinterpret_cast<float2 *>(pos), c->status);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(DC_ERR_CUDA, "adaptive graph capture: %s / %s", cudaGetErrorString(e), cudaGetErrorString(e2));
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(DC_ERR_CUDA, "adaptive graph instantiate: %s", cudaGetErrorString(e));
     return DC_OK;
 }
 
@@ -478,7 +598,8 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
         if (cudaStreamCreate(&c->stream) != cudaSuccess) return bail(fail(DC_ERR_CUDA, "cudaStreamCreate"));
         c->own_stream = true;
     }
-    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(DC_ERR_CUDA, "cudaStreamCreateWithFlags"));
     const size_t NN = (size_t)N * N;
     const size_t agg_bytes = (size_t)c->g.nb * c->g.agg_stride * 8;
@@ -552,6 +673,11 @@ dc_status declutter_destroy(dc_ctx *c)
     cudaFree(c->inv);
     cudaFree(c->cursor);
     cudaFree(c->partials);
+    cudaFree(c->adapt);
+    cudaFree(c->lq);
+    cudaFree(c->lterms);
+    cudaFree(c->wcover);
+    if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -716,7 +842,7 @@ dc_status regularize(dc_ctx *c, float *pos, int64_t n, int32_t iters, double *un
     if (dc_status st = ensure_sort_buffers(c, n)) return st;
     cudaGraphExec_t exec = nullptr;
     for (auto &ge : c->graphs)
-        if (ge.pos == pos && ge.n == n && ge.iters == iters && ge.metrics == metrics) exec = ge.exec;
+        if (ge.pos == pos && ge.n == n && ge.iters == iters && ge.metrics == metrics && !ge.adaptive) exec = ge.exec;
     if (!exec) {
         if (c->graphs.size() >= 16) {
             cudaGraphExecDestroy(c->graphs.front().exec);
@@ -812,6 +938,180 @@ dc_status regularize_host(dc_ctx *c, float *host_pos, int64_t n, int32_t iters, 
     if (dc_status st = regularize(c, c->hpos, n, iters, uniformity_out)) return st;
     if (n > 0) DC_CUDA(cudaMemcpyAsync(host_pos, c->hpos, bytes, cudaMemcpyDeviceToHost, c->stream));
     return declutter_sync(c);
+}
+
+dc_status regularize_adaptive(dc_ctx *c, float *pos, int64_t n, int32_t max_iters, double target_cv,
+                              double min_move_px, double max_ms, int32_t *iters_out, double *cv_out,
+                              double *move_px_out)
+{
+    if (dc_status st = check_ctx(c)) return st;
+    if (dc_status st = check_samples(c, pos, n)) return st;
+    if (max_iters < 1 || max_iters > 1024) return fail(DC_ERR_INVALID_ARG, "max_iters = %d (1..1024)", max_iters);
+    if (!(target_cv >= 0.0) || !(min_move_px >= 0.0) || !(max_ms >= 0.0) || !std::isfinite(target_cv) ||
+        !std::isfinite(min_move_px) || !std::isfinite(max_ms))
+        return fail(DC_ERR_INVALID_ARG, "criteria must be finite and >= 0");
+    if (n == 0) return fail(DC_ERR_INVALID_ARG, "no samples");
+    DeviceGuard guard(c->device);
+    if (dc_status st = ensure_qslots(c, max_iters)) return st;
+    if (dc_status st = ensure_adapt(c, max_iters)) return st;
+    if (dc_status st = ensure_sort_buffers(c, n)) return st;
+    cudaGraphExec_t exec = nullptr;
+    for (auto &ge : c->graphs)
+        if (ge.adaptive && ge.pos == pos && ge.n == n && ge.iters == max_iters) exec = ge.exec;
+    if (!exec) {
+        if (c->graphs.size() >= 16) {
+            cudaGraphExecDestroy(c->graphs.front().exec);
+            c->graphs.erase(c->graphs.begin());
+        }
+        if (dc_status st = capture_adaptive(c, pos, n, max_iters, &exec)) return st;
+        GraphEntry ge;
+        ge.pos = pos;
+        ge.n = n;
+        ge.iters = max_iters;
+        ge.metrics = 1;
+        ge.adaptive = 1;
+        ge.exec = exec;
+        c->graphs.push_back(ge);
+    }
+    AdaptState hs{};
+    hs.target_cv = target_cv;
+    hs.min_move_px = min_move_px;
+    hs.max_ns = max_ms * 1e6;
+    DC_CUDA(cudaMemcpyAsync(c->adapt, &hs, sizeof(hs), cudaMemcpyHostToDevice, c->stream));
+    DC_CUDA(cudaGraphLaunch(exec, c->stream));
+    std::vector<double> cvs((size_t)max_iters), mvs((size_t)max_iters);
+    DC_CUDA(cudaMemcpyAsync(&hs, c->adapt, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
+    DC_CUDA(cudaMemcpyAsync(cvs.data(), adapt_cv(c), sizeof(double) * max_iters, cudaMemcpyDeviceToHost, c->stream));
+    DC_CUDA(cudaMemcpyAsync(mvs.data(), adapt_move(c), sizeof(double) * max_iters, cudaMemcpyDeviceToHost, c->stream));
+    const dc_status st = declutter_sync(c);
+    const int done = hs.iters;
+    c->n_last = n;
+    c->have_disp = true;
+    c->cur_counts = done & 1;  // every iteration splatted its moved samples
+    if (st != DC_OK) return st;
+    if (done < 1 || done > max_iters) return fail(DC_ERR_RANGE, "iterations done = %d", done);
+    if (iters_out) *iters_out = done;
+    for (int k = 0; k < done; ++k) {
+        if (cv_out) cv_out[k] = cvs[k];
+        if (move_px_out) move_px_out[k] = mvs[k];
+    }
+    return DC_OK;
+}
+
+dc_status transition_positions(dc_ctx *c, const float *from_xy, const float *to_xy, int64_t n, float s,
+                               float *out_xy)
+{
+    if (dc_status st = check_ctx(c)) return st;
+    if (dc_status st = check_samples(c, from_xy, n)) return st;
+    if (dc_status st = check_samples(c, to_xy, n)) return st;
+    if (dc_status st = check_samples(c, out_xy, n)) return st;
+    if (!(s >= 0.0f && s <= 1.0f)) return fail(DC_ERR_INVALID_ARG, "s = %g outside [0, 1]", (double)s);
+    DeviceGuard guard(c->device);
+    DC_CUDA(launch_transition(c->stream, from_xy, to_xy, 2 * n, s, out_xy));
+    return DC_OK;
+}
+
+dc_status layout_metrics(dc_ctx *c, const float *orig_xy, const float *reg_xy, int64_t n, const uint32_t *queries,
+                         int32_t n_queries, int32_t k, double *out, int64_t *terms_out)
+{
+    if (dc_status st = check_ctx(c)) return st;
+    if (dc_status st = check_samples(c, orig_xy, n)) return st;
+    if (dc_status st = check_samples(c, reg_xy, n)) return st;
+    if (!out) return fail(DC_ERR_INVALID_ARG, "null out");
+    if (n >= (int64_t(1) << 31)) return fail(DC_ERR_INVALID_ARG, "n = %lld (< 2^31)", (long long)n);
+    if (k < 1 || k > 32 || 2 * (int64_t)k >= n)
+        return fail(DC_ERR_INVALID_ARG, "k = %d (1..32, k < n / 2)", k);
+    if (n_queries < 1 || n_queries > (1 << 24) || (!queries && n_queries > n))
+        return fail(DC_ERR_INVALID_ARG, "n_queries = %d", n_queries);
+    if (queries && !aligned(queries, 4)) return fail(DC_ERR_INVALID_ARG, "queries not 4-byte aligned");
+    DeviceGuard guard(c->device);
+    if (n > c->lq_cap || n_queries > c->lterms_cap) {
+        DC_CUDA(cudaStreamSynchronize(c->stream));
+        if (n > c->lq_cap) {
+            cudaFree(c->lq);
+            c->lq = nullptr;
+            c->lq_cap = 0;
+            if (cudaMalloc(&c->lq, sizeof(uint32_t) * 2 * (size_t)n) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(DC_ERR_OOM, "layout scratch");
+            }
+            c->lq_cap = n;
+        }
+        if (n_queries > c->lterms_cap) {
+            cudaFree(c->lterms);
+            c->lterms = nullptr;
+            c->lterms_cap = 0;
+            if (cudaMalloc(&c->lterms, sizeof(long long) * 2 * (size_t)n_queries) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(DC_ERR_OOM, "layout terms");
+            }
+            c->lterms_cap = n_queries;
+        }
+    }
+    DC_CUDA(launch_layout_terms(c->stream, reinterpret_cast<const float2 *>(orig_xy),
+                                reinterpret_cast<const float2 *>(reg_xy), n, queries, n_queries, k, c->lq,
+                                c->lq + n, c->lterms));
+    std::vector<long long> terms(2 * (size_t)n_queries);
+    DC_CUDA(cudaMemcpyAsync(terms.data(), c->lterms, sizeof(long long) * terms.size(), cudaMemcpyDeviceToHost,
+                            c->stream));
+    if (dc_status st = declutter_sync(c)) return st;
+    double tsum = 0.0, osum = 0.0;
+    for (int q = 0; q < n_queries; ++q) {
+        if (terms[2 * (size_t)q] < 0) return fail(DC_ERR_RANGE, "query %d: index outside [0, n)", q);
+        tsum += (double)terms[2 * (size_t)q];
+        osum += (double)terms[2 * (size_t)q + 1];
+    }
+    if (terms_out)
+        for (size_t q = 0; q < terms.size(); ++q) terms_out[q] = (int64_t)terms[q];
+    const double m = (double)n_queries, nn = (double)n, kk = (double)k;
+    out[0] = 1.0 - 2.0 / (m * kk * (2.0 * nn - 3.0 * kk - 1.0)) * tsum;
+    out[1] = 1.0 - osum / (m * (nn - 1.0));
+    return DC_OK;
+}
+
+dc_status warp_texture(dc_ctx *c, const float *nodes_xy, const float *texture, int32_t out_log2, int32_t mode,
+                       float *out, int32_t *tri_out)
+{
+    if (dc_status st = check_ctx(c)) return st;
+    if (!nodes_xy || !texture || !out) return fail(DC_ERR_INVALID_ARG, "null nodes, texture or output");
+    if (!aligned(nodes_xy, 8) || !aligned(texture, 4) || !aligned(out, 4) || (tri_out && !aligned(tri_out, 4)))
+        return fail(DC_ERR_INVALID_ARG, "misaligned pointer");
+    if (out_log2 < 4 || out_log2 > 13) return fail(DC_ERR_INVALID_ARG, "out_log2 = %d (4..13)", out_log2);
+    if (mode != DC_WARP_VALUE && mode != DC_WARP_MASS) return fail(DC_ERR_INVALID_ARG, "mode = %d", mode);
+    DeviceGuard guard(c->device);
+    const int64_t MM = (int64_t)1 << (2 * out_log2);
+    uint32_t *cover = reinterpret_cast<uint32_t *>(tri_out);
+    if (!cover) {
+        if (MM > c->wcover_cap) {
+            DC_CUDA(cudaStreamSynchronize(c->stream));
+            cudaFree(c->wcover);
+            c->wcover = nullptr;
+            c->wcover_cap = 0;
+            if (cudaMalloc(&c->wcover, sizeof(uint32_t) * (size_t)MM) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(DC_ERR_OOM, "coverage scratch");
+            }
+            c->wcover_cap = MM;
+        }
+        cover = c->wcover;
+    }
+    DC_CUDA(launch_warp_texture(c->stream, reinterpret_cast<const float2 *>(nodes_xy), texture, c->g.log2N, out_log2,
+                                mode == DC_WARP_MASS, cover, out));
+    return DC_OK;
+}
+
+dc_status transfer_function(dc_ctx *c, const float *values, int64_t count, float lo, float hi, const uint32_t *lut,
+                            uint32_t *rgba_out)
+{
+    if (dc_status st = check_ctx(c)) return st;
+    if (count < 0) return fail(DC_ERR_INVALID_ARG, "count = %lld", (long long)count);
+    if (count > 0 && (!values || !lut || !rgba_out)) return fail(DC_ERR_INVALID_ARG, "null pointer");
+    if (!aligned(values, 4) || !aligned(lut, 4) || !aligned(rgba_out, 4))
+        return fail(DC_ERR_INVALID_ARG, "misaligned pointer");
+    if (!std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo)) return fail(DC_ERR_INVALID_ARG, "need lo < hi, finite");
+    DeviceGuard guard(c->device);
+    DC_CUDA(launch_transfer(c->stream, values, count, lo, hi, lut, rgba_out));
+    return DC_OK;
 }
 
 dc_status declutter_counts(dc_ctx *c, uint32_t *counts_out)

@@ -125,15 +125,19 @@ struct GraphEntry {
     int64_t n = 0;
     int iters = 0;
     int metrics = 0;
+    int adaptive = 0;  // regularize_adaptive's graph (conditional iterations)
     cudaGraphExec_t exec = nullptr;
 };
 
 // Launchers (all enqueue on `s`; return cudaGetLastError()).
 cudaError_t launch_splat(cudaStream_t s, const float2 *pos, int64_t n, uint32_t *counts, int log2N);
 // counts_next: if not null, the moved samples are also splatted into it (must
-// be zero); sorted: the samples are in pixel order (run aggregation pays)
+// be zero); sorted: the samples are in pixel order (run aggregation pays);
+// dmax: if not null, the largest squared move of a sample (domain units) is
+// maxed into it as float bits
 cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *disp, int log2N,
-                          int pixel_center, int clamp, uint32_t *counts_next, bool sorted = false);
+                          int pixel_center, int clamp, uint32_t *counts_next, bool sorted = false,
+                          unsigned *dmax = nullptr);
 cudaError_t launch_quality(cudaStream_t s, const uint32_t *counts, int log2N, unsigned long long *acc);
 // reordering of the samples by pixel: the first splat also records each
 // sample's rank within its pixel; exclusive scan of the counts into cursor
@@ -188,6 +192,42 @@ cudaError_t launch_smooth_batched(cudaStream_t s, const PanelDesc *tab, int P, i
 // aggregate, carries and final pass (grids below 2048^2, the per-thread-contiguous band kernels)
 cudaError_t launch_band_batched(cudaStream_t s, const BandGeom &g, int mode, int carry_mode, const PanelDesc *tab,
                                 int P, int cur, bool zero_next);
+// out[k] = (1 - t) a[k] + t b[k] for count floats, rounded as written
+cudaError_t launch_transition(cudaStream_t s, const float *a, const float *b, int64_t count, float t, float *out);
+// per-query terms of the Sec. 6.2 layout measures (trustworthiness, orthogonal
+// ordering) of reg against orig: terms[2q] = sum of (rank - k) over the new
+// k-neighbours of query q missing from its original k-neighbourhood,
+// terms[2q + 1] = samples whose orthogonal order relative to q changed (-1, -1
+// for a query index outside [0, n)); qo, qn: uint32[n] scratch; queries: device
+// uint32[n_queries] or null for 0 .. n_queries - 1; 1 <= k <= 32
+cudaError_t launch_layout_terms(cudaStream_t s, const float2 *orig, const float2 *reg, int64_t n,
+                                const uint32_t *queries, int n_queries, int k, uint32_t *qo, uint32_t *qn,
+                                long long *terms);
+// Sec. 4.3 step 4, inside a graph: the start kernel stamps the time; the
+// check kernel of iteration it reads its Sec. 6.2 accumulators and largest
+// move, records them, and sets the condition of iteration it + 1 (when
+// has_next) to 0 once a criterion holds
+struct AdaptState {
+    double target_cv;      // stop when bin std / mean <= target_cv (> 0)
+    double min_move_px;    // stop when the largest move <= min_move_px (> 0)
+    double max_ns;         // stop when the elapsed device time >= max_ns (> 0)
+    unsigned long long t0; // %globaltimer at the start of the graph
+    int iters;             // iterations done
+    int pad;
+};
+cudaError_t launch_adapt_start(cudaStream_t s, AdaptState *st);
+cudaError_t launch_adapt_check(cudaStream_t s, const unsigned long long *qacc, const unsigned *dmax, AdaptState *st,
+                               double *cv, double *move_px, int it, int log2N, cudaGraphConditionalHandle next,
+                               int has_next);
+// Sec. 5 density texture on the deformed node mesh (N = 2^log2N nodes a
+// side, texture N x N) rasterised into M x M, M = 2^log2M: cover[M*M]
+// receives the winning triangle per pixel (0xffffffff: none), out[M*M] the
+// value (push-forward density with mass); and the transfer function
+// value -> lut[rint((v - lo) 255 / (hi - lo))] (RGBA8)
+cudaError_t launch_warp_texture(cudaStream_t s, const float2 *nodes, const float *tex, int log2N, int log2M,
+                                int mass, uint32_t *cover, float *out);
+cudaError_t launch_transfer(cudaStream_t s, const float *v, int64_t count, float lo, float hi, const uint32_t *lut,
+                            uint32_t *rgba);
 cudaError_t prepare_kernels();  // per-device kernel attributes; call with the device current
 cudaError_t prepare_point_kernels();  // part of prepare_kernels: launch shapes of the sample kernels
 void set_last_error(const char *msg);  // message returned by declutter_last_error()
@@ -237,6 +277,20 @@ struct dc_ctx {
     uint32_t *partials = nullptr;       // <= 1024 chunk sums
     int64_t hpos_cap = 0;
     int64_t scratch_bytes = 0;
+    // regularize_adaptive: AdaptState, then cv[cap], move_px[cap] (double),
+    // then dmax[cap] (float bits); the bodies of the conditional iterations
+    // are captured on cap_stream2
+    void *adapt = nullptr;
+    int adapt_cap = 0;
+    cudaStream_t cap_stream2 = nullptr;
+    // layout_metrics scratch: lattice coordinates of both layouts, query terms
+    uint32_t *lq = nullptr;
+    int64_t lq_cap = 0;
+    long long *lterms = nullptr;
+    int64_t lterms_cap = 0;
+    // warp_texture coverage scratch (uint32 per output pixel)
+    uint32_t *wcover = nullptr;
+    int64_t wcover_cap = 0;
 
     int64_t n_last = -1;                // n of the last splat
     bool have_disp = false;

@@ -176,9 +176,21 @@ __device__ __forceinline__ void splat_warp_runs(uint32_t *__restrict__ counts, i
 // pixel, neighbouring lanes mostly hold samples of the same pixel.  A sample
 // before the first 16-byte boundary and one left after the last pair are
 // handled by thread 0 of block 0.
-template <bool RUNS>
+// Squared length of a sample's move (domain units); lanes that hold no
+// sample give 0.
+__device__ __forceinline__ float move2(float2 a, float2 b, bool valid)
+{
+    const float dx = b.x - a.x, dy = b.y - a.y;
+    return valid ? dx * dx + dy * dy : 0.0f;
+}
+
+// MAXD: the largest squared move of a sample is atomically maxed into
+// *dmax as float bits (non-negative floats order like their bit patterns),
+// one atomic per warp and trip: the impact of the iteration (Sec. 4.3 step 4).
+template <bool RUNS, bool MAXD = false>
 __device__ __forceinline__ void advect_body(float2 *__restrict__ pos, int64_t n, const float2 *__restrict__ D,
-                                            int log2N, float off, int clamp, uint32_t *__restrict__ counts_next)
+                                            int log2N, float off, int clamp, uint32_t *__restrict__ counts_next,
+                                            unsigned *__restrict__ dmax = nullptr)
 {
     pdl_wait();
     const float fN = (float)(1 << log2N);
@@ -212,6 +224,12 @@ __device__ __forceinline__ void advect_body(float2 *__restrict__ pos, int64_t n,
         const Moved m3 = advect_one(make_float2(b.z, b.w), D, log2N, fN, off, clamp);
         if (v1) pp[q1] = make_float4(m0.z.x, m0.z.y, m1.z.x, m1.z.y);
         if (v2) pp[q2] = make_float4(m2.z.x, m2.z.y, m3.z.x, m3.z.y);
+        if constexpr (MAXD) {
+            const float d = fmaxf(fmaxf(move2(make_float2(a.x, a.y), m0.z, v1), move2(make_float2(a.z, a.w), m1.z, v1)),
+                                  fmaxf(move2(make_float2(b.x, b.y), m2.z, v2), move2(make_float2(b.z, b.w), m3.z, v2)));
+            const unsigned w = __reduce_max_sync(0xffffffffu, __float_as_uint(d));
+            if (lane == 0 && w) atomicMax(dmax, w);
+        }
         if (counts_next) {
             if constexpr (RUNS) {
                 splat_warp_runs(counts_next, m0.pix, v1);
@@ -230,18 +248,24 @@ __device__ __forceinline__ void advect_body(float2 *__restrict__ pos, int64_t n,
         int64_t singles[2] = {head ? 0 : -1, (n - head) & 1 ? n - 1 : -1};
         for (int s = 0; s < 2; ++s) {
             if (singles[s] < 0) continue;
-            const Moved m = advect_one(pos[singles[s]], D, log2N, fN, off, clamp);
+            const float2 z0 = pos[singles[s]];
+            const Moved m = advect_one(z0, D, log2N, fN, off, clamp);
             pos[singles[s]] = m.z;
             if (counts_next) atomicAdd(&counts_next[m.pix], 1u);
+            if constexpr (MAXD) {
+                const unsigned w = __float_as_uint(move2(z0, m.z, true));
+                if (w) atomicMax(dmax, w);
+            }
         }
     }
 }
-template <bool RUNS>
+template <bool RUNS, bool MAXD>
 __global__ void __launch_bounds__(kThreads) advect_kernel(float2 *__restrict__ pos, int64_t n,
                                                           const float2 *__restrict__ D, int log2N, float off,
-                                                          int clamp, uint32_t *__restrict__ counts_next)
+                                                          int clamp, uint32_t *__restrict__ counts_next,
+                                                          unsigned *__restrict__ dmax)
 {
-    advect_body<RUNS>(pos, n, D, log2N, off, clamp, counts_next);
+    advect_body<RUNS, MAXD>(pos, n, D, log2N, off, clamp, counts_next, dmax);
 }
 
 // ------------------------------------------------------------------------
@@ -494,8 +518,10 @@ cudaError_t prepare_point_kernels()
     int dev = 0, sms = 0, p0 = 0, p1 = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p0, advect_kernel<false>, kThreads, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, advect_kernel<true>, kThreads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p0, advect_kernel<false, false>, kThreads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, advect_kernel<true, false>, kThreads, 0);
     if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices && sms > 0 && p0 > 0 && p1 > 0)
         g_advect_wave[dev].store((p0 < p1 ? p0 : p1) * sms, std::memory_order_relaxed);
     return e;
@@ -509,18 +535,27 @@ cudaError_t launch_splat(cudaStream_t s, const float2 *pos, int64_t n, uint32_t 
 }
 
 cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *disp, int log2N,
-                          int pixel_center, int clamp, uint32_t *counts_next, bool sorted)
+                          int pixel_center, int clamp, uint32_t *counts_next, bool sorted, unsigned *dmax)
 {
     if (n <= 0) return cudaSuccess;
     // two pairs (four samples) per thread and trip, at most one wave; run
     // aggregation for samples in pixel order up to 1024^2 (measured faster
     // there)
     const dim3 grid(grid_for((n + 3) / 4, kThreads, advect_wave()));
-    if (sorted && log2N <= 10)
-        return launch_kernel(advect_kernel<true>, grid, dim3(kThreads), 0, s, pos, n, disp, log2N,
-                             pixel_center ? 0.5f : 0.0f, clamp, counts_next);
-    return launch_kernel(advect_kernel<false>, grid, dim3(kThreads), 0, s, pos, n, disp, log2N,
-                         pixel_center ? 0.5f : 0.0f, clamp, counts_next);
+    const float off = pixel_center ? 0.5f : 0.0f;
+    const bool runs = sorted && log2N <= 10;
+    if (dmax) {
+        if (runs)
+            return launch_kernel(advect_kernel<true, true>, grid, dim3(kThreads), 0, s, pos, n, disp, log2N, off,
+                                 clamp, counts_next, dmax);
+        return launch_kernel(advect_kernel<false, true>, grid, dim3(kThreads), 0, s, pos, n, disp, log2N, off, clamp,
+                             counts_next, dmax);
+    }
+    if (runs)
+        return launch_kernel(advect_kernel<true, false>, grid, dim3(kThreads), 0, s, pos, n, disp, log2N, off, clamp,
+                             counts_next, (unsigned *)nullptr);
+    return launch_kernel(advect_kernel<false, false>, grid, dim3(kThreads), 0, s, pos, n, disp, log2N, off, clamp,
+                         counts_next, (unsigned *)nullptr);
 }
 
 int64_t reorder_scan_chunk(int log2N)

@@ -26,7 +26,8 @@ __all__ = [
     "DeclutterError", "Context", "dc_params", "dc_info", "load_library", "exported_symbols",
     "declutter_create", "declutter_destroy", "declutter_get_info", "splat_density", "integral_images",
     "integral_images_u32", "displacement_field", "lens_field", "contour_segments", "advect_samples", "regularize", "regularize_host",
-    "quality_metrics", "declutter_counts", "declutter_sync", "declutter_profile_regularize", "declutter_kernel_name",
+    "quality_metrics", "declutter_counts", "declutter_sync", "regularize_adaptive", "transition_positions",
+    "layout_metrics", "warp_texture", "transfer_function", "DC_WARP_VALUE", "DC_WARP_MASS", "declutter_profile_regularize", "declutter_kernel_name",
     "declutter_status_string", "declutter_last_error", "DC_CARRY_COMPENSATED", "DC_CARRY_F64",
     "DC_OPT_FUSED_BANDS", "DC_OPT_SEPARATE_SMOOTH", "DC_OPT_STAGE_HOST", "DC_OPT_BATCHED_LAUNCHES",
     "DC_OPT_TEST_UNREACHED_BARRIER", "DC_SG_MMA_SYNC", "DC_SG_TCGEN05",
@@ -50,6 +51,9 @@ DC_OPT_SEPARATE_SMOOTH = 2
 DC_OPT_STAGE_HOST = 4
 DC_OPT_BATCHED_LAUNCHES = 8
 DC_OPT_TEST_UNREACHED_BARRIER = 1 << 30
+# warp_texture modes
+DC_WARP_VALUE = 0
+DC_WARP_MASS = 1
 # surrogate_set_tensor_path
 DC_SG_MMA_SYNC = 0
 DC_SG_TCGEN05 = 1
@@ -111,6 +115,12 @@ _SIGS = [
     ("regularize_host", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
     ("quality_metrics", ctypes.c_int, [_P, _P]),
     ("declutter_counts", ctypes.c_int, [_P, _P]),
+    ("regularize_adaptive", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, _P, _P, _P]),
+    ("transition_positions", ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_float, _P]),
+    ("layout_metrics", ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    ("warp_texture", ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    ("transfer_function", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, _P, _P]),
     ("declutter_sync", ctypes.c_int, [_P]),
     ("declutter_profile_regularize", ctypes.c_int,
      [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
@@ -383,6 +393,88 @@ def regularize_host(ctx: Context, host_pos, iters: int, uniformity: bool = False
     _check(load_library().regularize_host(ctx.handle, ctypes.c_void_p(ptr), int(n), int(iters), out),
            "regularize_host")
     return list(out)[:iters] if uniformity else None
+
+
+def regularize_adaptive(ctx: Context, pos, max_iters: int, target_cv: float = 0.0, min_move_px: float = 0.0,
+                        max_ms: float = 0.0) -> dict:
+    """Iterate until a stopping criterion holds (see the C header); returns
+    ``{"iters": k, "cv": [...], "move_px": [...]}`` for the k iterations done."""
+    pp, n = _pos_args(pos, ctx.device)
+    it = ctypes.c_int32()
+    cv = (ctypes.c_double * max(int(max_iters), 1))()
+    mv = (ctypes.c_double * max(int(max_iters), 1))()
+    _check(load_library().regularize_adaptive(ctx.handle, pp, n, int(max_iters), float(target_cv),
+                                              float(min_move_px), float(max_ms), ctypes.byref(it), cv, mv),
+           "regularize_adaptive")
+    k = int(it.value)
+    return {"iters": k, "cv": list(cv)[:k], "move_px": list(mv)[:k]}
+
+
+def transition_positions(ctx: Context, from_pos, to_pos, s: float, out) -> None:
+    """out = (1 - s) from + s to for CUDA float32 [n, 2] tensors."""
+    fp, n = _pos_args(from_pos, ctx.device, "from_pos")
+    tp, n2 = _pos_args(to_pos, ctx.device, "to_pos")
+    op, n3 = _pos_args(out, ctx.device, "out")
+    if not (n == n2 == n3):
+        raise ValueError("from_pos, to_pos and out must have the same shape")
+    _check(load_library().transition_positions(ctx.handle, fp, tp, n, float(s), op), "transition_positions")
+
+
+def layout_metrics(ctx: Context, orig, reg, k: int, queries=None, n_queries: int | None = None,
+                   want_terms: bool = False) -> dict:
+    """Trustworthiness and orthogonal ordering of ``reg`` against ``orig``
+    (CUDA float32 [n, 2]) over the query samples: ``queries`` a CUDA int32
+    tensor of indices, or None for the first ``n_queries`` samples (all when
+    None).  Returns ``{"trustworthiness": T, "ordering": O}`` (+ ``"terms"``,
+    int64 [m, 2], with ``want_terms``)."""
+    import torch
+    op, n = _pos_args(orig, ctx.device, "orig")
+    rp, n2 = _pos_args(reg, ctx.device, "reg")
+    if n != n2:
+        raise ValueError("orig and reg must have the same shape")
+    if queries is not None:
+        m = int(queries.numel())
+        qp = _ptr(queries, torch.int32, m, "queries", ctx.device)
+    else:
+        m = int(n if n_queries is None else n_queries)
+        qp = None
+    out = (ctypes.c_double * 2)()
+    terms = np.zeros((m, 2), np.int64) if want_terms else None
+    _check(load_library().layout_metrics(ctx.handle, op, rp, n, qp, m, int(k), out,
+                                         terms.ctypes.data_as(ctypes.c_void_p) if want_terms else None),
+           "layout_metrics")
+    res = {"trustworthiness": out[0], "ordering": out[1]}
+    if want_terms:
+        res["terms"] = terms
+    return res
+
+
+def warp_texture(ctx: Context, nodes, texture, out_log2: int, out, mass: bool = False, tri_out=None) -> None:
+    """Draw ``texture`` (CUDA float32, N*N values at the pixel nodes) on the
+    mesh of the moved nodes ``nodes`` (CUDA float32 [N*N, 2]) into ``out``
+    (CUDA float32, M*M, M = 2^out_log2); ``tri_out`` (CUDA int32 M*M) gets
+    the winning triangle per pixel (-1: none)."""
+    import torch
+    NN = ctx.N * ctx.N
+    MM = 1 << (2 * int(out_log2))
+    np_, nn = _pos_args(nodes, ctx.device, "nodes")
+    if nn != NN:
+        raise ValueError(f"nodes must have {NN} rows")
+    _check(load_library().warp_texture(ctx.handle, np_, _ptr(texture, torch.float32, NN, "texture", ctx.device),
+                                       int(out_log2), DC_WARP_MASS if mass else DC_WARP_VALUE,
+                                       _ptr(out, torch.float32, MM, "out", ctx.device),
+                                       _ptr(tri_out, torch.int32, MM, "tri_out", ctx.device)), "warp_texture")
+
+
+def transfer_function(ctx: Context, values, lo: float, hi: float, lut, rgba_out) -> None:
+    """RGBA8 colours (CUDA int32 bit patterns) of CUDA float32 ``values``
+    through the 256-entry table ``lut`` (CUDA int32)."""
+    import torch
+    n = int(values.numel())
+    _check(load_library().transfer_function(ctx.handle, _ptr(values, torch.float32, None, "values", ctx.device), n,
+                                            float(lo), float(hi), _ptr(lut, torch.int32, 256, "lut", ctx.device),
+                                            _ptr(rgba_out, torch.int32, n, "rgba_out", ctx.device)),
+           "transfer_function")
 
 
 def declutter_counts(ctx: Context, counts_out) -> None:

@@ -250,3 +250,13 @@ def test_push_forward_keeps_the_mass():
     ident, _ = L.warp_texture(L.identity_nodes(N), tex, log2M, mass=True)
     warped, _ = L.warp_texture(nodes, tex, log2M, mass=True)
     assert abs(warped.sum() / ident.sum() - 1.0) < 0.01
+
+
+def test_transfer_closed_form():
+    lut = np.arange(256, dtype=np.uint32) * 3 + 7
+    v = np.array([0.0, 1.0, 0.5, -3.0, 9.0, np.nan, 0.25, 1.0 / 255.0], np.float32)
+    got = L.transfer(v, 0.0, 1.0, lut)
+    # rint(127.5) = 128 (ties to even), rint(63.75) = 64
+    assert got.tolist() == [7, 7 + 3 * 255, 7 + 3 * 128, 7, 7 + 3 * 255, 7, 7 + 3 * 64, 7 + 3]
+    g2 = L.transfer(np.array([2.0, 6.0], np.float32), 2.0, 6.0, lut)
+    assert g2.tolist() == [7, 7 + 3 * 255]
