@@ -309,30 +309,38 @@ def oracle_sample_size(z_full, iters, target_step_s):
 # ---------------------------------------------------------------------------
 
 def run_reference(args, world, rank):
+    """The CPU oracle on the work the GPU arm does: one scatterplot per rank
+    (seed offset by rank, as the GPU ranks generate them), all timed on rank
+    0's host cores; each step a bounded sample of every plot."""
     if rank != 0:
         return
-    z_full = gen_samples(0)
     iters = WORKLOAD["iters"]
     total_steps = args.steps + args.warmup
-    # each step a bounded sample: the whole run stays within a few minutes
-    n_s = oracle_sample_size(z_full, iters, target_step_s=max(0.2, min(args.cpu_budget, 150.0 / max(total_steps, 1))))
-    z = np.ascontiguousarray(z_full[:n_s])
+    plots = [gen_samples(k) for k in range(world)]
+    # each step a bounded sample of every plot: the whole run stays within a few minutes
+    target = max(0.2, min(args.cpu_budget, 150.0 / max(total_steps, 1))) / world
+    n_s = oracle_sample_size(plots[0], iters, target_step_s=target)
+    zs = [np.ascontiguousarray(z[:n_s]) for z in plots]
     import oracle
     p = oracle.Params(log2_res=WORKLOAD["log2_res"], kernel_r=WORKLOAD["kernel_r"])
+
+    def step():
+        for z in zs:
+            cur = z
+            for _ in range(iters):
+                cur = oracle.iterate(cur, p)
+
     for _ in range(args.warmup):
-        cur = z
-        for _ in range(iters):
-            cur = oracle.iterate(cur, p)
+        step()
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        cur = z
-        for _ in range(iters):
-            cur = oracle.iterate(cur, p)
+        step()
         times.append(time.perf_counter() - t0)
     per = sum(times) / len(times)
-    value = n_s * iters / per / 1e6
-    sample = f"first {n_s} of the 1M samples, 512x512, r=4, 8 iterations per step"
+    value = world * n_s * iters / per / 1e6
+    sample = (f"first {n_s} of the 1M samples of each of {world} plot(s) (one per rank, as the GPU arm), "
+              f"512x512, r=4, 8 iterations per step")
     line = {
         "impl": "reference",
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,

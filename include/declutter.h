@@ -160,6 +160,20 @@ dc_status declutter_get_info(const dc_ctx *ctx, dc_info *out);
 dc_status splat_density(dc_ctx *ctx, const float *pos_xy, int64_t n, uint32_t *counts_out,
                         float *density_out);
 
+/* Step (a) split at the count grid, for a plot whose samples are sharded
+ * over several devices or processes (Sec. 4.3 step 1: the counts are integer
+ * sums, so per-shard grids added together give exactly the grid of all
+ * samples).  splat_counts: the single-pixel accumulation of this shard's n
+ * samples into counts_out (device uint32[N*N], 16-byte aligned; zeroed
+ * first); the context's own grids are not touched.  density_from_counts:
+ * takes the summed grid (device uint32[N*N], 16-byte aligned) of all n
+ * samples of the plot as the context's count grid and smooths it as
+ * splat_density does; displacement_field() and advect_samples() (on this
+ * shard's samples) follow.  Asynchronous.  Errors: DC_ERR_INVALID_ARG for a
+ * null or misaligned pointer or n outside [0, 2^32). */
+dc_status splat_counts(dc_ctx *ctx, const float *pos_xy, int64_t n, uint32_t *counts_out);
+dc_status density_from_counts(dc_ctx *ctx, const uint32_t *counts, int64_t n);
+
 /* Step (b), Sec. 3.1: alpha (sum over i' <= i, j' <= j) and alpha_t (sum over
  * i'+j' <= i+j, i'-j' >= i-j) of the density of the last splat_density call.
  * The other six images follow from these two and their marginals

@@ -716,6 +716,32 @@ dc_status splat_density(dc_ctx *c, const float *pos, int64_t n, uint32_t *counts
     return DC_OK;
 }
 
+dc_status splat_counts(dc_ctx *c, const float *pos, int64_t n, uint32_t *counts_out)
+{
+    if (dc_status st = check_ctx(c)) return st;
+    if (dc_status st = check_samples(c, pos, n)) return st;
+    if (!counts_out || !aligned(counts_out, 16)) return fail(DC_ERR_INVALID_ARG, "counts_out null or misaligned");
+    DeviceGuard guard(c->device);
+    DC_CUDA(cudaMemsetAsync(counts_out, 0, sizeof(uint32_t) * (size_t)c->g.N * c->g.N, c->stream));
+    DC_CUDA(launch_splat(c->stream, reinterpret_cast<const float2 *>(pos), n, counts_out, c->g.log2N));
+    return DC_OK;
+}
+
+dc_status density_from_counts(dc_ctx *c, const uint32_t *counts, int64_t n)
+{
+    if (dc_status st = check_ctx(c)) return st;
+    if (!counts || !aligned(counts, 16)) return fail(DC_ERR_INVALID_ARG, "counts null or misaligned");
+    if (n < 0 || n >= (int64_t(1) << 32)) return fail(DC_ERR_INVALID_ARG, "n = %lld", (long long)n);
+    DeviceGuard guard(c->device);
+    const size_t NN = (size_t)c->g.N * c->g.N;
+    DC_CUDA(cudaMemcpyAsync(c->counts_buf[0], counts, NN * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->mode == MODE_FLOAT) DC_CUDA(launch_smooth(c->stream, c->counts_buf[0], c->dens, c->g.log2N, c->w, nullptr));
+    c->cur_counts = 0;
+    c->n_last = n;
+    c->have_disp = false;
+    return DC_OK;
+}
+
 dc_status integral_images(dc_ctx *c, void *alpha_out, void *alpha_t_out)
 {
     if (dc_status st = check_ctx(c)) return st;

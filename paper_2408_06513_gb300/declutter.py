@@ -25,7 +25,7 @@ import numpy as np
 __all__ = [
     "DeclutterError", "Context", "dc_params", "dc_info", "load_library", "exported_symbols",
     "declutter_create", "declutter_destroy", "declutter_get_info", "splat_density", "integral_images",
-    "integral_images_u32", "displacement_field", "lens_field", "contour_segments", "advect_samples", "regularize", "regularize_host",
+    "integral_images_u32", "splat_counts", "density_from_counts", "displacement_field", "lens_field", "contour_segments", "advect_samples", "regularize", "regularize_host",
     "quality_metrics", "declutter_counts", "declutter_sync", "regularize_adaptive", "transition_positions",
     "layout_metrics", "warp_texture", "transfer_function", "DC_WARP_VALUE", "DC_WARP_MASS", "declutter_profile_regularize", "declutter_kernel_name",
     "declutter_status_string", "declutter_last_error", "DC_CARRY_COMPENSATED", "DC_CARRY_F64",
@@ -105,6 +105,8 @@ _SIGS = [
     ("declutter_destroy", ctypes.c_int, [_P]),
     ("declutter_get_info", ctypes.c_int, [_P, ctypes.POINTER(dc_info)]),
     ("splat_density", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    ("splat_counts", ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    ("density_from_counts", ctypes.c_int, [_P, _P, ctypes.c_int64]),
     ("integral_images", ctypes.c_int, [_P, _P, _P]),
     ("integral_images_u32", ctypes.c_int, [_P, _P, _P, _P]),
     ("displacement_field", ctypes.c_int, [_P, _P]),
@@ -308,6 +310,23 @@ def splat_density(ctx: Context, pos, counts_out=None, density_out=None) -> None:
     _check(load_library().splat_density(ctx.handle, pp, n,
                                         _ptr(counts_out, torch.int32, NN, "counts_out", ctx.device),
                                         _ptr(density_out, torch.float32, NN, "density_out", ctx.device)), "splat_density")
+
+
+def splat_counts(ctx: Context, pos, counts_out) -> None:
+    """This shard's counts (uint32 bit patterns) into the CUDA int32 tensor
+    ``counts_out`` of N*N elements."""
+    import torch
+    pp, n = _pos_args(pos, ctx.device)
+    _check(load_library().splat_counts(ctx.handle, pp, n, _ptr(counts_out, torch.int32, ctx.N * ctx.N, "counts_out",
+                                                               ctx.device)), "splat_counts")
+
+
+def density_from_counts(ctx: Context, counts, n_total: int) -> None:
+    """The summed count grid of all ``n_total`` samples (CUDA int32, N*N) as
+    the context's density."""
+    import torch
+    _check(load_library().density_from_counts(ctx.handle, _ptr(counts, torch.int32, ctx.N * ctx.N, "counts",
+                                                               ctx.device), int(n_total)), "density_from_counts")
 
 
 def _u64(t, NN, name, device=None):

@@ -89,4 +89,6 @@ def test_reference_arm_torchrun_world2():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 1 and d["warmup"] == 3
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    # the same work as the GPU arm: one plot per rank
+    assert "each of 2 plot(s)" in d["cpu_baseline"]["sample"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0
