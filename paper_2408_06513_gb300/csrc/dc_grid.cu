@@ -110,6 +110,42 @@ __global__ void __launch_bounds__(256) smooth_kernel(const uint32_t *__restrict_
     }
 }
 
+// R consecutive outputs of a 1-D Gaussian pass: acc[k] = sum over taps t
+// (ascending) of g[t] x(k + t), one fused multiply-add each, x(i) = load(i)
+// for i in [0, R + 2r).  RAD >= 0 is the radius known at compile time: the
+// taps are fully unrolled, each weight an operand straight from the kernel
+// parameters and every input loaded once into registers; RAD < 0 slides a
+// register window through a loop over the runtime radius r.  Both sum in
+// the same order, so they give identical results.
+template <int R, int RAD, typename Load>
+__device__ __forceinline__ void gauss_window(const GaussW &w, int r, Load load, float (&acc)[R])
+{
+#pragma unroll
+    for (int k = 0; k < R; ++k) acc[k] = 0.0f;
+    if constexpr (RAD >= 0) {
+        float x[R + 2 * RAD];
+#pragma unroll
+        for (int i = 0; i < R + 2 * RAD; ++i) x[i] = load(i);
+#pragma unroll
+        for (int t = 0; t <= 2 * RAD; ++t)
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] = fmaf(w.g[t], x[k + t], acc[k]);
+    } else {
+        float win[R];
+#pragma unroll
+        for (int k = 0; k + 1 < R; ++k) win[k + 1] = load(k);
+#pragma unroll R
+        for (int t = 0; t <= 2 * r; ++t) {
+#pragma unroll
+            for (int k = 0; k + 1 < R; ++k) win[k] = win[k + 1];
+            win[R - 1] = load(t + R - 1);
+            const float g = w.g[t];
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] = fmaf(g, win[k], acc[k]);
+        }
+    }
+}
+
 // The same smoothing with register sliding windows: each thread computes R
 // consecutive outputs of a column (vertical pass) or of a row (horizontal
 // pass), loading R + 2r values instead of R (2r + 1).  Taps are summed in
@@ -117,7 +153,7 @@ __global__ void __launch_bounds__(256) smooth_kernel(const uint32_t *__restrict_
 // kernels give identical results.  TS x TS outputs per CTA; the vertical
 // pass's output rows are padded to an odd stride so that the horizontal
 // pass's lanes (one row each) read conflict-free.
-template <int TS, int R>
+template <int TS, int R, int RAD>
 __device__ __forceinline__ void smooth_win_body(const uint32_t *__restrict__ counts, float *__restrict__ dens,
                                                 int log2N, const GaussW &w, uint32_t *__restrict__ zero_out)
 {
@@ -150,20 +186,9 @@ __device__ __forceinline__ void smooth_win_body(const uint32_t *__restrict__ cou
     for (int item = tid; item < (TS / R) * W; item += blockDim.x) {
         const int seg = item / W, xx = item - seg * W;
         const int y0 = seg * R;
-        float acc[R], win[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) acc[k] = 0.0f;
-#pragma unroll
-        for (int k = 0; k + 1 < R; ++k) win[k + 1] = s_in[(y0 + k) * W + xx];
-#pragma unroll R
-        for (int t = 0; t <= 2 * r; ++t) {
-#pragma unroll
-            for (int k = 0; k + 1 < R; ++k) win[k] = win[k + 1];
-            win[R - 1] = s_in[(y0 + t + R - 1) * W + xx];
-            const float g = w.g[t];
-#pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] = fmaf(g, win[k], acc[k]);
-        }
+        const float *col = s_in + y0 * W + xx;
+        float acc[R];
+        gauss_window<R, RAD>(w, r, [&](int i) { return col[i * W]; }, acc);
 #pragma unroll
         for (int k = 0; k < R; ++k) s_mid[(y0 + k) * Wp + xx] = acc[k];
     }
@@ -173,32 +198,20 @@ __device__ __forceinline__ void smooth_win_body(const uint32_t *__restrict__ cou
         const int seg = item / TS, y = item - seg * TS;
         const int x0 = seg * R;
         const float *row = s_mid + y * Wp + x0;
-        float acc[R], win[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) acc[k] = 0.0f;
-#pragma unroll
-        for (int k = 0; k + 1 < R; ++k) win[k + 1] = row[k];
-#pragma unroll R
-        for (int t = 0; t <= 2 * r; ++t) {
-#pragma unroll
-            for (int k = 0; k + 1 < R; ++k) win[k] = win[k + 1];
-            win[R - 1] = row[t + R - 1];
-            const float g = w.g[t];
-#pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] = fmaf(g, win[k], acc[k]);
-        }
+        float acc[R];
+        gauss_window<R, RAD>(w, r, [&](int i) { return row[i]; }, acc);
         float *o = dens + ((size_t)(oy + y) << log2N) + ox + x0;
 #pragma unroll
         for (int k = 0; k < R; k += 4)
             *reinterpret_cast<float4 *>(o + k) = make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
     }
 }
-template <int TS, int R>
+template <int TS, int R, int RAD>
 __global__ void __launch_bounds__(256) smooth_win_kernel(const uint32_t *__restrict__ counts,
                                                          float *__restrict__ dens, int log2N, GaussW w,
                                                          uint32_t *__restrict__ zero_out)
 {
-    smooth_win_body<TS, R>(counts, dens, log2N, w, zero_out);
+    smooth_win_body<TS, R, RAD>(counts, dens, log2N, w, zero_out);
 }
 
 // ------------------------------------------------------------------------
@@ -685,7 +698,7 @@ __device__ __noinline__ void band_body_wide(BandArgs a, int log2N, int T)
 // ------------------------------------------------------------------------
 __device__ __forceinline__ int swz32(int x) { return x + (x >> 5); }
 
-template <int CPT, int R>
+template <int CPT, int R, int RAD>
 __global__ void __launch_bounds__(1024) smooth_agg_kernel(BandArgs a, int log2N, int T, GaussW w,
                                                          const uint32_t *__restrict__ counts,
                                                          float *__restrict__ dens, uint32_t *__restrict__ zero_out)
@@ -753,20 +766,9 @@ __global__ void __launch_bounds__(1024) smooth_agg_kernel(BandArgs a, int log2N,
     for (int item = tid; item < nseg * W; item += blockDim.x) {
         const int seg = item / W, xx = item - seg * W;
         const int y0 = seg * R;
-        float acc[R], win[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) acc[k] = 0.0f;
-#pragma unroll
-        for (int k = 0; k + 1 < R; ++k) win[k + 1] = s_in[(size_t)(y0 + k) * W + xx];
-#pragma unroll R
-        for (int t = 0; t <= 2 * r; ++t) {
-#pragma unroll
-            for (int k = 0; k + 1 < R; ++k) win[k] = win[k + 1];
-            win[R - 1] = s_in[(size_t)(y0 + t + R - 1) * W + xx];
-            const float g = w.g[t];
-#pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] = fmaf(g, win[k], acc[k]);
-        }
+        const float *col = s_in + (size_t)y0 * W + xx;
+        float acc[R];
+        gauss_window<R, RAD>(w, r, [&](int i) { return col[(size_t)i * W]; }, acc);
 #pragma unroll
         for (int k = 0; k < R; ++k)
             if (y0 + k < Tb) s_mid[(size_t)(y0 + k) * Ws + swz32(xx)] = acc[k];
@@ -777,20 +779,8 @@ __global__ void __launch_bounds__(1024) smooth_agg_kernel(BandArgs a, int log2N,
     for (int item = tid; item < Tb * segs; item += blockDim.x) {
         const int y = item / segs, x0 = (item - y * segs) * R;
         const float *row = s_mid + (size_t)y * Ws;
-        float acc[R], win[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) acc[k] = 0.0f;
-#pragma unroll
-        for (int k = 0; k + 1 < R; ++k) win[k + 1] = row[swz32(x0 + k)];
-#pragma unroll R
-        for (int t = 0; t <= 2 * r; ++t) {
-#pragma unroll
-            for (int k = 0; k + 1 < R; ++k) win[k] = win[k + 1];
-            win[R - 1] = row[swz32(x0 + t + R - 1)];
-            const float g = w.g[t];
-#pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] = fmaf(g, win[k], acc[k]);
-        }
+        float acc[R];
+        gauss_window<R, RAD>(w, r, [&](int i) { return row[swz32(x0 + i)]; }, acc);
         float *o = dens + ((size_t)(j0 + y) << log2N) + x0;
         float *so = s_rows + ((size_t)y << log2N) + x0;
 #pragma unroll
@@ -1839,12 +1829,12 @@ __global__ void __launch_bounds__(CPT == 1 ? 64 : 512) band_fused_kernel(BandArg
 // Batched wrappers: panel blockIdx.y (blockIdx.z for the smoothing tiles) of
 // a PanelDesc table
 // ------------------------------------------------------------------------
-template <int TS, int R>
+template <int TS, int R, int RAD>
 __global__ void __launch_bounds__(256) smooth_batched_kernel(const PanelDesc *__restrict__ tab, int log2N, GaussW w,
                                                              int cur, int zero_next)
 {
     const PanelDesc &d = tab[blockIdx.z];
-    smooth_win_body<TS, R>(d.counts[cur], d.dens, log2N, w, zero_next ? d.counts[cur ^ 1] : nullptr);
+    smooth_win_body<TS, R, RAD>(d.counts[cur], d.dens, log2N, w, zero_next ? d.counts[cur ^ 1] : nullptr);
 }
 
 template <int MODE, int CPT, bool FINAL>
@@ -1928,29 +1918,53 @@ static cudaError_t allow_band2_smem_all()
     return e;
 }
 
+// dynamic shared memory of the smoothing kernels of one radius instantiation
+template <int RAD>
+static cudaError_t allow_smooth_smem()
+{
+    const int rmax = RAD >= 0 ? RAD : 64;
+    cudaError_t e = cudaFuncSetAttribute(smooth_win_kernel<64, 8, RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smooth_win_smem_bytes(64, rmax));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(smooth_win_kernel<32, 8, RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smooth_win_smem_bytes(32, rmax));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(smooth_batched_kernel<64, 8, RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smooth_win_smem_bytes(64, rmax));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(smooth_batched_kernel<32, 8, RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smooth_win_smem_bytes(32, rmax));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(smooth_agg_kernel<4, 4, RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmoothAggSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(smooth_agg_kernel<4, 8, RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmoothAggSmemMax);
+    return e;
+}
+
+// F(RAD) for the smoothing instantiation of radius r
+#define DC_RADIUS_DISPATCH(r, F)                                                                                      \
+    switch (r) {                                                                                                     \
+    case 2: F(2);                                                                                                    \
+    case 4: F(4);                                                                                                    \
+    case 8: F(8);                                                                                                    \
+    case 16: F(16);                                                                                                  \
+    case 32: F(32);                                                                                                  \
+    default: F(-1);                                                                                                  \
+    }
+
 cudaError_t prepare_kernels()
 {
     // dynamic shared memory of the smoothing tile for the largest radius
     cudaError_t e = cudaFuncSetAttribute(smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smooth_smem_bytes(64));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(smooth_win_kernel<64, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smooth_win_smem_bytes(64, 64));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(smooth_win_kernel<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smooth_win_smem_bytes(32, 64));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(smooth_batched_kernel<64, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smooth_win_smem_bytes(64, 64));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(smooth_batched_kernel<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smooth_win_smem_bytes(32, 64));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(smooth_agg_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmoothAggSmemMax);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(smooth_agg_kernel<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmoothAggSmemMax);
+    if (e == cudaSuccess) e = allow_smooth_smem<-1>();
+    if (e == cudaSuccess) e = allow_smooth_smem<2>();
+    if (e == cudaSuccess) e = allow_smooth_smem<4>();
+    if (e == cudaSuccess) e = allow_smooth_smem<8>();
+    if (e == cudaSuccess) e = allow_smooth_smem<16>();
+    if (e == cudaSuccess) e = allow_smooth_smem<32>();
     if (e == cudaSuccess) e = allow_band2_smem_all<MODE_COUNT>();
     if (e == cudaSuccess) e = allow_band2_smem_all<MODE_FLOAT>();
     if (e == cudaSuccess) e = allow_band2_smem_all<MODE_GRID64>();
@@ -1966,9 +1980,13 @@ cudaError_t launch_smooth(cudaStream_t s, const uint32_t *counts, float *dens, i
         const int TS = smooth_tile(log2N);
         const size_t bytes = (size_t)smooth_win_smem_bytes(TS, w.r);
         const dim3 grid(N / TS, N / TS);
-        if (TS == 64)
-            return launch_kernel(smooth_win_kernel<64, 8>, grid, dim3(256), bytes, s, counts, dens, log2N, w, zero_out);
-        return launch_kernel(smooth_win_kernel<32, 8>, grid, dim3(256), bytes, s, counts, dens, log2N, w, zero_out);
+#define DC_LAUNCH_WIN(RAD)                                                                                            \
+    return TS == 64 ? launch_kernel(smooth_win_kernel<64, 8, RAD>, grid, dim3(256), bytes, s, counts, dens, log2N, w,  \
+                                    zero_out)                                                                         \
+                    : launch_kernel(smooth_win_kernel<32, 8, RAD>, grid, dim3(256), bytes, s, counts, dens, log2N, w,  \
+                                    zero_out)
+        DC_RADIUS_DISPATCH(w.r, DC_LAUNCH_WIN)
+#undef DC_LAUNCH_WIN
     }
     const int TW = N;
     const int bytes = smooth_smem_bytes(w.r);
@@ -1999,11 +2017,14 @@ cudaError_t launch_smooth_agg(cudaStream_t s, const BandGeom &g, const BandArgs 
     if (!smooth_agg_available(g, w)) return cudaErrorInvalidValue;
     const size_t smem = smooth_agg_smem_bytes(g, w.r);
     const int nt = 4 * g.NT < 1024 ? 4 * g.NT : 1024;  // g.NT = N / 4 band threads
-    if (smooth_agg_R(g.T) == 4)
-        return launch_kernel(smooth_agg_kernel<4, 4>, dim3(g.nb), dim3(nt), smem, s, a, g.log2N, g.T, w, counts,
-                             dens, zero_out);
-    return launch_kernel(smooth_agg_kernel<4, 8>, dim3(g.nb), dim3(nt), smem, s, a, g.log2N, g.T, w, counts, dens,
-                         zero_out);
+    const bool r4 = smooth_agg_R(g.T) == 4;
+#define DC_LAUNCH_AGG(RAD)                                                                                            \
+    return r4 ? launch_kernel(smooth_agg_kernel<4, 4, RAD>, dim3(g.nb), dim3(nt), smem, s, a, g.log2N, g.T, w, counts,  \
+                              dens, zero_out)                                                                         \
+              : launch_kernel(smooth_agg_kernel<4, 8, RAD>, dim3(g.nb), dim3(nt), smem, s, a, g.log2N, g.T, w, counts,  \
+                              dens, zero_out)
+    DC_RADIUS_DISPATCH(w.r, DC_LAUNCH_AGG)
+#undef DC_LAUNCH_AGG
 }
 
 // Ring slots of the interleaved kernels: up to 128 KB of rows for the
@@ -2200,11 +2221,12 @@ cudaError_t launch_smooth_batched(cudaStream_t s, const PanelDesc *tab, int P, i
     const int TS = smooth_tile(log2N);
     const size_t bytes = (size_t)smooth_win_smem_bytes(TS, w.r);
     const dim3 grid(N / TS, N / TS, P);
-    if (TS == 64)
-        return launch_kernel(smooth_batched_kernel<64, 8>, grid, dim3(256), bytes, s, tab, log2N, w, cur,
-                             zero_next ? 1 : 0);
-    return launch_kernel(smooth_batched_kernel<32, 8>, grid, dim3(256), bytes, s, tab, log2N, w, cur,
-                         zero_next ? 1 : 0);
+    const int zn = zero_next ? 1 : 0;
+#define DC_LAUNCH_BAT(RAD)                                                                                            \
+    return TS == 64 ? launch_kernel(smooth_batched_kernel<64, 8, RAD>, grid, dim3(256), bytes, s, tab, log2N, w, cur, zn) \
+                    : launch_kernel(smooth_batched_kernel<32, 8, RAD>, grid, dim3(256), bytes, s, tab, log2N, w, cur, zn)
+    DC_RADIUS_DISPATCH(w.r, DC_LAUNCH_BAT)
+#undef DC_LAUNCH_BAT
 }
 
 template <int MODE, int CPT>

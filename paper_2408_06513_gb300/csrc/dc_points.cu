@@ -378,26 +378,42 @@ __device__ __forceinline__ int sample_pixel(float2 z, int log2N, float fN)
 // [prefix(p), prefix(p) + counts(p)), so every slot < n when cursor and rank
 // come from the splat of these same samples; a slot out of range sets
 // DC_ERR_RANGE in the status word and is skipped.
+//
+// Only slots in [lo, hi) are written by one launch: the sorted array is
+// filled in windows small enough to stay in L2, so that the 8-byte writes
+// to random slots of a window merge there into whole sectors before they
+// reach DRAM (a sector written piecemeal after eviction costs a DRAM
+// read-modify-write per sample).  The first window's launch (first = 1)
+// computes the slots and stores them in inv; the later ones read them back.
+// Sources are read with the streaming (evict-first) hint to spare the
+// window's lines.
 __device__ __forceinline__ void reorder_scatter_body(const float2 *__restrict__ pos, int64_t n,
                                                                    int log2N, const uint32_t *__restrict__ cursor,
                                                                    const uint32_t *__restrict__ rank,
                                                                    float2 *__restrict__ spos,
                                                                    uint32_t *__restrict__ inv,
-                                                                   unsigned *__restrict__ status)
+                                                                   unsigned *__restrict__ status, int64_t lo,
+                                                                   int64_t hi, int first)
 {
     pdl_wait();
     const float fN = (float)(1 << log2N);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-        const float2 z = pos[k];
-        const uint32_t slot = __ldg(&cursor[sample_pixel(z, log2N, fN)]) + rank[k];
-        if ((int64_t)slot < n) {
-            spos[slot] = z;
+        const float2 z = __ldcs(pos + k);
+        uint32_t slot;
+        if (first) {
+            slot = __ldg(&cursor[sample_pixel(z, log2N, fN)]) + __ldcs(rank + k);
+            if ((int64_t)slot >= n) {
+                inv[k] = 0xffffffffu;
+                atomicOr(status, (unsigned)DC_ERR_RANGE);
+                continue;
+            }
             inv[k] = slot;
         } else {
-            inv[k] = 0xffffffffu;
-            atomicOr(status, (unsigned)DC_ERR_RANGE);
+            slot = __ldcs(inv + k);
+            if ((int64_t)slot >= n) continue;  // reported by the first launch
         }
+        if ((int64_t)slot >= lo && (int64_t)slot < hi) spos[slot] = z;
     }
 }
 __global__ void __launch_bounds__(kThreads) reorder_scatter_kernel(const float2 *__restrict__ pos, int64_t n,
@@ -405,9 +421,10 @@ __global__ void __launch_bounds__(kThreads) reorder_scatter_kernel(const float2 
                                                                    const uint32_t *__restrict__ rank,
                                                                    float2 *__restrict__ spos,
                                                                    uint32_t *__restrict__ inv,
-                                                                   unsigned *__restrict__ status)
+                                                                   unsigned *__restrict__ status, int64_t lo,
+                                                                   int64_t hi, int first)
 {
-    reorder_scatter_body(pos, n, log2N, cursor, rank, spos, inv, status);
+    reorder_scatter_body(pos, n, log2N, cursor, rank, spos, inv, status, lo, hi, first);
 }
 
 // pos[k] = spos[inv[k]]
@@ -587,12 +604,21 @@ cudaError_t launch_splat_rank(cudaStream_t s, const float2 *pos, int64_t n, uint
                          counts, log2N, rank);
 }
 
+// Slots a scatter window holds: 32 MB of samples, a quarter of the L2.
+constexpr int64_t kScatterWindow = (int64_t)(32 << 20) / sizeof(float2);
+
 cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n, int log2N, const uint32_t *cursor,
                                    const uint32_t *rank, float2 *spos, uint32_t *inv, unsigned *status)
 {
     if (n <= 0) return cudaSuccess;
-    return launch_kernel(reorder_scatter_kernel, dim3(grid_for(n, kThreads, device_sms() * 8)), dim3(kThreads), 0, s, pos, n,
-                         log2N, cursor, rank, spos, inv, status);
+    const int64_t passes = (n + kScatterWindow - 1) / kScatterWindow;
+    const int64_t win = (n + passes - 1) / passes;
+    const dim3 grid(grid_for(n, kThreads, device_sms() * 8));
+    cudaError_t e = cudaSuccess;
+    for (int64_t p = 0; p < passes && e == cudaSuccess; ++p)
+        e = launch_kernel(reorder_scatter_kernel, grid, dim3(kThreads), 0, s, pos, n, log2N, cursor, rank, spos, inv,
+                          status, p * win, p + 1 == passes ? n : (p + 1) * win, p == 0 ? 1 : 0);
+    return e;
 }
 
 cudaError_t launch_reorder_back(cudaStream_t s, const float2 *spos, const uint32_t *inv, int64_t n, float2 *pos,
@@ -647,7 +673,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_batched_kernel(const 
 __global__ void __launch_bounds__(kThreads) scatter_batched_kernel(const PanelDesc *__restrict__ tab, int log2N)
 {
     const PanelDesc &d = tab[blockIdx.y];
-    reorder_scatter_body(d.pos, d.n, log2N, d.cursor, d.rank, d.spos, d.inv, d.status);
+    reorder_scatter_body(d.pos, d.n, log2N, d.cursor, d.rank, d.spos, d.inv, d.status, 0, d.n, 1);
 }
 template <bool RUNS>
 __global__ void __launch_bounds__(kThreads) advect_batched_kernel(const PanelDesc *__restrict__ tab, int log2N,
