@@ -74,7 +74,11 @@ enum {
 typedef struct {
     uint32_t log2_res;       /* N = 1 << log2_res, 4..13 */
     int32_t kernel_r;        /* Gaussian taps |k| <= r (Sec. 4.1): 0 = no smoothing,
-                                exact integer mode; < 0 = N/128, at least 2; max 64, < N */
+                                exact integer mode (any N); < 0 = N/128, at least 2;
+                                max 64, < N.  r > 0 (float mode) needs N <= 2048:
+                                there its displacement is within 1e-4 px of FP64;
+                                above, the FP32 region sums alone err by about
+                                2^-24 N / 2 px, and creation fails */
     float sigma;             /* Gaussian width; <= 0 = r / 3 */
     float d0;                /* regularising constant of eq. (d0); < 0 = n / N^2 */
     int32_t pixel_center;    /* 0: pixel at (i, j)/N; 1: at (i + 1/2, j + 1/2)/N */
@@ -211,10 +215,15 @@ dc_status displacement_field(dc_ctx *ctx, float *disp_xy_out);
  *   density_mean: a hint that centres the float sums (the density's mean,
  *                 or 0); the mapping does not depend on it, only the
  *                 rounding does.
- * Float arithmetic as in displacement_field.  Asynchronous.  Errors:
- * DC_ERR_INVALID_ARG for a null or misaligned pointer or a negative or
- * non-finite density_mean (nothing is launched); DC_ERR_CUDA for a failed
- * launch. */
+ * Float arithmetic as in displacement_field, N <= 2048.  With the
+ * density's mean as density_mean the pixel position cancels in exact
+ * integers before any rounding and the result is within 1e-4 px of FP64;
+ * with 0, t is formed as an O(1) float first (about 6 N 2^-24 px).  A
+ * density without mass has no mapping: the field is written as zero and the
+ * status word reports DC_ERR_INVALID_ARG.  Asynchronous.  Errors:
+ * DC_ERR_INVALID_ARG for a null or misaligned pointer, a negative or
+ * non-finite density_mean or N > 2048 (nothing is launched); DC_ERR_CUDA for
+ * a failed launch. */
 dc_status lens_field(dc_ctx *ctx, const float *density, float density_mean, float *disp_xy_out);
 
 /* Contour lines of a density (Sec. 5: the original density's contours,

@@ -16,6 +16,9 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// largest grid of the float (smoothed-density) integral images
+constexpr int kFloatMaxN = 2048;
+
 dc_status fail(dc_status s, const char *fmt, ...)
 {
     char buf[512];
@@ -552,6 +555,13 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
     int r = p.kernel_r;
     if (r < 0) r = N / 128 < 2 ? 2 : N / 128;
     if (r > 64 || r >= N) return fail(DC_ERR_INVALID_ARG, "kernel_r = %d (max 64, < N)", r);
+    // float (smoothed) mode keeps its 1e-4 px bound against FP64 only up to
+    // 2048^2: above, the FP32 region sums alone err by about 2^-24 N / 2 px
+    if (r > 0 && N > kFloatMaxN)
+        return fail(DC_ERR_INVALID_ARG,
+                    "float (smoothed) mode is limited to N <= %d (its FP32 sums miss the 1e-4 px bound above); "
+                    "kernel_r = 0 gives the exact integer mode at any N",
+                    kFloatMaxN);
     if (p.pixel_center != 0 && p.pixel_center != 1) return fail(DC_ERR_INVALID_ARG, "pixel_center");
     if (p.clamp_positions != 0 && p.clamp_positions != 1) return fail(DC_ERR_INVALID_ARG, "clamp_positions");
     if (p.carry_mode != DC_CARRY_COMPENSATED && p.carry_mode != DC_CARRY_F64)
@@ -799,6 +809,7 @@ dc_status lens_field(dc_ctx *c, const float *density, float density_mean, float 
     if (disp_out && !aligned(disp_out, 16)) return fail(DC_ERR_INVALID_ARG, "output must be 16-byte aligned");
     if (!(density_mean >= 0.f) || !std::isfinite(density_mean))
         return fail(DC_ERR_INVALID_ARG, "density_mean = %g", (double)density_mean);
+    if (c->g.N > kFloatMaxN) return fail(DC_ERR_INVALID_ARG, "lens_field runs the float passes: N <= %d", kFloatMaxN);
     DeviceGuard guard(c->device);
     // float-mode band passes over the caller's grid; mu = the mean hint only
     // centres the sums (any constant gives the same mapping), d0 = 0

@@ -617,19 +617,34 @@ def test_student_t_2048_full_size_one_iteration(dc, carry_mode):
         dc.declutter_destroy(ctx)
 
 
-@pytest.mark.parametrize("r", [0, 8])
-def test_largest_grid_8192_one_iteration(dc, r):
-    # the largest resolution (8192 x 8192): counts bit-exact, the field and
-    # the moved samples against the oracle (exact mode and a float radius).
-    # Float mode: the FP32 region sums bound the field's error by about
-    # eps_f32 * N / 2 pixel, so the 1e-4 px bound of the 512^2 and 2048^2
-    # workloads scales with N / 2048 here (measured: 3.3e-4 px).
+def test_largest_grid_8192_one_iteration(dc):
+    # the largest resolution (8192 x 8192) in exact mode: counts bit-exact,
+    # the field and the moved samples against the oracle
     z, _ = synth.student_t_clusters(2_000_000, seed=5)
-    p = oracle.Params(log2_res=13, kernel_r=r)
-    ctx = dc.declutter_create(13, kernel_r=r)
+    p = oracle.Params(log2_res=13, kernel_r=0)
+    ctx = dc.declutter_create(13, kernel_r=0)
     try:
-        err = check_iteration(dc, ctx, z, p, exact_disp=(r == 0), disp_tol_px=DISP_TOL_PX * 8192 / 2048)
-        print(f"8192^2 r={r}: max |D - D_fp64| = {err:.3e} px")
+        err = check_iteration(dc, ctx, z, p, exact_disp=True)
+        print(f"8192^2 exact: max |D - D_fp64| = {err:.3e} px")
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+@pytest.mark.parametrize("k", [12, 13])
+def test_float_mode_above_2048_is_refused(dc, k):
+    # float (smoothed) mode holds the 1e-4 px bound up to 2048^2; above, the
+    # FP32 region sums alone err by about 2^-24 N / 2 px, so contexts and
+    # the lens refuse it (exact mode runs at every size)
+    with pytest.raises(dc.DeclutterError) as ei:
+        dc.declutter_create(k, kernel_r=8)
+    assert ei.value.status == 1 and "kernel_r = 0" in dc.declutter_last_error()
+    with pytest.raises(dc.DeclutterError):
+        dc.declutter_create(k)  # the automatic radius N / 128
+    ctx = dc.declutter_create(k, kernel_r=0)
+    try:
+        N = 1 << k
+        with pytest.raises(dc.DeclutterError):
+            dc.lens_field(ctx, torch.ones(N * N, dtype=torch.float32, device=DEV), 1.0)
     finally:
         dc.declutter_destroy(ctx)
 
@@ -890,7 +905,7 @@ def test_contour_segments_match_oracle(dc, k, kind, pixel_center):
     rng = np.random.default_rng(k)
     cells = np.arange(M * M) if N <= 128 else np.unique(np.concatenate([
         rng.integers(0, M * M, size=4000), np.arange(M * 700, M * 702), np.arange(M * M - 2 * M, M * M)]))
-    ctx = dc.declutter_create(k, kernel_r=2, pixel_center=pixel_center)
+    ctx = dc.declutter_create(k, kernel_r=0, pixel_center=pixel_center)
     try:
         fg = torch.from_numpy(f).to(DEV)
         for lv in levels:
