@@ -469,6 +469,8 @@ def run_gpu(args, world, rank, local, pg):
     lens = None if args.no_inim_sweep else run_lens(args, dc, dev, stream, flush)
     contours = None if args.no_inim_sweep else run_contours(args, dc, dev, stream, flush)
     surrogate = None if args.surrogate_budget <= 0 else run_surrogate(args, dc, dev)
+    c3 = None if args.no_c3 else run_c3(args, dc, dev, stream, flush)
+    rows = None if args.no_rows else run_rows(args, dc, dev, stream, flush)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -493,9 +495,162 @@ def run_gpu(args, world, rank, local, pg):
             "contours": contours,
             "batched": batched,
             "surrogate": surrogate,
+            "student_t_2048": c3,
+            "rows": rows,
             "clocks": clocks.summary(),
         }
         print(json.dumps(line), flush=True)
+
+
+def event_ms(fn, stream, reps: int, before=None):
+    """Mean CUDA-event time of fn() on stream over reps runs (after one
+    untimed run); before() runs ahead of each, outside the timed span."""
+    import torch
+    times = []
+    for r in range(reps + 1):
+        if before:
+            with torch.cuda.stream(stream):
+                before()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        if r:
+            times.append(a.elapsed_time(b))
+    return sum(times) / len(times)
+
+
+def run_c3(args, dc, dev, stream, flush, reps: int = 8):
+    """The 16M-sample Student-t workload at 2048x2048, r = 16, 8 iterations:
+    step time, per-kernel in-graph times and the advection's fraction of the
+    HBM roofline (inputs larger than L2)."""
+    import torch
+    import synth
+    w = WORKLOADS["student_t_2048"]
+    n, k, r, iters = w["n"], w["log2_res"], w["kernel_r"], w["iters"]
+    N = 1 << k
+    z, _ = synth.student_t_clusters(n, seed=3)
+    ctx = dc.declutter_create(k, kernel_r=r, stream=stream)
+    try:
+        info = dc.declutter_get_info(ctx)
+        src = torch.from_numpy(z).to(dev)
+        pos = torch.empty_like(src)
+        torch.cuda.synchronize()
+        ms = event_ms(lambda: dc.regularize(ctx, pos, iters), stream, reps,
+                      before=lambda: (pos.copy_(src), flush()))
+        prof = dc.declutter_profile_regularize(ctx, pos, iters, reps=reps, reset_src=src)
+        dc.declutter_sync(ctx)
+    finally:
+        dc.declutter_destroy(ctx)
+    peaks, peak_src = measured_peaks()
+    kernels = {}
+    for kname, v in prof["kernels"].items():
+        if v["launches"] == 0:
+            continue
+        avg_ms = v["ms"] / v["launches"]
+        by = algorithmic_bytes(kname, n, N, info)
+        kernels[kname] = {"avg_us": avg_ms * 1e3, "launches_per_step": v["launches"],
+                          "share": v["ms"] / max(prof["step_ms"], 1e-9),
+                          "GBps": by / max(avg_ms * 1e-3, 1e-12) / 1e9}
+    adv = kernels["advect"]
+    return {"workload": w["text"], "ms_per_step": ms, "value": n * iters / (ms * 1e-3) / 1e6, "unit": METRIC,
+            "kernels": kernels,
+            "roofline_advect": {"bound": "hbm", "achieved": adv["GBps"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                "frac": adv["GBps"] / peaks["hbm_gbs"], "peak_source": peak_src,
+                                "algorithmic_bytes_per_launch": algorithmic_bytes("advect", n, N, info)},
+            "l2": "inputs larger than L2 (128 MB of samples), positions reset before each step"}
+
+
+def run_rows(args, dc, dev, stream, flush, reps: int = 10):
+    """Timings of the rows around the iteration: the stopping criteria in one
+    graph launch, the transition blend, the layout measures, the warped
+    density texture and the sample-sharded steps (two shards on one GPU)."""
+    import torch
+    import synth
+    from paper_2408_06513_gb300 import sharded
+    peaks, _ = measured_peaks()
+    out = {}
+    z, _ = synth.gmm20()
+    n = z.shape[0]
+    ctx = dc.declutter_create(9, kernel_r=4, stream=stream)
+    try:
+        src = torch.from_numpy(z).to(dev)
+        pos = torch.empty_like(src)
+        torch.cuda.synchronize()
+        reset = lambda: (pos.copy_(src), flush())
+        fixed = event_ms(lambda: dc.regularize(ctx, pos, 8), stream, reps, before=reset)
+        adapt = event_ms(lambda: dc.regularize_adaptive(ctx, pos, 8), stream, reps, before=reset)
+        with torch.cuda.stream(stream):
+            reset()
+        full = dc.regularize_adaptive(ctx, pos, 8)
+        tgt = 0.5 * (full["cv"][3] + full["cv"][4])
+        early = event_ms(lambda: dc.regularize_adaptive(ctx, pos, 8, target_cv=tgt), stream, reps, before=reset)
+        out["adaptive"] = {"workload": "gmm20_512", "ms_fixed_8": fixed, "ms_adaptive_8": adapt,
+                           "ms_adaptive_stopped_at_5": early,
+                           "note": "regularize_adaptive synchronises and reads its measures back; one graph launch"}
+        # transition blend: 16M samples, 24 B a sample (two reads, one write)
+        big = torch.rand(16_000_000, 2, device=dev)
+        big2 = torch.rand(16_000_000, 2, device=dev)
+        outp = torch.empty_like(big)
+        torch.cuda.synchronize()
+        ms = event_ms(lambda: dc.transition_positions(ctx, big, big2, 0.3, outp), stream, reps, before=flush)
+        gbs = 24 * 16e6 / (ms * 1e-3) / 1e9
+        out["transition"] = {"samples": 16_000_000, "us": ms * 1e3, "GBps": gbs, "frac": gbs / peaks["hbm_gbs"],
+                             "bytes_per_sample": 24}
+        del big, big2, outp
+        # layout measures of the 8-iteration layout, 256 queries, k = 10
+        with torch.cuda.stream(stream):
+            reset()
+        dc.regularize(ctx, pos, 8)
+        q = torch.from_numpy(np.random.default_rng(0).choice(n, 256, replace=False).astype(np.int32)).to(dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = dc.layout_metrics(ctx, src, pos, 10, queries=q)
+        t1 = time.perf_counter()
+        out["layout_metrics"] = {"samples": n, "queries": 256, "k": 10, "ms": (t1 - t0) * 1e3,
+                                 "trustworthiness": m["trustworthiness"], "ordering": m["ordering"]}
+        # sharded steps: two shards, the exchange an in-process sum
+        parts = [src[slice(*sharded.shard_bounds(n, 2, k))].clone() for k in range(2)]
+        grids = [torch.empty(512 * 512, dtype=torch.int32, device=dev) for _ in range(2)]
+        torch.cuda.synchronize()
+
+        def sharded_step():
+            for part, g in zip(parts, grids):
+                dc.splat_counts(ctx, part, g)
+            total = (grids[0] + grids[1])
+            dc.density_from_counts(ctx, total, n)
+            dc.displacement_field(ctx)
+            for part in parts:
+                dc.advect_samples(ctx, part)
+
+        with torch.cuda.stream(stream):
+            sh = event_ms(sharded_step, stream, reps)
+        out["sharded"] = {"workload": "gmm20_512", "shards": 2, "ms_per_iteration": sh,
+                          "ms_per_iteration_regularize": fixed / 8,
+                          "note": "step-by-step calls and an in-process sum of the grids (one GPU)"}
+    finally:
+        dc.declutter_destroy(ctx)
+    # warped density texture: 2048^2 nodes moved by 8 iterations, 2048^2 raster
+    zs, _ = synth.student_t_clusters(4_000_000, seed=4)
+    ctx = dc.declutter_create(11, kernel_r=16, stream=stream)
+    try:
+        p2 = torch.from_numpy(zs).to(dev)
+        jj, ii = np.meshgrid(np.arange(2048), np.arange(2048), indexing="ij")
+        nodes = torch.from_numpy(np.stack([ii / 2048, jj / 2048], -1).reshape(-1, 2).astype(np.float32)).to(dev)
+        torch.cuda.synchronize()
+        dc.regularize_tracers(ctx, p2, nodes, 8)
+        dens = torch.empty(2048 * 2048, device=dev)
+        dc.splat_density(ctx, torch.from_numpy(zs).to(dev), density_out=dens)
+        img = torch.empty(2048 * 2048, device=dev)
+        torch.cuda.synchronize()
+        ms = event_ms(lambda: dc.warp_texture(ctx, nodes, dens, 11, img, mass=True), stream, reps, before=flush)
+        out["warp_texture"] = {"nodes": "2048^2", "raster": "2048^2", "us": ms * 1e3,
+                               "note": "coverage pass (one thread per triangle) and shading pass"}
+    finally:
+        dc.declutter_destroy(ctx)
+    return out
 
 
 def run_inim_sweep(args, dc, dev, stream, flush, reps: int = 15):
@@ -882,6 +1037,9 @@ def main():
     ap.add_argument("--surrogate-budget", type=float, default=60.0,
                     help="seconds of surrogate training before its comparison (0 skips it)")
     ap.add_argument("--surrogate-pairs", type=int, default=4000)
+    ap.add_argument("--no-c3", action="store_true", help="skip the 16M-sample 2048x2048 measurement")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the stopping-criteria, transition, layout-measure, texture and sharding timings")
     ap.add_argument("--ncu-inim", type=int, default=0, metavar="LOG2",
                     help="profiler capture of the standalone integral images of a 2^LOG2 grid: "
                          "warm-up plus --steps launches, no bench line")
