@@ -981,9 +981,11 @@ def run_surrogate(args, dc, dev):
             return (time.perf_counter() - a) * 1e3, r
 
         rows = []
-        n = 2_000_000
-        mean = n / (256 // 4) ** 2
-        for t in range(4):
+        # held-out mixtures at the largest training size (2M samples), and at
+        # 16M samples, where a plain iteration costs about 8x more while the
+        # surrogate's pass depends on the grid only
+        for t, n in enumerate([2_000_000] * 4 + [16_000_000] * 2):
+            mean = n / (256 // 4) ** 2
             r2 = np.random.default_rng(700 + t)
             z = SG.gmm_samples(n, int(r2.integers(2, 31)), r2, dev)
             u = dc.regularize(ctx, z.clone(), 8, uniformity=True)
@@ -998,12 +1000,15 @@ def run_surrogate(args, dc, dev):
             ms_plain_eq = wall(lambda: dc.regularize(ctx, z.clone(), max(worth, 1)))[0] if worth else 0.0
             ms_plain8 = wall(lambda: dc.regularize(ctx, z.clone(), 8))[0]
             ms_fb, (used, cv_fb) = wall(lambda: dc.surrogate_apply(ctx, sg, z.clone(), target_cv, 16))
-            rows.append({"cv0_plain": cv_plain[0], "cv_plain8": cv_plain[-1], "cv_surrogate": cv_sg,
+            rows.append({"samples": n, "cv0_plain": cv_plain[0], "cv_plain8": cv_plain[-1], "cv_surrogate": cv_sg,
                          "worth_plain_iters": worth, "ms_surrogate_pass": ms_sg, "ms_plain_equal_quality": ms_plain_eq,
                          "ms_plain8": ms_plain8, "ms_surrogate_to_plain8_quality": ms_fb, "fallback_plain_iters": used,
                          "cv_after_fallback": cv_fb})
         tensor = surrogate_tensor_rate(dc, sg, dens, scales, field, target)
-        avg = lambda k: float(np.mean([r[k] for r in rows]))  # noqa: E731
+        avg = lambda k, n=2_000_000: float(np.mean([r[k] for r in rows if r["samples"] == n]))  # noqa: E731
+        at16 = {k: avg(k, 16_000_000) for k in ("worth_plain_iters", "ms_surrogate_pass", "ms_plain_equal_quality",
+                                                 "ms_plain8", "ms_surrogate_to_plain8_quality",
+                                                 "fallback_plain_iters")}
         return {"model": "conv encoder-decoder, 4 levels, 32/64/128/256 channels, 3x3, bf16 weights, fp32 accumulation; "
                          "input density + one iteration's field, output kappa * field + network",
                 "kappa": kappa, "skip_only_field_rms_px": skip_only["rms_px"],
@@ -1011,11 +1016,12 @@ def run_surrogate(args, dc, dev):
                 "train_s": t_train, "train_steps": losses[-1][0] + 1 if losses else 0, "batch": 16,
                 "loss_first": losses[0][1] if losses else None, "loss_last": losses[-1][1] if losses else None,
                 "field_rms_px": err["rms_px"], "field_target_rms_px": err["target_rms_px"],
-                "eval_samples": n, "worth_plain_iters_mean": avg("worth_plain_iters"),
+                "eval_samples": 2_000_000, "worth_plain_iters_mean": avg("worth_plain_iters"),
                 "ms_surrogate_pass": avg("ms_surrogate_pass"), "ms_plain_equal_quality": avg("ms_plain_equal_quality"),
                 "ms_plain8": avg("ms_plain8"), "ms_surrogate_to_plain8_quality": avg("ms_surrogate_to_plain8_quality"),
                 "fallback_plain_iters_mean": avg("fallback_plain_iters"),
-                "fixed_error": "bin std/mean within 1.05x of 8 plain iterations", "tensor": tensor, "cases": rows}
+                "fixed_error": "bin std/mean within 1.05x of 8 plain iterations", "at_16M_samples": at16,
+                "tensor": tensor, "cases": rows}
     finally:
         dc.declutter_destroy(ctx)
         dc.surrogate_destroy(sg)
@@ -1036,7 +1042,7 @@ def main():
     ap.add_argument("--no-inim-sweep", action="store_true", help="skip the standalone integral-image sweep")
     ap.add_argument("--surrogate-budget", type=float, default=60.0,
                     help="seconds of surrogate training before its comparison (0 skips it)")
-    ap.add_argument("--surrogate-pairs", type=int, default=4000)
+    ap.add_argument("--surrogate-pairs", type=int, default=50000)
     ap.add_argument("--no-c3", action="store_true", help="skip the 16M-sample 2048x2048 measurement")
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the stopping-criteria, transition, layout-measure, texture and sharding timings")
