@@ -6,7 +6,9 @@ their largest error within 2 % of the largest gradient, or within twice the
 oracle's own bfloat16-versus-FP64 difference when that is larger (two
 bfloat16 pipelines that sum in different orders can flip a rounding, each
 sits that far from the exact gradient, and the deepest layers of the 4-level
-network sit at that noise floor).  Then a short
+network sit at that noise floor).  On data where no rounding can act
+(weights in {-1, 0, 1}, small-integer inputs and targets) the output and
+every gradient must equal the oracle's exactly.  Then a short
 training run on pairs generated by the plain method shows what the network
 gains."""
 
@@ -164,3 +166,69 @@ def test_training_gains_over_untrained_and_over_no_iteration(dc, c_in):
     finally:
         dc.declutter_destroy(ctx)
         dc.surrogate_destroy(sg)
+
+
+def exact_problem(levels, c0, c_in, H, B, seed, dens=0.03):
+    """Weights in {-1, 0, 1} (sparser for wider layers), biases in
+    {-1/4, 0, 1/4}, inputs and targets small integers: every value the
+    network stores is a short binary fraction, exact in bfloat16, and every
+    sum is exact in FP32, so rounding plays no part on either side."""
+    rng = np.random.default_rng(seed)
+    P = {}
+    for name, co, ci in S.layer_shapes(levels, c0, c_in):
+        d = min(0.5, dens * 8 / ci) if ci > 1 else 0.5
+        P[name + ".w"] = rng.choice([-1.0, 0.0, 1.0], size=(co, 3, 3, ci), p=[d / 2, 1 - d, d / 2])
+        P[name + ".b"] = rng.choice([-0.25, 0.0, 0.25], size=(co,))
+    x = rng.integers(0, 2, size=(B, H, H)).astype(np.float64)
+    f = rng.integers(-1, 2, size=(B, H, H, 2)).astype(np.float64) if c_in == 3 else None
+    t = rng.integers(-1, 2, size=(B, H, H, 2)).astype(np.float64)
+    return P, x, f, t
+
+
+@pytest.mark.parametrize("levels,c0,c_in,seed,tc", [(2, 8, 1, 0, "0"), (3, 8, 1, 268, "0"), (2, 32, 1, 0, "1"),
+                                                   (2, 32, 3, 3, "1"), (2, 32, 3, 3, "0")])
+def test_gradients_exact_when_rounding_cannot_act(dc, levels, c0, c_in, seed, tc):
+    # Tighter than the bf16-noise bound above: on data where the oracle
+    # gives the same result with and without its bfloat16 roundings (checked
+    # here first) and every sum is exact in FP32, the GPU's output and every
+    # layer's weight and bias gradient must equal the oracle's exactly, in
+    # any summation order (an error in one tap of one layer shows at once).
+    H = 16 if levels == 2 else 32  # the grid needs levels + 2 halvings
+    B = 2 if c0 == 8 else 1
+    P, x, f, t = exact_problem(levels, c0, c_in, H, B, seed)
+    xin = x[..., None] if f is None else np.concatenate([x[..., None], f], -1)
+    ref_out, cache = S.forward(P, xin, levels)
+    out64, cache64 = S.forward(P, xin, levels, round_bf16=False)
+    assert np.array_equal(ref_out, out64)
+    _, dout = S.mse_loss(ref_out, t)
+    G = S.backward(cache, dout, levels)
+    G64 = S.backward(cache64, dout, levels, round_bf16=False)
+    for k in G:
+        assert np.array_equal(G[k], G64[k]), k
+        if k.endswith(".w"):
+            assert np.any(G[k]), k  # every layer's weights get a gradient
+    sg = dc.surrogate_create(H.bit_length() - 1, levels, c0, max_batch=B, seed=0, in_channels=c_in)
+    try:
+        dc.surrogate_set_tensor_path(sg, dc.DC_SG_TCGEN05 if tc == "1" else dc.DC_SG_MMA_SYNC)
+        w, b = flat_params(P, levels, c0, c_in)
+        dc.surrogate_set_params(sg, w, b)
+        xd = torch.from_numpy(x.astype(np.float32)).cuda()
+        fd = torch.from_numpy(f.astype(np.float32)).cuda() if f is not None else None
+        td = torch.from_numpy(t.astype(np.float32)).cuda()
+        out = torch.empty(B, H, H, 2, device="cuda")
+        dc.surrogate_forward(sg, xd, None, out, field=fd)
+        dc.surrogate_loss_grad(sg, xd, None, td, field=fd)
+        gw, gb = dc.surrogate_get_grads(sg)
+    finally:
+        dc.surrogate_destroy(sg)
+    o = out.cpu().numpy().astype(np.float64)
+    assert np.array_equal(o, ref_out)
+    g = split_params(gw.astype(np.float64), gb.astype(np.float64), levels, c0, c_in)
+    worst = 0.0
+    for name, _, _ in S.layer_shapes(levels, c0, c_in):
+        for kind in (".w", ".b"):
+            ref = G[name + kind]
+            err = float(np.max(np.abs(g[name + kind] - ref)))
+            worst = max(worst, err / max(np.max(np.abs(ref)), 1e-30))
+            assert err == 0.0, (name + kind, err, np.max(np.abs(ref)))
+    print(f"levels={levels} c0={c0} c_in={c_in} tcgen05={tc}: largest relative gradient error {worst:.2e}")
