@@ -456,11 +456,35 @@ dc_status declutter_batch_sync(dc_batch *batch);
  * 1, 2, 4, ... 64 with at most 1024 bands and for the automatic height, and
  * returns the fastest in
  * *best_out (its median time in *best_ms_out, or -1 when the answer came
- * from the cache).  Answers are cached per (device, resolution, radius, carry
- * mode, floor(log2 n)) for the life of the process.  The samples are not
+ * from the cache).  Answers are cached per (GPU model, resolution, radius,
+ * carry mode, keep_order, floor(log2 n)), see declutter_autotune_save.  The samples are not
  * modified.  Synchronises. */
 dc_status declutter_autotune_band_rows(const dc_params *params, int device, void *cuda_stream, const float *pos_xy,
                                        int64_t n, int32_t iters, int32_t *best_out, float *best_ms_out);
+
+/* The autotuner over band heights and launch sequences: times
+ * regularize(iters) on a copy of the samples for every band height 1, 2, 4,
+ * .. 64 (at most 1024 bands) and the automatic one, each with the default
+ * launch sequence, DC_OPT_SEPARATE_SMOOTH (float mode) and
+ * DC_OPT_FUSED_BANDS (below 2048 x 2048), and writes params with the
+ * fastest band_rows and options into *best_out (host).  The launch
+ * options never change the results; in float mode the band height changes
+ * the order of the float sums (every height within the float bound).  The
+ * answer is cached per (GPU model and SM count,
+ * resolution, radius, carry mode, keep_order, floor(log2 n)); *best_ms_out
+ * (host, or NULL) is the median time, -1 for a cached answer.  The samples
+ * are not modified.  Synchronises. */
+dc_status declutter_autotune(const dc_params *params, int device, void *cuda_stream, const float *pos_xy, int64_t n,
+                             int32_t iters, dc_params *best_out, float *best_ms_out);
+
+/* The autotuner's cache in a text file (host paths), so that tuned settings
+ * carry over to later runs on the same GPU model: save writes every entry,
+ * load adds the file's entries (DC_ERR_INVALID_ARG for an unreadable or
+ * malformed file, nothing added), clear empties the cache.  No device is
+ * used. */
+dc_status declutter_autotune_save(const char *path);
+dc_status declutter_autotune_load(const char *path);
+dc_status declutter_autotune_clear(void);
 
 /* Autotunes every resolution of a batch on its largest panel and rebuilds the
  * panels' contexts with the chosen band heights (band_rows_out: host

@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <string>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -84,9 +85,28 @@ struct Guard {
     }
 };
 
-// autotuned band heights: (device, log2 N, radius, carry mode, log2 of n) -> rows
+// Autotuned settings, per GPU model (name and SM count, so that a cache file
+// carries over to other runs and devices of the same model), resolution,
+// radius, carry mode, sample order, floor(log2 n) and whether the launch
+// options were searched: -> (band rows, options).
+using TuneKey = std::tuple<std::string, int, int, int, int, int, int, int>;
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+std::string gpu_model(int device, int *sms)
+{
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        cudaGetLastError();
+        *sms = 0;
+        return "unknown";
+    }
+    *sms = prop.multiProcessorCount;
+    std::string name = prop.name;
+    for (auto &ch : name)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    return name;
+}
 
 int n_bucket(int64_t n) { return n > 0 ? (int)std::floor(std::log2((double)n)) : 0; }
 
@@ -139,27 +159,39 @@ cudaError_t enqueue_class(const dc_ctx *c0, cudaStream_t s, const PanelDesc *tab
 
 extern "C" {
 
-dc_status declutter_autotune_band_rows(const dc_params *params, int device, void *cuda_stream, const float *pos_xy,
-                                       int64_t n, int32_t iters, int32_t *best_out, float *best_ms_out)
+}  // extern "C"
+
+namespace {
+
+// Times regularize(iters) on a copy of the samples for every band height
+// 1, 2, 4, .. 64 with at most 1024 bands and the automatic height, and, with
+// search_options, for each of the launch sequences (default, separate
+// smoothing in float mode, one cooperative band launch below 2048^2); keeps
+// the fastest (median of five runs after two warm-ups).
+dc_status tune(const dc_params *params, int device, void *cuda_stream, const float *pos_xy, int64_t n, int32_t iters,
+               bool search_options, int *best_rows, int *best_opts, float *best_ms_out)
 {
-    if (!params || !best_out) return bfail(DC_ERR_INVALID_ARG, "null params or best_out");
+    if (!params) return bfail(DC_ERR_INVALID_ARG, "null params");
     if (n <= 0 || !pos_xy || (reinterpret_cast<uintptr_t>(pos_xy) & 7)) return bfail(DC_ERR_INVALID_ARG, "samples");
     if (iters < 1) return bfail(DC_ERR_INVALID_ARG, "iters = %d", iters);
     if (params->log2_res < 4 || params->log2_res > 13) return bfail(DC_ERR_NOT_POW2, "log2_res");
     const int N = 1 << params->log2_res;
     const int r = params->kernel_r < 0 ? (N / 128 < 2 ? 2 : N / 128) : params->kernel_r;
-    const auto key = std::make_tuple(device, (int)params->log2_res, r, (int)params->carry_mode, n_bucket(n));
+    int sms = 0;
+    const std::string model = gpu_model(device, &sms);
+    const TuneKey key{model, sms, (int)params->log2_res, r, (int)params->carry_mode, (int)params->keep_order,
+                      n_bucket(n), search_options ? 1 : 0};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            *best_out = it->second;
+            *best_rows = it->second.first;
+            *best_opts = it->second.second;
             if (best_ms_out) *best_ms_out = -1.f;
             return DC_OK;
         }
     }
     Guard guard(device);
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     float *tmp = nullptr;
     if (cudaMalloc(&tmp, sizeof(float) * 2 * (size_t)n) != cudaSuccess) {
         cudaGetLastError();
@@ -168,52 +200,141 @@ dc_status declutter_autotune_band_rows(const dc_params *params, int device, void
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = 0;
+    int best = 0, best_o = params->options;
     float best_ms = 0.f;
     dc_status st = DC_OK;
+    const int base_opts = params->options & ~(DC_OPT_FUSED_BANDS | DC_OPT_SEPARATE_SMOOTH);
+    std::vector<int> opt_set{search_options ? base_opts : params->options};
+    if (search_options) {
+        if (r > 0) opt_set.push_back(base_opts | DC_OPT_SEPARATE_SMOOTH);
+        if (N < 2048) opt_set.push_back(base_opts | DC_OPT_FUSED_BANDS);
+    }
     // powers of two, then the automatic height (one band per SM)
     const int T_auto = make_band_geom(params->log2_res, 0, device_sms()).T;
-    for (int Tk = 1; Tk <= 128 && st == DC_OK; Tk *= 2) {
-        const int T = Tk <= 64 ? Tk : T_auto;
-        if (Tk > 64 && (T_auto & (T_auto - 1)) == 0) continue;  // already timed
-        if (T > N || (N + T - 1) / T > 1024) continue;
-        dc_params p = *params;
-        p.band_rows = T;
-        dc_ctx *c = nullptr;
-        if ((st = declutter_create(&p, device, cuda_stream, &c)) != DC_OK) break;
-        float ms[5];
-        for (int rep = -2; rep < 5 && st == DC_OK; ++rep) {
-            if (cudaMemcpyAsync(tmp, pos_xy, sizeof(float) * 2 * (size_t)n, cudaMemcpyDeviceToDevice, c->stream) !=
-                cudaSuccess) {
-                st = bfail(DC_ERR_CUDA, "autotune copy");
-                break;
+    for (int opts : opt_set) {
+        for (int Tk = 1; Tk <= 128 && st == DC_OK; Tk *= 2) {
+            const int T = Tk <= 64 ? Tk : T_auto;
+            if (Tk > 64 && (T_auto & (T_auto - 1)) == 0) continue;  // already timed
+            if (T > N || (N + T - 1) / T > 1024) continue;
+            dc_params p = *params;
+            p.band_rows = T;
+            p.options = opts;
+            dc_ctx *c = nullptr;
+            if ((st = declutter_create(&p, device, cuda_stream, &c)) != DC_OK) break;
+            float ms[5];
+            for (int rep = -2; rep < 5 && st == DC_OK; ++rep) {
+                if (cudaMemcpyAsync(tmp, pos_xy, sizeof(float) * 2 * (size_t)n, cudaMemcpyDeviceToDevice,
+                                    c->stream) != cudaSuccess) {
+                    st = bfail(DC_ERR_CUDA, "autotune copy");
+                    break;
+                }
+                cudaEventRecord(e0, c->stream);
+                st = regularize(c, tmp, n, iters, nullptr);
+                cudaEventRecord(e1, c->stream);
+                if (st == DC_OK && cudaEventSynchronize(e1) != cudaSuccess) st = bfail(DC_ERR_CUDA, "autotune sync");
+                if (st == DC_OK && rep >= 0) cudaEventElapsedTime(&ms[rep], e0, e1);
             }
-            cudaEventRecord(e0, c->stream);
-            st = regularize(c, tmp, n, iters, nullptr);
-            cudaEventRecord(e1, c->stream);
-            if (st == DC_OK && cudaEventSynchronize(e1) != cudaSuccess) st = bfail(DC_ERR_CUDA, "autotune sync");
-            if (st == DC_OK && rep >= 0) cudaEventElapsedTime(&ms[rep], e0, e1);
+            declutter_destroy(c);
+            if (st != DC_OK) break;
+            std::sort(ms, ms + 5);
+            if (!best || ms[2] < best_ms) {
+                best = T;
+                best_o = opts;
+                best_ms = ms[2];
+            }
         }
-        declutter_destroy(c);
         if (st != DC_OK) break;
-        std::sort(ms, ms + 5);
-        if (!best || ms[2] < best_ms) {
-            best = T;
-            best_ms = ms[2];
-        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(tmp);
-    (void)s;
     if (st != DC_OK) return st;
     if (!best) return bfail(DC_ERR_INVALID_ARG, "no band height fits");
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune_cache[key] = best;
+        g_tune_cache[key] = {best, best_o};
     }
-    *best_out = best;
+    *best_rows = best;
+    *best_opts = best_o;
     if (best_ms_out) *best_ms_out = best_ms;
+    return DC_OK;
+}
+
+constexpr const char *kTuneHeader = "declutter-autotune 1";
+
+}  // namespace
+
+extern "C" {
+
+dc_status declutter_autotune_band_rows(const dc_params *params, int device, void *cuda_stream, const float *pos_xy,
+                                       int64_t n, int32_t iters, int32_t *best_out, float *best_ms_out)
+{
+    if (!best_out) return bfail(DC_ERR_INVALID_ARG, "null best_out");
+    int rows = 0, opts = 0;
+    if (dc_status st = tune(params, device, cuda_stream, pos_xy, n, iters, false, &rows, &opts, best_ms_out)) return st;
+    *best_out = rows;
+    return DC_OK;
+}
+
+dc_status declutter_autotune(const dc_params *params, int device, void *cuda_stream, const float *pos_xy, int64_t n,
+                             int32_t iters, dc_params *best_out, float *best_ms_out)
+{
+    if (!best_out) return bfail(DC_ERR_INVALID_ARG, "null best_out");
+    int rows = 0, opts = 0;
+    if (dc_status st = tune(params, device, cuda_stream, pos_xy, n, iters, true, &rows, &opts, best_ms_out)) return st;
+    *best_out = *params;
+    best_out->band_rows = rows;
+    best_out->options = opts;
+    return DC_OK;
+}
+
+dc_status declutter_autotune_save(const char *path)
+{
+    if (!path) return bfail(DC_ERR_INVALID_ARG, "null path");
+    FILE *f = std::fopen(path, "w");
+    if (!f) return bfail(DC_ERR_INVALID_ARG, "cannot write %s", path);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    std::fprintf(f, "%s\n", kTuneHeader);
+    for (const auto &kv : g_tune_cache) {
+        const auto &k = kv.first;
+        std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d\n", std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k),
+                     std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k), std::get<7>(k), kv.second.first,
+                     kv.second.second);
+    }
+    const bool ok = std::fclose(f) == 0;
+    return ok ? DC_OK : bfail(DC_ERR_INVALID_ARG, "write error on %s", path);
+}
+
+dc_status declutter_autotune_load(const char *path)
+{
+    if (!path) return bfail(DC_ERR_INVALID_ARG, "null path");
+    FILE *f = std::fopen(path, "r");
+    if (!f) return bfail(DC_ERR_INVALID_ARG, "cannot read %s", path);
+    char line[512];
+    std::vector<std::pair<TuneKey, std::pair<int, int>>> got;
+    bool ok = std::fgets(line, sizeof(line), f) && std::strncmp(line, kTuneHeader, std::strlen(kTuneHeader)) == 0;
+    while (ok && std::fgets(line, sizeof(line), f)) {
+        char name[256];
+        int v[10];
+        if (std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %d", name, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+                        &v[7], &v[8]) != 10 ||
+            v[7] < 1 || v[7] > 64 || v[1] < 4 || v[1] > 13) {
+            ok = false;
+            break;
+        }
+        got.push_back({TuneKey{name, v[0], v[1], v[2], v[3], v[4], v[5], v[6]}, {v[7], v[8]}});
+    }
+    std::fclose(f);
+    if (!ok) return bfail(DC_ERR_INVALID_ARG, "%s is not a declutter autotune cache", path);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto &e : got) g_tune_cache[e.first] = e.second;
+    return DC_OK;
+}
+
+dc_status declutter_autotune_clear(void)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.clear();
     return DC_OK;
 }
 

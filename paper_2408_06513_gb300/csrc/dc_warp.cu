@@ -2,8 +2,9 @@
 // the mesh of pixel nodes after the nodes have been moved by the method's
 // mapping (e.g. as tracers of regularize_tracers), then mapped to colours by
 // a transfer function.  A plain two-pass rasteriser in CUDA: (1) one thread
-// per triangle of the deformed mesh marks the output pixels whose centres it
-// covers (fixed-point vertices with 8 sub-pixel bits, exact integer edge
+// per triangle of the deformed mesh (the whole warp for a triangle the
+// mapping expanded) marks the output pixels whose centres it covers
+// (fixed-point vertices with 8 sub-pixel bits, exact integer edge
 // functions, a fill rule that gives a point on a shared edge or vertex to
 // exactly one triangle, the lowest triangle index winning where triangles
 // overlap); (2) one thread per output pixel takes the texture at the source
@@ -69,41 +70,68 @@ __global__ void __launch_bounds__(kThreads) clear_u32_kernel(uint32_t *__restric
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) p[k] = v;
 }
 
+// Triangles whose bounding box holds at most kSmallBox pixel centres are
+// covered by their own thread; larger ones (cells the mapping expanded) by
+// the whole warp, one triangle after another, the lanes striding over its
+// box, so that one expanded cell does not hold up its warp.
+constexpr long long kSmallBox = 64;
+
 __global__ void __launch_bounds__(kThreads) warp_raster_kernel(const float2 *__restrict__ nodes, int N, int log2M,
                                                                uint32_t *__restrict__ cover)
 {
     pdl_wait();
     const uint32_t ntri = 2u * (uint32_t)(N - 1) * (uint32_t)(N - 1);
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ntri) return;
+    const int lane = threadIdx.x & 31;
     const int M = 1 << log2M;
     const float scale = (float)(1 << (log2M + kSub));
-    int ni[3], nj[3];
-    tri_nodes(t, N, ni, nj);
-    Fx a = fixed_vertex(nodes[nj[0] * N + ni[0]], scale);
-    Fx b = fixed_vertex(nodes[nj[1] * N + ni[1]], scale);
-    Fx c = fixed_vertex(nodes[nj[2] * N + ni[2]], scale);
-    const long long area = (b.x - a.x) * (c.y - a.y) - (b.y - a.y) * (c.x - a.x);
-    if (area == 0) return;
-    if (area < 0) {  // orient positively
-        const Fx s = b;
-        b = c;
-        c = s;
-    }
     const long long half = 1ll << (kSub - 1), one = 1ll << kSub;
-    const long long mnx = min(a.x, min(b.x, c.x)), mxx = max(a.x, max(b.x, c.x));
-    const long long mny = min(a.y, min(b.y, c.y)), mxy = max(a.y, max(b.y, c.y));
-    const long long p0 = max(0ll, (mnx - half + one - 1) >> kSub), p1 = min((long long)M - 1, (mxx - half) >> kSub);
-    const long long q0 = max(0ll, (mny - half + one - 1) >> kSub), q1 = min((long long)M - 1, (mxy - half) >> kSub);
-    const bool oab = owns(a, b), obc = owns(b, c), oca = owns(c, a);
-    for (long long q = q0; q <= q1; ++q) {
-        const long long py = (q << kSub) + half;
-        for (long long p = p0; p <= p1; ++p) {
-            const long long px = (p << kSub) + half;
-            const long long e0 = edge(a, b, px, py), e1 = edge(b, c, px, py), e2 = edge(c, a, px, py);
-            const bool in = (e0 > 0 || (e0 == 0 && oab)) && (e1 > 0 || (e1 == 0 && obc)) && (e2 > 0 || (e2 == 0 && oca));
-            if (in) atomicMin(&cover[(q << log2M) + p], t);
+    Fx a{0, 0}, b{0, 0}, c{0, 0};
+    long long p0 = 0, p1 = -1, q0 = 0, q1 = -1;
+    if (t < ntri) {
+        int ni[3], nj[3];
+        tri_nodes(t, N, ni, nj);
+        a = fixed_vertex(nodes[nj[0] * N + ni[0]], scale);
+        b = fixed_vertex(nodes[nj[1] * N + ni[1]], scale);
+        c = fixed_vertex(nodes[nj[2] * N + ni[2]], scale);
+        const long long area = (b.x - a.x) * (c.y - a.y) - (b.y - a.y) * (c.x - a.x);
+        if (area < 0) {  // orient positively
+            const Fx s = b;
+            b = c;
+            c = s;
         }
+        if (area != 0) {  // a degenerate triangle covers nothing: empty box
+            const long long mnx = min(a.x, min(b.x, c.x)), mxx = max(a.x, max(b.x, c.x));
+            const long long mny = min(a.y, min(b.y, c.y)), mxy = max(a.y, max(b.y, c.y));
+            p0 = max(0ll, (mnx - half + one - 1) >> kSub);
+            p1 = min((long long)M - 1, (mxx - half) >> kSub);
+            q0 = max(0ll, (mny - half + one - 1) >> kSub);
+            q1 = min((long long)M - 1, (mxy - half) >> kSub);
+        }
+    }
+    const long long box = (p1 >= p0 && q1 >= q0) ? (p1 - p0 + 1) * (q1 - q0 + 1) : 0;
+    auto cover_pixel = [&](const Fx &ta, const Fx &tb, const Fx &tc, uint32_t tri, long long p, long long q) {
+        const long long px = (p << kSub) + half, py = (q << kSub) + half;
+        const long long e0 = edge(ta, tb, px, py), e1 = edge(tb, tc, px, py), e2 = edge(tc, ta, px, py);
+        const bool in = (e0 > 0 || (e0 == 0 && owns(ta, tb))) && (e1 > 0 || (e1 == 0 && owns(tb, tc))) &&
+                        (e2 > 0 || (e2 == 0 && owns(tc, ta)));
+        if (in) atomicMin(&cover[(q << log2M) + p], tri);
+    };
+    if (box > 0 && box <= kSmallBox)
+        for (long long q = q0; q <= q1; ++q)
+            for (long long p = p0; p <= p1; ++p) cover_pixel(a, b, c, t, p, q);
+    unsigned big = __ballot_sync(0xffffffffu, box > kSmallBox);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const Fx ta{__shfl_sync(0xffffffffu, a.x, src), __shfl_sync(0xffffffffu, a.y, src)};
+        const Fx tb{__shfl_sync(0xffffffffu, b.x, src), __shfl_sync(0xffffffffu, b.y, src)};
+        const Fx tc{__shfl_sync(0xffffffffu, c.x, src), __shfl_sync(0xffffffffu, c.y, src)};
+        const long long bp0 = __shfl_sync(0xffffffffu, p0, src), bq0 = __shfl_sync(0xffffffffu, q0, src);
+        const long long bw = __shfl_sync(0xffffffffu, p1, src) - bp0 + 1;
+        const long long bbox = __shfl_sync(0xffffffffu, box, src);
+        const uint32_t tri = __shfl_sync(0xffffffffu, t, src);
+        for (long long k = lane; k < bbox; k += 32) cover_pixel(ta, tb, tc, tri, bp0 + k % bw, bq0 + k / bw);
     }
 }
 

@@ -33,7 +33,8 @@ __all__ = [
     "DC_OPT_TEST_UNREACHED_BARRIER", "DC_SG_MMA_SYNC", "DC_SG_TCGEN05",
     "integral_images_u32_noalloc", "DC_NOALLOC_MAX_LOG2_RES", "Batch", "declutter_batch_create",
     "declutter_batch_destroy", "declutter_batch_regularize", "declutter_batch_sync",
-    "declutter_autotune_band_rows", "declutter_batch_autotune", "regularize_tracers", "Surrogate",
+    "declutter_autotune_band_rows", "declutter_batch_autotune", "declutter_autotune", "declutter_autotune_save",
+    "declutter_autotune_load", "declutter_autotune_clear", "regularize_tracers", "Surrogate",
     "surrogate_create", "surrogate_destroy", "surrogate_num_params", "surrogate_get_params", "surrogate_set_params",
     "surrogate_get_grads", "surrogate_set_skip", "surrogate_set_tensor_path", "surrogate_forward", "surrogate_loss_grad", "surrogate_train_step", "surrogate_apply",
 ]
@@ -135,6 +136,11 @@ _SIGS = [
     ("declutter_autotune_band_rows", ctypes.c_int,
      [ctypes.POINTER(dc_params), ctypes.c_int, _P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]),
     ("declutter_batch_autotune", ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P]),
+    ("declutter_autotune", ctypes.c_int,
+     [ctypes.POINTER(dc_params), ctypes.c_int, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(dc_params), _P]),
+    ("declutter_autotune_save", ctypes.c_int, [ctypes.c_char_p]),
+    ("declutter_autotune_load", ctypes.c_int, [ctypes.c_char_p]),
+    ("declutter_autotune_clear", ctypes.c_int, []),
     ("regularize_tracers", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32]),
     ("surrogate_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_uint64, ctypes.c_int, _P, ctypes.POINTER(_P)]),
@@ -638,6 +644,34 @@ def declutter_autotune_band_rows(pos, iters: int, log2_res: int, device: int | N
                                                        n, int(iters), ctypes.byref(best), ctypes.byref(ms)),
            "declutter_autotune_band_rows")
     return int(best.value), float(ms.value)
+
+
+def declutter_autotune(pos, iters: int, log2_res: int, device: int | None = None, stream=None, **params):
+    """Tuned band height and launch options for these samples: returns
+    ``(band_rows, options, median_ms)`` (median -1 when cached)."""
+    import torch
+    lib = load_library()
+    if device is None:
+        device = torch.cuda.current_device()
+    pp, n = _pos_args(pos, device)
+    p = make_params(log2_res, **params)
+    best = dc_params()
+    ms = ctypes.c_float()
+    _check(lib.declutter_autotune(ctypes.byref(p), int(device), _stream_ptr(stream, device), pp, n, int(iters),
+                                  ctypes.byref(best), ctypes.byref(ms)), "declutter_autotune")
+    return int(best.band_rows), int(best.options), float(ms.value)
+
+
+def declutter_autotune_save(path: str) -> None:
+    _check(load_library().declutter_autotune_save(os.fsencode(path)), "declutter_autotune_save")
+
+
+def declutter_autotune_load(path: str) -> None:
+    _check(load_library().declutter_autotune_load(os.fsencode(path)), "declutter_autotune_load")
+
+
+def declutter_autotune_clear() -> None:
+    _check(load_library().declutter_autotune_clear(), "declutter_autotune_clear")
 
 
 def declutter_batch_autotune(batch: Batch, positions, iters: int):

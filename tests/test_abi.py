@@ -114,3 +114,30 @@ def test_surrogate_flop_count():
     assert len(layers) == 15
     assert sum(layers) == 17_704_157_184
     assert layers[0] == 2 * 65536 * 32 * 27 and layers[-1] == 2 * 65536 * 2 * 288
+
+
+def test_autotune_cache_file_round_trip(tmp_path):
+    # the autotuner's cache file (host only, no device needed): a file
+    # written by hand loads, saves back with the same entries, and a
+    # malformed file is refused without changing the cache
+    from paper_2408_06513_gb300 import declutter as dc
+    dc.declutter_autotune_clear()
+    good = tmp_path / "tune.txt"
+    good.write_text("declutter-autotune 1\nNVIDIA_GB300 152 9 4 0 0 19 1 2 0\nNVIDIA_GB300 152 11 16 0 0 23 0 14 1\n")
+    dc.declutter_autotune_load(str(good))
+    out = tmp_path / "out.txt"
+    dc.declutter_autotune_save(str(out))
+    lines = out.read_text().splitlines()
+    assert lines[0] == "declutter-autotune 1"
+    assert sorted(lines[1:]) == sorted(good.read_text().splitlines()[1:])
+    bad = tmp_path / "bad.txt"
+    bad.write_text("declutter-autotune 1\nNVIDIA_GB300 152 9 4 0 0 19 1 99 0\n")  # band rows out of range
+    with pytest.raises(dc.DeclutterError):
+        dc.declutter_autotune_load(str(bad))
+    with pytest.raises(dc.DeclutterError):
+        dc.declutter_autotune_load(str(tmp_path / "missing.txt"))
+    dc.declutter_autotune_save(str(out))
+    assert len(out.read_text().splitlines()) == 3
+    dc.declutter_autotune_clear()
+    dc.declutter_autotune_save(str(out))
+    assert out.read_text().splitlines() == ["declutter-autotune 1"]

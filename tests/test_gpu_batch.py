@@ -100,6 +100,41 @@ def test_autotune_band_rows(dc, panels):
     assert torch.equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("r", [2, 0])
+def test_autotune_options_and_cache_file(dc, panels, tmp_path, r):
+    # band heights x launch sequences: the tuned settings give the bits of
+    # the default ones; the cache survives a save, clear and load
+    z, log2 = panels[1]
+    pos = torch.from_numpy(z).cuda()
+    before = pos.clone()
+    dc.declutter_autotune_clear()
+    T, opts, ms = dc.declutter_autotune(pos, 2, log2, kernel_r=r)
+    assert ms > 0 and torch.equal(pos, before)
+    assert opts & ~(dc.DC_OPT_FUSED_BANDS | dc.DC_OPT_SEPARATE_SMOOTH) == 0
+    path = tmp_path / "tune.txt"
+    dc.declutter_autotune_save(str(path))
+    dc.declutter_autotune_clear()
+    dc.declutter_autotune_load(str(path))
+    T2, opts2, ms2 = dc.declutter_autotune(pos, 2, log2, kernel_r=r)
+    assert (T2, opts2, ms2) == (T, opts, -1.0)
+    outs = []
+    for bt, o in ((0, 0), (T, opts)):
+        ctx = dc.declutter_create(log2, kernel_r=r, band_rows=bt, options=o)
+        try:
+            q = torch.from_numpy(z).cuda()
+            dc.regularize(ctx, q, 1)
+            dc.declutter_sync(ctx)
+            outs.append(q)
+        finally:
+            dc.declutter_destroy(ctx)
+    if r == 0:  # exact mode: every band height gives the same bits
+        assert torch.equal(outs[0], outs[1])
+    else:  # float mode: the band height changes the order of the float
+        # sums; both fields are within 1e-4 px of FP64
+        assert float((outs[0] - outs[1]).abs().max()) * (1 << log2) <= 2e-4 + 2 * (1 << log2) * 2.0 ** -23
+    print(f"r={r}: band rows {T}, options {opts}, {ms:.3f} ms")
+
+
 def test_batch_autotune_keeps_results(dc, panels):
     pos_a = [torch.from_numpy(z).cuda() for z, _ in panels]
     pos_b = [torch.from_numpy(z).cuda() for z, _ in panels]
