@@ -647,7 +647,7 @@ def run_rows(args, dc, dev, stream, flush, reps: int = 10):
         torch.cuda.synchronize()
         ms = event_ms(lambda: dc.warp_texture(ctx, nodes, dens, 11, img, mass=True), stream, reps, before=flush)
         out["warp_texture"] = {"nodes": "2048^2", "raster": "2048^2", "us": ms * 1e3,
-                               "note": "coverage pass (one thread per triangle) and shading pass"}
+                               "note": "coverage pass (a thread a triangle, a warp for a large one) and shading pass"}
     finally:
         dc.declutter_destroy(ctx)
     return out

@@ -343,3 +343,25 @@ def test_transfer_function_bit_exact(dc):
     finally:
         dc.declutter_destroy(ctx)
     assert np.array_equal(got, L.transfer(v, -0.25, 1.3, lut))
+
+
+@pytest.mark.parametrize("opts", ["fused", "separate_smooth", "pixel_center"])
+def test_adaptive_with_launch_options(dc, opts):
+    # the conditional graph holds whatever the context launches: the
+    # cooperative band kernel, the separate smoothing, other conventions
+    z, _ = synth.tiny_mixture()
+    kw = {"fused": {"options": dc.DC_OPT_FUSED_BANDS}, "separate_smooth": {"options": dc.DC_OPT_SEPARATE_SMOOTH},
+          "pixel_center": {"pixel_center": True}}[opts]
+    ctx = dc.declutter_create(7, kernel_r=2, **kw)
+    try:
+        a = to_dev(z)
+        res = dc.regularize_adaptive(ctx, a, 5)
+        b = to_dev(z)
+        dc.regularize(ctx, b, res["iters"])
+        dc.declutter_sync(ctx)
+        assert res["iters"] == 5 and torch.equal(a, b)
+        tgt = 0.5 * (res["cv"][1] + res["cv"][2])
+        c = to_dev(z)
+        assert dc.regularize_adaptive(ctx, c, 5, target_cv=tgt)["iters"] == 3
+    finally:
+        dc.declutter_destroy(ctx)
