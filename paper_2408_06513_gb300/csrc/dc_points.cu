@@ -103,15 +103,25 @@ struct Moved {
     int pix;
 };
 
+// floor(v) for -2^22 <= v < 2^22 on the FMA pipe: adding 1.5 * 2^23 with
+// rounding toward -inf leaves floor(v) in the low mantissa bits; fl is
+// floor(v) as a float (exact)
+__device__ __forceinline__ int floor_fma(float v, float &fl)
+{
+    const float r = __fadd_rd(v, 12582912.0f);
+    fl = r - 12582912.0f;
+    return __float_as_int(r) - 0x4B400000;
+}
+
 __device__ __forceinline__ Moved advect_one(float2 z, const float2 *__restrict__ D, int log2N, float fN, float off,
                                             int clamp)
 {
     const int N = 1 << log2N;
     const float px = fminf(fmaxf(z.x * fN - off, -1.0f), fN);
     const float py = fminf(fmaxf(z.y * fN - off, -1.0f), fN);
-    const float fx = floorf(px), fy = floorf(py);
+    float fx, fy;
+    const int ix = floor_fma(px, fx), iy = floor_fma(py, fy);
     const float f = px - fx, h = py - fy;
-    const int ix = (int)fx, iy = (int)fy;
     const int i0 = min(max(ix, 0), N - 1), i1 = min(max(ix + 1, 0), N - 1);
     const int j0 = min(max(iy, 0), N - 1), j1 = min(max(iy + 1, 0), N - 1);
     const float2 d00 = __ldg(&D[(j0 << log2N) + i0]);
@@ -127,8 +137,9 @@ __device__ __forceinline__ Moved advect_one(float2 z, const float2 *__restrict__
         z.y = clamp01(z.y);
     }
     // pixel of the moved sample for the next iteration's splat (Sec. 4.1 rule)
-    const int si = min((int)(clamp01(z.x) * fN), N - 1);
-    const int sj = min((int)(clamp01(z.y) * fN), N - 1);
+    float unused;
+    const int si = min(floor_fma(clamp01(z.x) * fN, unused), N - 1);
+    const int sj = min(floor_fma(clamp01(z.y) * fN, unused), N - 1);
     return {z, (sj << log2N) + si};
 }
 
@@ -153,19 +164,31 @@ __device__ __forceinline__ void splat_warp(uint32_t *__restrict__ counts, int pi
     if (valid && lane == __ffs(m) - 1) atomicAdd(&counts[pix], (uint32_t)__popc(m));
 }
 
-// The same with runs: after the reordering by pixel, lanes holding the same
-// pixel are mostly neighbours, so a run of equal keys (found with one shuffle
-// and one ballot) shares one atomic; cheaper than __match_any_sync, but equal
-// keys that are not adjacent get separate atomics (faster up to 1024^2).
-__device__ __forceinline__ void splat_warp_runs(uint32_t *__restrict__ counts, int pix, bool valid)
+// Runs over the warp's 64 samples of one row of pairs: lane L holds samples
+// 2L (pixel p0) and 2L + 1 (pixel p1), so in sample order the keys are
+// p0(0), p1(0), p0(1), p1(1), ...  A sample starts a run when its key
+// differs from the one before it; the run's first sample adds the run's
+// length (the distance to the next start, or to the end of the row).  One
+// shuffle and two ballots a row, no __match_any_sync (whose issue rate
+// limited the kernel at 16M samples); after the reordering by pixel nearly
+// every duplicate is a neighbour.  All 32 lanes must call this together;
+// lanes with valid = false add nothing.
+__device__ __forceinline__ void splat_pair_runs(uint32_t *__restrict__ counts, int p0, int p1, bool valid)
 {
     const int lane = threadIdx.x & 31;
-    const int key = valid ? pix : -1 - lane;
-    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || key != prev);
-    const unsigned above = heads & ~((2u << lane) - 1u);  // heads after this lane (lane 31: none)
-    const int next = above ? __ffs(above) - 1 : 32;
-    if (valid && ((heads >> lane) & 1u)) atomicAdd(&counts[pix], (uint32_t)(next - lane));
+    const int k0 = valid ? p0 : -1 - 2 * lane;  // distinct negative keys for empty lanes
+    const int k1 = valid ? p1 : -2 - 2 * lane;
+    const int prev = __shfl_up_sync(0xffffffffu, k1, 1);
+    const bool h0 = lane == 0 || k0 != prev;
+    const bool h1 = k1 != k0;
+    const unsigned b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
+    const unsigned above = ~((2u << lane) - 1u);  // lanes after this one (lane 31: none)
+    const unsigned a0 = b0 & above, a1 = b1 & above;
+    const int s0 = a0 ? 2 * (__ffs(a0) - 1) : 64;
+    const int s1 = a1 ? 2 * (__ffs(a1) - 1) + 1 : 64;
+    const int next = min(s0, s1);  // first run start after this lane's pair
+    if (valid && h0) atomicAdd(&counts[p0], (uint32_t)(h1 ? 1 : next - 2 * lane));
+    if (valid && h1) atomicAdd(&counts[p1], (uint32_t)(next - 2 * lane - 1));
 }
 
 // Samples are processed in aligned pairs (one float4 = two samples), two
@@ -232,10 +255,8 @@ __device__ __forceinline__ void advect_body(float2 *__restrict__ pos, int64_t n,
         }
         if (counts_next) {
             if constexpr (RUNS) {
-                splat_warp_runs(counts_next, m0.pix, v1);
-                splat_warp_runs(counts_next, m1.pix, v1);
-                splat_warp_runs(counts_next, m2.pix, v2);
-                splat_warp_runs(counts_next, m3.pix, v2);
+                splat_pair_runs(counts_next, m0.pix, m1.pix, v1);
+                splat_pair_runs(counts_next, m2.pix, m3.pix, v2);
             } else {
                 splat_warp(counts_next, m0.pix, v1);
                 splat_warp(counts_next, m1.pix, v1);
@@ -556,11 +577,10 @@ cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *
 {
     if (n <= 0) return cudaSuccess;
     // two pairs (four samples) per thread and trip, at most one wave; run
-    // aggregation for samples in pixel order up to 1024^2 (measured faster
-    // there)
+    // aggregation for samples in pixel order
     const dim3 grid(grid_for((n + 3) / 4, kThreads, advect_wave()));
     const float off = pixel_center ? 0.5f : 0.0f;
-    const bool runs = sorted && log2N <= 10;
+    const bool runs = sorted;
     if (dmax) {
         if (runs)
             return launch_kernel(advect_kernel<true, true>, grid, dim3(kThreads), 0, s, pos, n, disp, log2N, off,
@@ -730,7 +750,7 @@ cudaError_t launch_advect_batched(cudaStream_t s, const PanelDesc *tab, int P, i
 {
     if (max_n <= 0) return cudaSuccess;
     const dim3 grid(grid_for((max_n + 3) / 4, kThreads, device_sms() * 8), P);
-    if (sorted && log2N <= 10)
+    if (sorted)
         return launch_kernel(advect_batched_kernel<true>, grid, dim3(kThreads), 0, s, tab, log2N,
                              pixel_center ? 0.5f : 0.0f, clamp, nxt);
     return launch_kernel(advect_batched_kernel<false>, grid, dim3(kThreads), 0, s, tab, log2N,
