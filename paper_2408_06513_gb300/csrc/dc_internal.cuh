@@ -12,11 +12,12 @@ namespace dc {
 
 // Programmatic dependent launch.  Every kernel is launched with programmatic
 // stream serialisation, so that its launch overlaps the tail of the kernel
-// before it; every kernel calls pdl_wait() before it touches any global
-// memory, which blocks until the preceding grid has completed and its writes
-// are visible.  pdl_trigger() lets the next kernel's CTAs be scheduled.
+// before it; every CTA of every kernel calls pdl_wait() before it touches any
+// global memory and before any early return: it blocks until the preceding
+// grid has completed and its writes are visible.  No kernel releases its
+// dependents early (griddepcontrol.launch_dependents): that measured slower
+// (0.243 against 0.237 ms a 512^2 step, 2.47 against 2.02 ms at 16M samples).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,

@@ -679,6 +679,7 @@ __global__ void __launch_bounds__(kThreads) splat_rank_batched_kernel(const Pane
 __global__ void __launch_bounds__(kScanThreads) scan_partials_batched_kernel(const PanelDesc *__restrict__ tab,
                                                                              int64_t M, int64_t chunk)
 {
+    pdl_wait();  // before the early return (see pdl_wait)
     const PanelDesc &d = tab[blockIdx.y];
     if (d.n <= 0) return;  // no samples: no sort buffers, nothing to reorder
     scan_partials_body(d.counts[0], M, chunk, d.partials);
@@ -686,6 +687,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_partials_batched_kernel(con
 __global__ void __launch_bounds__(kScanThreads) scan_apply_batched_kernel(const PanelDesc *__restrict__ tab,
                                                                           int64_t M, int64_t chunk)
 {
+    pdl_wait();
     const PanelDesc &d = tab[blockIdx.y];
     if (d.n <= 0) return;
     scan_apply_body(d.counts[0], M, chunk, d.partials, d.cursor);

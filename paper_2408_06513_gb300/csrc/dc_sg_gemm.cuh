@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(P p, int k_per_split
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * TN;
     const int k_begin = blockIdx.z * k_per_split;
     const int k_end = min(p.K, k_begin + k_per_split);
+    pdl_wait();
     if (k_begin >= k_end) return;
 
     auto stage = [&](int buf, int k0) {

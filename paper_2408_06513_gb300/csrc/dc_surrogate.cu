@@ -225,7 +225,11 @@ __global__ void conv_finalize_kernel(const float *__restrict__ acc, int64_t M, i
     }
 }
 
-__global__ void set_value_kernel(float *p, float v) { *p = v; }
+__global__ void set_value_kernel(float *p, float v)
+{
+    pdl_wait();
+    *p = v;
+}
 
 // out[p][c] += kappa * field[p][c]
 __global__ void add_skip_kernel(float *__restrict__ out, const float *__restrict__ field, float kappa, int64_t n)
