@@ -991,15 +991,28 @@ def run_surrogate(args, dc, dev):
             u = dc.regularize(ctx, z.clone(), 8, uniformity=True)
             cv_plain = [x / mean for x in u]
             target_cv = 1.05 * cv_plain[-1]
-            for _ in range(2):  # warm-up: graph capture of every iteration count used below
-                dc.regularize(ctx, z.clone(), 8)
-                dc.regularize(ctx, z.clone(), 1)
-                dc.surrogate_apply(ctx, sg, z.clone(), 0.0, 0)
-            ms_sg, (used0, cv_sg) = wall(lambda: dc.surrogate_apply(ctx, sg, z.clone(), 0.0, 0))
+            # one sample buffer for every timed call (the captured graphs are
+            # keyed by the sample pointer), refilled outside the timed span
+            zb = torch.empty_like(z)
+
+            def fresh():
+                zb.copy_(z)
+                return zb
+
+            for _ in range(2):  # warm-up: graph capture of every launch used below
+                for k in range(1, 9):
+                    dc.regularize(ctx, fresh(), k)
+                dc.surrogate_apply(ctx, sg, fresh(), 0.0, 0)
+                dc.surrogate_apply(ctx, sg, fresh(), target_cv, 16)
+            fresh()
+            ms_sg, (used0, cv_sg) = wall(lambda: dc.surrogate_apply(ctx, sg, zb, 0.0, 0))
             worth = sum(1 for c in cv_plain if c >= cv_sg)
-            ms_plain_eq = wall(lambda: dc.regularize(ctx, z.clone(), max(worth, 1)))[0] if worth else 0.0
-            ms_plain8 = wall(lambda: dc.regularize(ctx, z.clone(), 8))[0]
-            ms_fb, (used, cv_fb) = wall(lambda: dc.surrogate_apply(ctx, sg, z.clone(), target_cv, 16))
+            fresh()
+            ms_plain_eq = wall(lambda: dc.regularize(ctx, zb, max(worth, 1)))[0] if worth else 0.0
+            fresh()
+            ms_plain8 = wall(lambda: dc.regularize(ctx, zb, 8))[0]
+            fresh()
+            ms_fb, (used, cv_fb) = wall(lambda: dc.surrogate_apply(ctx, sg, zb, target_cv, 16))
             rows.append({"samples": n, "cv0_plain": cv_plain[0], "cv_plain8": cv_plain[-1], "cv_surrogate": cv_sg,
                          "worth_plain_iters": worth, "ms_surrogate_pass": ms_sg, "ms_plain_equal_quality": ms_plain_eq,
                          "ms_plain8": ms_plain8, "ms_surrogate_to_plain8_quality": ms_fb, "fallback_plain_iters": used,

@@ -553,10 +553,14 @@ dc_status surrogate_train_step(dc_surrogate *sg, const float *density, const flo
 /* One-shot regularisation of device samples with the surrogate (context in
  * float mode at the surrogate's resolution): predict the composed field from
  * the samples' density (and, with in_channels = 3, the field of one plain
- * iteration, computed here), move every sample once by it, then run plain
- * iterations while the Sec. 6.2 bin std / mean exceeds target_cv (at most
- * max_plain_iters).  Returns the plain iterations used and the final ratio.
- * Synchronises. */
+ * iteration, computed here), move every sample once by it, then, if the
+ * Sec. 6.2 bin std / mean of the moved samples exceeds target_cv, run plain
+ * iterations as regularize_adaptive() does (one graph launch, stopped on the
+ * GPU after the first iteration that meets target_cv; at most
+ * max_plain_iters, 0..1024; target_cv = 0 runs all of them).  Returns the
+ * plain iterations used and the final ratio.  Synchronises.  Errors:
+ * DC_ERR_INVALID_ARG also for max_plain_iters outside 0..1024 or a negative
+ * or non-finite target_cv. */
 dc_status surrogate_apply(dc_ctx *ctx, dc_surrogate *sg, float *pos_xy, int64_t n, float target_cv,
                           int32_t max_plain_iters, int32_t *plain_iters_out, double *cv_out);
 

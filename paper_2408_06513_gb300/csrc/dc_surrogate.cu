@@ -1019,6 +1019,8 @@ dc_status surrogate_apply(dc_ctx *ctx, dc_surrogate *s, float *pos_xy, int64_t n
     if (dc_status st = check_sg(s)) return st;
     if (!ctx || (int)ctx->p.log2_res != s->log2H) return sfail(DC_ERR_INVALID_ARG, "context resolution");
     if (n <= 0 || !pos_xy) return sfail(DC_ERR_INVALID_ARG, "samples");
+    if (max_plain_iters < 0 || max_plain_iters > 1024) return sfail(DC_ERR_INVALID_ARG, "max_plain_iters (0..1024)");
+    if (!(target_cv >= 0.f) || !std::isfinite(target_cv)) return sfail(DC_ERR_INVALID_ARG, "target_cv");
     if (ctx->mode != MODE_FLOAT) return sfail(DC_ERR_INVALID_ARG, "the surrogate takes a smoothed density");
     SgGuard guard(s->device);
     // no host synchronisation until the quality measure: the context's
@@ -1068,12 +1070,18 @@ dc_status surrogate_apply(dc_ctx *ctx, dc_surrogate *s, float *pos_xy, int64_t n
     if (dc_status st = advect_samples(ctx, pos_xy, n)) return st;
     int used = 0;
     double m[3] = {0, 0, 0};
-    for (;;) {
-        if (dc_status st = splat_density(ctx, pos_xy, n, nullptr, nullptr)) return st;
-        if (dc_status st = quality_metrics(ctx, m)) return st;
-        if (m[1] <= target_cv || used >= max_plain_iters) break;
-        if (dc_status st = regularize(ctx, pos_xy, n, 1, nullptr)) return st;
-        ++used;
+    if (dc_status st = splat_density(ctx, pos_xy, n, nullptr, nullptr)) return st;
+    if (dc_status st = quality_metrics(ctx, m)) return st;
+    if (m[1] > target_cv && max_plain_iters > 0) {
+        // the fallback iterations in one graph launch, stopped on the GPU
+        // after the first iteration whose moved samples meet target_cv
+        std::vector<double> cvs((size_t)max_plain_iters);
+        int32_t done = 0;
+        if (dc_status st = regularize_adaptive(ctx, pos_xy, n, max_plain_iters, target_cv > 0.f ? target_cv : 0.0,
+                                               0.0, 0.0, &done, cvs.data(), nullptr))
+            return st;
+        used = done;
+        m[1] = cvs[(size_t)done - 1];
     }
     if (plain_iters_out) *plain_iters_out = used;
     if (cv_out) *cv_out = m[1];

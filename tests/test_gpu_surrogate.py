@@ -161,6 +161,22 @@ def test_training_gains_over_untrained_and_over_no_iteration(dc, c_in):
             used, cv = dc.surrogate_apply(ctx, sg, z.clone(), 0.0, 0)
             assert used == 0
             worth.append(sum(1 for c in cv_plain if c >= cv))
+            if t == 0:
+                # fallback: plain iterations in one adaptive launch until the
+                # measure meets the target; the returned ratio is that of the
+                # returned positions
+                target = 0.9 * cv
+                pos = z.clone()
+                used_f, cv_f = dc.surrogate_apply(ctx, sg, pos, float(target), 6)
+                dc.splat_density(ctx, pos)
+                q = dc.quality_metrics(ctx)["bin_cv"]
+                assert abs(q - cv_f) <= 1e-9 * max(1.0, cv_f), (q, cv_f)
+                assert 0 <= used_f <= 6 and (used_f == 6 or cv_f <= target), (used_f, cv_f, target)
+                assert dc.surrogate_apply(ctx, sg, z.clone(), 0.0, 3)[0] == 3
+                assert dc.surrogate_apply(ctx, sg, z.clone(), 1e9, 3)[0] == 0
+                for bad in ((0.5, -1), (0.5, 1025), (-0.1, 2), (float("nan"), 2)):
+                    with pytest.raises(dc.DeclutterError):
+                        dc.surrogate_apply(ctx, sg, z.clone(), *bad)
         print("surrogate pass worth (plain iterations):", worth, "field rms px:", before, after)
         assert min(worth) >= 1, worth
     finally:
