@@ -46,6 +46,9 @@ __global__ void __launch_bounds__(kThreads) splat_kernel(const float2 *__restric
 // The same splat, also recording each sample's rank among the samples of its
 // pixel (the counter value its atomic increment returned), for the
 // reordering below.  Ranks of a pixel's samples are exactly 0 .. count - 1.
+// One atomic a sample, without warp aggregation: the samples arrive in the
+// caller's order, where lanes of a warp rarely share a pixel (the 512^2
+// step measured 0.2275 against 0.2347 ms with __match_any_sync).
 __device__ __forceinline__ void splat_rank_body(const float2 *__restrict__ pos, int64_t n,
                                                               uint32_t *__restrict__ counts, int log2N,
                                                               uint32_t *__restrict__ rank)
@@ -70,20 +73,11 @@ __device__ __forceinline__ void splat_rank_body(const float2 *__restrict__ pos, 
                 pix[u] = (j << log2N) + i;
             }
         }
-        unsigned m[kU];
-        uint32_t r0[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            m[u] = __match_any_sync(0xffffffffu, pix[u]);
-            r0[u] = 0;
-            if (base + u * stride + lane < n && lane == __ffs(m[u]) - 1)
-                r0[u] = atomicAdd(&counts[pix[u]], (uint32_t)__popc(m[u]));
-        }
+        // one atomic a sample: its return value is the sample's rank
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int64_t k = base + u * stride + lane;
-            const uint32_t lead = __shfl_sync(0xffffffffu, r0[u], __ffs(m[u]) - 1);
-            if (k < n) rank[k] = lead + __popc(m[u] & ((1u << lane) - 1u));
+            if (k < n) rank[k] = atomicAdd(&counts[pix[u]], 1u);
         }
     }
 }
