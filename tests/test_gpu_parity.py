@@ -658,17 +658,21 @@ FUSED_CASES = {
     # name: (generator, log2 N, r)
     "gmm20_512": (lambda: synth.gmm20()[0], 9, 4),
     "student_t_2048": (lambda: synth.student_t_clusters()[0], 11, 16),
+    # an odd sample count: the last sample is moved and splatted outside the
+    # pairs of the warp-wide run aggregation
+    "tiny_odd": (lambda: synth.tiny_mixture(20_001, seed=3)[0], 7, 2),
 }
 
 
 @pytest.mark.parametrize("case,keep_order,k", [("gmm20_512", False, 2), ("gmm20_512", False, 3),
                                                ("gmm20_512", True, 2), ("student_t_2048", False, 2),
-                                               ("student_t_2048", False, 3)])
+                                               ("student_t_2048", False, 3), ("tiny_odd", False, 3),
+                                               ("tiny_odd", True, 3)])
 def test_fused_splat_inside_regularize_matches_oracle(dc, case, keep_order, k):
     # Inside regularize(k) the advection of iteration m splats the moved
-    # samples into the count grid of iteration m + 1 (run-aggregated atomics
-    # on pixel-ordered samples up to 1024^2, __match_any_sync otherwise and
-    # in the caller's order).  Three checks:
+    # samples into the count grid of iteration m + 1 (atomics aggregated over
+    # runs of equal pixels on pixel-ordered samples, __match_any_sync in the
+    # caller's order).  Three checks:
     #  (1) regularize(k) without metrics leaves the input grid of its last
     #      iteration, i.e. the in-graph splat of the positions after k - 1
     #      iterations (regularize(k - 1) on a copy gives those bits):
@@ -710,6 +714,38 @@ def test_fused_splat_inside_regularize_matches_oracle(dc, case, keep_order, k):
         assert np.array_equal(c_out, ref_c), "in-graph splat of the final positions"
         assert abs(u[-1] - oracle.quality(ref_c)["bin_std"]) <= 1e-9 * max(1.0, u[-1])
         print(f"{case} keep_order={keep_order} k={k}: counts bit-exact, last iteration {perr:.3e} px")
+    finally:
+        dc.declutter_destroy(ctx)
+
+
+@pytest.mark.parametrize("keep_order", [False, True])
+def test_fused_splat_with_unaligned_samples(dc, keep_order):
+    # samples starting 8 bytes past a 16-byte boundary and an odd count: in
+    # the caller's order the first and the last sample fall outside the
+    # aligned pairs of the advection; counts of the in-graph splat bit-exact
+    log2, r, k = 7, 2, 3
+    z, _ = synth.tiny_mixture(20_001, seed=8)
+    N = 1 << log2
+    ctx = dc.declutter_create(log2, kernel_r=r, keep_order=keep_order)
+    try:
+        buf = torch.zeros(z.shape[0] + 1, 2, dtype=torch.float32, device=DEV)
+        pos = buf[1:]
+        assert pos.data_ptr() % 16 == 8
+        pos.copy_(to_dev(z))
+        dc.regularize(ctx, pos, k - 1)
+        dc.declutter_sync(ctx)
+        prev_np = pos.cpu().numpy()
+        pos.copy_(to_dev(z))
+        counts = torch.empty(N * N, dtype=torch.int32, device=DEV)
+        dc.regularize(ctx, pos, k, uniformity=True)
+        dc.declutter_counts(ctx, counts)
+        dc.declutter_sync(ctx)
+        fin = pos.cpu().numpy()
+        assert np.array_equal(u32(counts, N).astype(np.uint64), oracle.splat(fin, log2))
+        ref = oracle.iterate(prev_np, oracle.Params(log2_res=log2, kernel_r=r))
+        perr = float(np.max(np.abs(fin.astype(np.float64) - ref))) * N
+        assert perr <= pos_tol_px(N), perr
+        assert float(buf[0].abs().sum()) == 0.0, "the slot before the samples must stay untouched"
     finally:
         dc.declutter_destroy(ctx)
 
