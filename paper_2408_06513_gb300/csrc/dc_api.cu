@@ -163,12 +163,19 @@ cudaError_t enqueue_first_splat(dc_ctx *c, cudaStream_t s, const float *pos, int
     // its next use, so that these counts stay those of pos
     if (e == cudaSuccess && rec.times(K_SPLAT) > 1) e = launch_splat(s, p2, n, cb[1], c->g.log2N);
     if (e != cudaSuccess || !reorder) return e;
+    // the reordering reads only the counts, the ranks and the caller's
+    // samples, which the first iteration's grid passes do not write: it runs
+    // on a branch beside them, and the first advection joins it
+    // (enqueue_iteration with join_reorder)
+    e = cudaEventRecord(c->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     rec.count(K_REORDER);
     for (int t = 0; t < rec.times(K_REORDER) && e == cudaSuccess; ++t) {
-        e = launch_reorder_scan(s, cb[0], c->g.log2N, c->partials, c->cursor);
+        e = launch_reorder_scan(c->side, cb[0], c->g.log2N, c->partials, c->cursor);
         if (e == cudaSuccess)
-            e = launch_reorder_scatter(s, p2, n, c->g.log2N, c->cursor, c->rank, c->spos, c->inv, c->status);
+            e = launch_reorder_scatter(c->side, p2, n, c->g.log2N, c->cursor, c->rank, c->spos, c->inv, c->status);
     }
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
     return e;
 }
 
@@ -179,7 +186,7 @@ cudaError_t enqueue_first_splat(dc_ctx *c, cudaStream_t s, const float *pos, int
 // dmax (or null): the largest squared move of the iteration.
 cudaError_t enqueue_iteration(dc_ctx *c, cudaStream_t s, const float *pos, float *ipos, int64_t n, int cur,
                               bool need_next, unsigned long long *qacc, unsigned *dmax, Recorder &rec,
-                              float *tracers = nullptr, int64_t n_tracers = 0)
+                              float *tracers = nullptr, int64_t n_tracers = 0, bool join_reorder = false)
 {
     cudaError_t e = cudaSuccess;
     uint32_t *cb[2] = {c->counts_buf[0], c->counts_buf[1]};
@@ -198,6 +205,7 @@ cudaError_t enqueue_iteration(dc_ctx *c, cudaStream_t s, const float *pos, float
     e = smooth_fused ? enqueue_inims(c, s, a, c->mode, rec, cb[cur], need_next ? cb[nxt] : nullptr)
                      : enqueue_inims(c, s, a, c->mode, rec);
     if (e != cudaSuccess) return e;
+    if (join_reorder && (e = cudaStreamWaitEvent(s, c->ev_join, 0)) != cudaSuccess) return e;
     rec.count(K_ADVECT);
     for (int t = 0; t < rec.times(K_ADVECT) && e == cudaSuccess; ++t)
         e = launch_advect(s, reinterpret_cast<float2 *>(ipos), n, c->disp, c->g.log2N, c->p.pixel_center,
@@ -233,7 +241,7 @@ cudaError_t enqueue_iterations(dc_ctx *c, cudaStream_t s, float *pos, int64_t n,
         const bool need_next = (it + 1 < iters) || metrics;
         if (it == 0 && (e = enqueue_first_splat(c, s, pos, n, reorder, rec)) != cudaSuccess) return e;
         e = enqueue_iteration(c, s, pos, ipos, n, cur, need_next, metrics ? c->qacc + 3 * it : nullptr, nullptr, rec,
-                              tracers, n_tracers);
+                              tracers, n_tracers, it == 0 && reorder);
         if (e != cudaSuccess) return e;
         if (need_next) cur ^= 1;
     }
@@ -347,7 +355,7 @@ dc_status capture_adaptive(dc_ctx *c, float *pos, int64_t n, int max_iters, cuda
     if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, sizeof(unsigned) * (size_t)max_iters, s);
     if (e == cudaSuccess) e = launch_adapt_start(s, st);
     if (e == cudaSuccess) e = enqueue_first_splat(c, s, pos, n, reorder, rec);
-    if (e == cudaSuccess) e = enqueue_iteration(c, s, pos, ipos, n, 0, true, c->qacc, dmax, rec);
+    if (e == cudaSuccess) e = enqueue_iteration(c, s, pos, ipos, n, 0, true, c->qacc, dmax, rec, nullptr, 0, reorder);
     if (e == cudaSuccess)
         e = launch_adapt_check(s, c->qacc, dmax, st, cv, mv, 0, c->g.log2N, h[1], max_iters > 1 ? 1 : 0);
     for (int it = 1; it < max_iters && e == cudaSuccess; ++it) {
@@ -609,8 +617,12 @@ dc_status declutter_create(const dc_params *params, int device, void *cuda_strea
         c->own_stream = true;
     }
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking) != cudaSuccess)
+        cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(DC_ERR_CUDA, "cudaStreamCreateWithFlags"));
+    if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(DC_ERR_CUDA, "cudaEventCreateWithFlags"));
     const size_t NN = (size_t)N * N;
     const size_t agg_bytes = (size_t)c->g.nb * c->g.agg_stride * 8;
     const size_t carry_bytes = (size_t)(c->g.nb + 1) * c->g.lanes * 8;
@@ -687,6 +699,9 @@ dc_status declutter_destroy(dc_ctx *c)
     cudaFree(c->lq);
     cudaFree(c->lterms);
     cudaFree(c->wcover);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -284,6 +284,10 @@ struct dc_ctx {
     void *adapt = nullptr;
     int adapt_cap = 0;
     cudaStream_t cap_stream2 = nullptr;
+    // the reordering's branch beside the first iteration's grid passes:
+    // forked from and joined back to the iteration stream by these events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // layout_metrics scratch: lattice coordinates of both layouts, query terms
     uint32_t *lq = nullptr;
     int64_t lq_cap = 0;
