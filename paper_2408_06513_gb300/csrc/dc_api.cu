@@ -158,7 +158,11 @@ cudaError_t enqueue_first_splat(dc_ctx *c, cudaStream_t s, const float *pos, int
     if (e != cudaSuccess) return e;
     rec.count(K_SPLAT);
     const float2 *p2 = reinterpret_cast<const float2 *>(pos);
-    e = reorder ? launch_splat_rank(s, p2, n, cb[0], c->g.log2N, c->rank) : launch_splat(s, p2, n, cb[0], c->g.log2N);
+    // samples in host memory: read once over the link, the scatter reads the
+    // device copy the splat leaves in hpos
+    float2 *copy = reorder && c->copy_first && c->hpos_cap >= n ? reinterpret_cast<float2 *>(c->hpos) : nullptr;
+    e = reorder ? launch_splat_rank(s, p2, n, cb[0], c->g.log2N, c->rank, copy)
+                : launch_splat(s, p2, n, cb[0], c->g.log2N);
     // a profiling duplicate goes to the other grid, which is zeroed before
     // its next use, so that these counts stay those of pos
     if (e == cudaSuccess && rec.times(K_SPLAT) > 1) e = launch_splat(s, p2, n, cb[1], c->g.log2N);
@@ -173,7 +177,8 @@ cudaError_t enqueue_first_splat(dc_ctx *c, cudaStream_t s, const float *pos, int
     for (int t = 0; t < rec.times(K_REORDER) && e == cudaSuccess; ++t) {
         e = launch_reorder_scan(c->side, cb[0], c->g.log2N, c->partials, c->cursor);
         if (e == cudaSuccess)
-            e = launch_reorder_scatter(c->side, p2, n, c->g.log2N, c->cursor, c->rank, c->spos, c->inv, c->status);
+            e = launch_reorder_scatter(c->side, copy ? copy : p2, n, c->g.log2N, c->cursor, c->rank, c->spos, c->inv,
+                                       c->status);
     }
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
     return e;
@@ -969,13 +974,13 @@ dc_status regularize_host(dc_ctx *c, float *host_pos, int64_t n, int32_t iters, 
     // the first splat and the reordering (one read each) and in the way back
     // (one write), so they run on it directly over the host link, without
     // staging copies (DC_OPT_STAGE_HOST: always stage).
-    if (n > 0 && c->p.keep_order == 0 && !(c->p.options & DC_OPT_STAGE_HOST))
-        if (float *dp = device_alias(host_pos)) {
-            if (dc_status st = regularize(c, dp, n, iters, uniformity_out)) return st;
-            return declutter_sync(c);
-        }
+    // the device buffer hpos: the staged copy, or the splat's copy of
+    // samples used in place; cached graphs hold its address, so they are
+    // dropped when it moves
     if (n > c->hpos_cap) {
         DC_CUDA(cudaStreamSynchronize(c->stream));
+        for (auto &ge : c->graphs) cudaGraphExecDestroy(ge.exec);
+        c->graphs.clear();
         cudaFree(c->hpos);
         c->hpos = nullptr;
         c->hpos_cap = 0;
@@ -985,6 +990,14 @@ dc_status regularize_host(dc_ctx *c, float *host_pos, int64_t n, int32_t iters, 
         }
         c->hpos_cap = n;
     }
+    if (n > 0 && c->p.keep_order == 0 && !(c->p.options & DC_OPT_STAGE_HOST))
+        if (float *dp = device_alias(host_pos)) {
+            c->copy_first = true;
+            const dc_status st = regularize(c, dp, n, iters, uniformity_out);
+            c->copy_first = false;
+            if (st != DC_OK) return st;
+            return declutter_sync(c);
+        }
     const size_t bytes = sizeof(float) * 2 * (size_t)n;
     if (n > 0) DC_CUDA(cudaMemcpyAsync(c->hpos, host_pos, bytes, cudaMemcpyHostToDevice, c->stream));
     if (dc_status st = regularize(c, c->hpos, n, iters, uniformity_out)) return st;

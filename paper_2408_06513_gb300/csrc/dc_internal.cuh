@@ -145,7 +145,7 @@ cudaError_t launch_quality(cudaStream_t s, const uint32_t *counts, int log2N, un
 // (partials: at most 1024 entries); scatter into spos with inv[k] = slot of
 // sample k; gather back pos[k] = spos[inv[k]]
 cudaError_t launch_splat_rank(cudaStream_t s, const float2 *pos, int64_t n, uint32_t *counts, int log2N,
-                              uint32_t *rank);
+                              uint32_t *rank, float2 *copy_out = nullptr);
 int64_t reorder_scan_chunk(int log2N);
 cudaError_t launch_reorder_scan(cudaStream_t s, const uint32_t *counts, int log2N, uint32_t *partials,
                                 uint32_t *cursor);
@@ -288,6 +288,10 @@ struct dc_ctx {
     // forked from and joined back to the iteration stream by these events
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // set by regularize_host around a run on the caller's host memory: the
+    // first splat copies the samples into hpos and the reordering's scatter
+    // reads that copy, so the host array is read over the link once
+    bool copy_first = false;
     // layout_metrics scratch: lattice coordinates of both layouts, query terms
     uint32_t *lq = nullptr;
     int64_t lq_cap = 0;

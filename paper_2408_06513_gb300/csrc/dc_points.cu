@@ -49,9 +49,12 @@ __global__ void __launch_bounds__(kThreads) splat_kernel(const float2 *__restric
 // One atomic a sample, without warp aggregation: the samples arrive in the
 // caller's order, where lanes of a warp rarely share a pixel (the 512^2
 // step measured 0.2275 against 0.2347 ms with __match_any_sync).
+// copy_out (or null): every sample is also written there (a device copy of
+// samples that live in host memory, for the reordering's scatter).
 __device__ __forceinline__ void splat_rank_body(const float2 *__restrict__ pos, int64_t n,
                                                               uint32_t *__restrict__ counts, int log2N,
-                                                              uint32_t *__restrict__ rank)
+                                                              uint32_t *__restrict__ rank,
+                                                              float2 *__restrict__ copy_out = nullptr)
 {
     pdl_wait();
     const int N = 1 << log2N;
@@ -68,6 +71,7 @@ __device__ __forceinline__ void splat_rank_body(const float2 *__restrict__ pos, 
             pix[u] = -1 - lane;
             if (k < n) {
                 const float2 z = pos[k];
+                if (copy_out) copy_out[k] = z;
                 const int i = min((int)(clamp01(z.x) * fN), N - 1);
                 const int j = min((int)(clamp01(z.y) * fN), N - 1);
                 pix[u] = (j << log2N) + i;
@@ -83,9 +87,10 @@ __device__ __forceinline__ void splat_rank_body(const float2 *__restrict__ pos, 
 }
 __global__ void __launch_bounds__(kThreads) splat_rank_kernel(const float2 *__restrict__ pos, int64_t n,
                                                               uint32_t *__restrict__ counts, int log2N,
-                                                              uint32_t *__restrict__ rank)
+                                                              uint32_t *__restrict__ rank,
+                                                              float2 *__restrict__ copy_out)
 {
-    splat_rank_body(pos, n, counts, log2N, rank);
+    splat_rank_body(pos, n, counts, log2N, rank, copy_out);
 }
 
 // Bilinear advection (Sec. 4.2): p = x N (- 1/2 for pixel centres),
@@ -611,11 +616,11 @@ cudaError_t launch_reorder_scan(cudaStream_t s, const uint32_t *counts, int log2
 }
 
 cudaError_t launch_splat_rank(cudaStream_t s, const float2 *pos, int64_t n, uint32_t *counts, int log2N,
-                              uint32_t *rank)
+                              uint32_t *rank, float2 *copy_out)
 {
     if (n <= 0) return cudaSuccess;
     return launch_kernel(splat_rank_kernel, dim3(grid_for(n, kThreads, device_sms() * 16)), dim3(kThreads), 0, s, pos, n,
-                         counts, log2N, rank);
+                         counts, log2N, rank, copy_out);
 }
 
 // Slots a scatter window holds: 32 MB of samples, a quarter of the L2.
