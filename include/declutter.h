@@ -588,7 +588,7 @@ dc_status surrogate_apply(dc_ctx *ctx, dc_surrogate *sg, float *pos_xy, int64_t 
  * DC_ERR_NOT_POW2; declutter_last_error() gives the reason.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) and sets the kernels' shared-memory attributes with
- * that device current; make that first call before any stream capture.  All
+ * that device current; later calls reuse both.  All
  * calls share the one array and it keeps the last call's contents (none of
  * it needs to start at zero): calls that overlap on the GPU, for instance on
  * two streams, race and must not be issued.
