@@ -971,9 +971,9 @@ dc_status regularize_host(dc_ctx *c, float *host_pos, int64_t n, int32_t iters, 
     DeviceGuard guard(c->device);
     // Pinned (or registered) host memory is addressable by the device: with
     // the samples reordered, the iterations touch the caller's array only in
-    // the first splat and the reordering (one read each) and in the way back
-    // (one write), so they run on it directly over the host link, without
-    // staging copies (DC_OPT_STAGE_HOST: always stage).
+    // the first splat (one read, leaving a device copy for the reordering)
+    // and in the way back (one write), so they run on it directly over the
+    // host link, without staging copies (DC_OPT_STAGE_HOST: always stage).
     // the device buffer hpos: the staged copy, or the splat's copy of
     // samples used in place; cached graphs hold its address, so they are
     // dropped when it moves
