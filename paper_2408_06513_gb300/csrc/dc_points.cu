@@ -623,8 +623,10 @@ cudaError_t launch_splat_rank(cudaStream_t s, const float2 *pos, int64_t n, uint
                          counts, log2N, rank, copy_out);
 }
 
-// Slots a scatter window holds: 32 MB of samples, a quarter of the L2.
-constexpr int64_t kScatterWindow = (int64_t)(32 << 20) / sizeof(float2);
+// Slots a scatter window holds: 64 MB of samples, half the L2 (16M samples:
+// two passes, 0.45 ms for the reordering against 0.49 ms with four passes of
+// 32 MB and 0.6 ms with one pass).
+constexpr int64_t kScatterWindow = (int64_t)(64 << 20) / sizeof(float2);
 
 cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n, int log2N, const uint32_t *cursor,
                                    const uint32_t *rank, float2 *spos, uint32_t *inv, unsigned *status)
