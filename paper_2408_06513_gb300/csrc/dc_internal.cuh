@@ -141,15 +141,16 @@ cudaError_t launch_advect(cudaStream_t s, float2 *pos, int64_t n, const float2 *
                           unsigned *dmax = nullptr);
 cudaError_t launch_quality(cudaStream_t s, const uint32_t *counts, int log2N, unsigned long long *acc);
 // reordering of the samples by pixel: the first splat also records each
-// sample's rank within its pixel; exclusive scan of the counts into cursor
-// (partials: at most 1024 entries); scatter into spos with inv[k] = slot of
-// sample k; gather back pos[k] = spos[inv[k]]
+// sample's rank within its pixel (rank not null); exclusive scan of the
+// counts into cursor (partials: at most 1024 entries); scatter into spos with
+// inv[k] = slot of sample k (without ranks, slots are claimed by atomic
+// increments of cursor); gather back pos[k] = spos[inv[k]]
 cudaError_t launch_splat_rank(cudaStream_t s, const float2 *pos, int64_t n, uint32_t *counts, int log2N,
                               uint32_t *rank, float2 *copy_out = nullptr);
 int64_t reorder_scan_chunk(int log2N);
 cudaError_t launch_reorder_scan(cudaStream_t s, const uint32_t *counts, int log2N, uint32_t *partials,
                                 uint32_t *cursor);
-cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n, int log2N, const uint32_t *cursor,
+cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n, int log2N, uint32_t *cursor,
                                    const uint32_t *rank, float2 *spos, uint32_t *inv, unsigned *status);
 cudaError_t launch_reorder_back(cudaStream_t s, const float2 *spos, const uint32_t *inv, int64_t n, float2 *pos,
                                 unsigned *status);

@@ -77,11 +77,15 @@ __device__ __forceinline__ void splat_rank_body(const float2 *__restrict__ pos, 
                 pix[u] = (j << log2N) + i;
             }
         }
-        // one atomic a sample: its return value is the sample's rank
+        // one atomic a sample: its return value is the sample's rank (or,
+        // without rank, a reduction whose value nobody waits for)
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int64_t k = base + u * stride + lane;
-            if (k < n) rank[k] = atomicAdd(&counts[pix[u]], 1u);
+            if (k < n) {
+                if (rank) rank[k] = atomicAdd(&counts[pix[u]], 1u);
+                else atomicAdd(&counts[pix[u]], 1u);
+            }
         }
     }
 }
@@ -394,7 +398,8 @@ __device__ __forceinline__ int sample_pixel(float2 z, int log2N, float fN)
 }
 
 // spos[slot] = pos[k] and inv[k] = slot, with slot = cursor[pixel] + rank[k]
-// (cursor: exclusive prefix of the counts).  The slots of pixel p are
+// (cursor: exclusive prefix of the counts), or, without ranks, the value an
+// atomic increment of cursor[pixel] returns.  The slots of pixel p are
 // [prefix(p), prefix(p) + counts(p)), so every slot < n when cursor and rank
 // come from the splat of these same samples; a slot out of range sets
 // DC_ERR_RANGE in the status word and is skipped.
@@ -408,7 +413,7 @@ __device__ __forceinline__ int sample_pixel(float2 z, int log2N, float fN)
 // Sources are read with the streaming (evict-first) hint to spare the
 // window's lines.
 __device__ __forceinline__ void reorder_scatter_body(const float2 *__restrict__ pos, int64_t n,
-                                                                   int log2N, const uint32_t *__restrict__ cursor,
+                                                                   int log2N, uint32_t *__restrict__ cursor,
                                                                    const uint32_t *__restrict__ rank,
                                                                    float2 *__restrict__ spos,
                                                                    uint32_t *__restrict__ inv,
@@ -422,7 +427,9 @@ __device__ __forceinline__ void reorder_scatter_body(const float2 *__restrict__ 
         const float2 z = __ldcs(pos + k);
         uint32_t slot;
         if (first) {
-            slot = __ldg(&cursor[sample_pixel(z, log2N, fN)]) + __ldcs(rank + k);
+            // without ranks the sample claims the next slot of its pixel
+            slot = rank ? __ldg(&cursor[sample_pixel(z, log2N, fN)]) + __ldcs(rank + k)
+                        : atomicAdd(&cursor[sample_pixel(z, log2N, fN)], 1u);
             if ((int64_t)slot >= n) {
                 inv[k] = 0xffffffffu;
                 atomicOr(status, (unsigned)DC_ERR_RANGE);
@@ -437,7 +444,7 @@ __device__ __forceinline__ void reorder_scatter_body(const float2 *__restrict__ 
     }
 }
 __global__ void __launch_bounds__(kThreads) reorder_scatter_kernel(const float2 *__restrict__ pos, int64_t n,
-                                                                   int log2N, const uint32_t *__restrict__ cursor,
+                                                                   int log2N, uint32_t *__restrict__ cursor,
                                                                    const uint32_t *__restrict__ rank,
                                                                    float2 *__restrict__ spos,
                                                                    uint32_t *__restrict__ inv,
@@ -628,7 +635,7 @@ cudaError_t launch_splat_rank(cudaStream_t s, const float2 *pos, int64_t n, uint
 // 32 MB and 0.6 ms with one pass).
 constexpr int64_t kScatterWindow = (int64_t)(64 << 20) / sizeof(float2);
 
-cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n, int log2N, const uint32_t *cursor,
+cudaError_t launch_reorder_scatter(cudaStream_t s, const float2 *pos, int64_t n, int log2N, uint32_t *cursor,
                                    const uint32_t *rank, float2 *spos, uint32_t *inv, unsigned *status)
 {
     if (n <= 0) return cudaSuccess;
