@@ -496,7 +496,8 @@ dc_status declutter_batch_autotune(dc_batch *batch, float *const *pos_xy, const 
  * Learned surrogate (not in the paper): a convolutional encoder-decoder that
  * maps a density grid to the displacement field composed over several plain
  * iterations, trained on pairs the plain method generates.  BF16 weights and
- * activations, FP32 accumulation on tensor cores (mma.sync BF16), FP32
+ * activations, FP32 accumulation on tensor cores (tcgen05 or mma.sync, see
+ * surrogate_set_tensor_path), FP32
  * master weights and Adam.  Layers, in order: enc{l}a, enc{l}b for
  * l = 0..L-1 (widths c_l = base_channels * 2^l), dec{l}up, dec{l}c for
  * l = L-2..0, head (2 outputs); 3x3 convolutions with zero padding, ReLU
@@ -519,10 +520,13 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
 dc_status surrogate_set_skip(dc_surrogate *sg, float kappa);
 
 /* Tensor-core path of the forward convolutions with 64..256 output
- * channels: DC_SG_MMA_SYNC (default; warp-level mma.sync) or DC_SG_TCGEN05
- * (fifth-generation tcgen05.mma with the accumulator in tensor memory).
- * The two sum in different orders (results within FP32 rounding). */
-enum { DC_SG_MMA_SYNC = 0, DC_SG_TCGEN05 = 1 };
+ * channels: DC_SG_MMA_SYNC (warp-level mma.sync), DC_SG_TCGEN05
+ * (fifth-generation tcgen05.mma with the accumulator in tensor memory, the
+ * weights staged by tensor memory access) or DC_SG_AUTO (default: tcgen05
+ * in batches of two or more samples, mma.sync for a single one, where each
+ * measured faster).  The paths sum in different orders (results within FP32
+ * rounding). */
+enum { DC_SG_MMA_SYNC = 0, DC_SG_TCGEN05 = 1, DC_SG_AUTO = 2 };
 dc_status surrogate_set_tensor_path(dc_surrogate *sg, int32_t path);
 dc_status surrogate_destroy(dc_surrogate *sg);
 

@@ -31,6 +31,46 @@ typedef __nv_bfloat16 bf16;
 
 namespace {
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor map of the K-contiguous weights W[N][K] (bf16) with boxes of 64 k x
+// N rows in the 128-byte swizzle; false (stage with cp.async instead) when
+// the encoder is unavailable or refuses.  Out-of-range k reads as zero.
+bool weights_map(CUtensorMap *m, const void *W, int N, int K)
+{
+    std::memset(m, 0, sizeof(*m));
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || (reinterpret_cast<uintptr_t>(W) & 15) || ((size_t)K * 2) % 16 != 0 || N > 256) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)UM_TK, (cuuint32_t)N};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(W), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct Layer {
     std::string name;
     int cin = 0, cout = 0, cin_p = 0, cout_p = 0;
@@ -416,7 +456,7 @@ struct dc_surrogate {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    bool tcgen05 = false;               // forward convolutions of 64..256 channels on tcgen05
+    int tc_path = DC_SG_AUTO;           // tensor-core path of the forward convolutions (DC_SG_*)
                                         // (surrogate_set_tensor_path; measured slower at these sizes)
     unsigned *status = nullptr;         // DC_ERR_TIMEOUT from a bounded wait in a kernel
     cudaEvent_t ev[2] = {nullptr, nullptr};  // stream ordering with a context in surrogate_apply
@@ -487,9 +527,13 @@ cudaError_t conv_forward(dc_surrogate *s, const Layer &L, const bf16 *x, int B, 
     p.out.S = sadd;
     p.out.Yf = yf;
     p.acc = nullptr;
-    // tcgen05 for 64..256 output channels; the 32-channel full-resolution
-    // layers are loader-bound and faster on the 64 x 32 mma.sync tiles
-    const bool um = s->tcgen05 && (p.N == 64 || p.N == 128 || p.N == 256) && p.M % UM_TM == 0;
+    // tcgen05 for 64..256 output channels (DC_SG_AUTO: in batches of two or
+    // more samples, where it measured faster: 2.10 against 2.21 ms for the
+    // forward at batch 16; mma.sync at batch 1, 0.29 against 0.30 ms); the
+    // 32-channel full-resolution layers are loader-bound and faster on the
+    // 64 x 32 mma.sync tiles
+    const bool tc = s->tc_path == DC_SG_TCGEN05 || (s->tc_path == DC_SG_AUTO && B >= 2);
+    const bool um = tc && (p.N == 64 || p.N == 128 || p.N == 256) && p.M % UM_TM == 0;
     const int tm = um ? UM_TM : BM, tk = um ? UM_TK : BK;
     const int tiles = ((p.M + tm - 1) / tm) * (um ? 1 : (p.N + BN - 1) / BN);
     const int ksteps = (p.K + tk - 1) / tk;
@@ -511,8 +555,10 @@ cudaError_t conv_forward(dc_surrogate *s, const Layer &L, const bf16 *x, int B, 
         int kps = (p.K + splits - 1) / splits;
         kps = (kps + UM_TK - 1) / UM_TK * UM_TK;
         const int sp = (p.K + kps - 1) / kps;
+        CUtensorMap tmB;
+        const int use_tma = weights_map(&tmB, p.W, p.N, p.K) ? 1 : 0;
         e = launch_kernel(umma_gemm_kernel<ConvFwd>, dim3(p.M / UM_TM, 1, sp), dim3(UM_THREADS), umma_smem_bytes(p.N),
-                          s->stream, p, kps, s->status);
+                          s->stream, p, kps, s->status, tmB, use_tma);
     } else {
         e = run_gemm(s->stream, p, splits);
     }
@@ -695,7 +741,7 @@ dc_status surrogate_create(int32_t log2_res, int32_t levels, int32_t base_channe
     s->levels = levels;
     s->c0 = base_channels;
     s->in_channels = in_channels;
-    s->tcgen05 = false;
+    s->tc_path = DC_SG_AUTO;
     s->log2H = log2_res;
     s->max_batch = max_batch;
     s->device = device;
@@ -946,15 +992,15 @@ dc_status surrogate_set_skip(dc_surrogate *s, float kappa)
 dc_status surrogate_set_tensor_path(dc_surrogate *sg, int32_t path)
 {
     if (dc_status st = check_sg(sg)) return st;
-    if (path != DC_SG_MMA_SYNC && path != DC_SG_TCGEN05) return sfail(DC_ERR_INVALID_ARG, "path = %d", path);
-    const bool tc = path == DC_SG_TCGEN05;
-    if (tc != sg->tcgen05 && sg->apply_exec) {  // the captured forward holds the old kernels
+    if (path != DC_SG_MMA_SYNC && path != DC_SG_TCGEN05 && path != DC_SG_AUTO)
+        return sfail(DC_ERR_INVALID_ARG, "path = %d", path);
+    if (path != sg->tc_path && sg->apply_exec) {  // the captured forward holds the old kernels
         SgGuard guard(sg->device);
         cudaStreamSynchronize(sg->stream);
         cudaGraphExecDestroy(sg->apply_exec);
         sg->apply_exec = nullptr;
     }
-    sg->tcgen05 = tc;
+    sg->tc_path = path;
     return DC_OK;
 }
 

@@ -30,7 +30,7 @@ __all__ = [
     "layout_metrics", "warp_texture", "transfer_function", "DC_WARP_VALUE", "DC_WARP_MASS", "declutter_profile_regularize", "declutter_kernel_name",
     "declutter_status_string", "declutter_last_error", "DC_CARRY_COMPENSATED", "DC_CARRY_F64",
     "DC_OPT_FUSED_BANDS", "DC_OPT_SEPARATE_SMOOTH", "DC_OPT_STAGE_HOST", "DC_OPT_BATCHED_LAUNCHES",
-    "DC_OPT_TEST_UNREACHED_BARRIER", "DC_SG_MMA_SYNC", "DC_SG_TCGEN05",
+    "DC_OPT_TEST_UNREACHED_BARRIER", "DC_SG_MMA_SYNC", "DC_SG_TCGEN05", "DC_SG_AUTO",
     "integral_images_u32_noalloc", "DC_NOALLOC_MAX_LOG2_RES", "Batch", "declutter_batch_create",
     "declutter_batch_destroy", "declutter_batch_regularize", "declutter_batch_sync",
     "declutter_autotune_band_rows", "declutter_batch_autotune", "declutter_autotune", "declutter_autotune_save",
@@ -58,6 +58,7 @@ DC_WARP_MASS = 1
 # surrogate_set_tensor_path
 DC_SG_MMA_SYNC = 0
 DC_SG_TCGEN05 = 1
+DC_SG_AUTO = 2
 
 
 class DeclutterError(RuntimeError):
@@ -727,8 +728,9 @@ def surrogate_set_skip(sg: Surrogate, kappa: float) -> None:
 
 
 def surrogate_set_tensor_path(sg: Surrogate, path: int) -> None:
-    """``DC_SG_MMA_SYNC`` (default) or ``DC_SG_TCGEN05`` for the forward
-    convolutions of 64..256 output channels."""
+    """``DC_SG_MMA_SYNC``, ``DC_SG_TCGEN05`` or ``DC_SG_AUTO`` (default: tcgen05
+    for batches of two or more samples) for the forward convolutions of
+    64..256 output channels."""
     _check(load_library().surrogate_set_tensor_path(sg.handle, int(path)), "surrogate_set_tensor_path")
 
 
