@@ -721,6 +721,32 @@ def run_ncu_inim(args):
     dc.declutter_destroy(ctx)
 
 
+def run_ncu_surrogate(args):
+    """Minimal run for profiler captures of the surrogate's forward
+    convolutions: the 4-level 32..256-channel network at 256^2 (seeded
+    initial weights, random inputs), warm-up plus --steps forward passes at
+    batch 16 on the default tensor-core path."""
+    import torch
+
+    from paper_2408_06513_gb300 import build as dc_build
+    from paper_2408_06513_gb300 import declutter as dc
+    dc_build.build()
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(3)
+    B = 16
+    d = torch.rand(B, 256, 256, device=dev, generator=g)
+    sc = torch.ones(B, device=dev)
+    f = torch.randn(B, 256, 256, 2, device=dev, generator=g)
+    out = torch.empty(B, 256, 256, 2, device=dev)
+    sg = dc.surrogate_create(8, 4, 32, max_batch=B, seed=1, device=0, in_channels=3)
+    try:
+        for _ in range(args.warmup + args.steps):
+            dc.surrogate_forward(sg, d, sc, out, field=f)
+        torch.cuda.synchronize()
+    finally:
+        dc.surrogate_destroy(sg)
+
+
 def run_lens(args, dc, dev, stream, flush, reps: int = 15):
     """Virtual lens (end of Sec. 3.2): lens_field() on a painted density
     (constant outside, rectangles of other constants inside) at 512^2 and
@@ -1062,6 +1088,9 @@ def main():
     ap.add_argument("--ncu-inim", type=int, default=0, metavar="LOG2",
                     help="profiler capture of the standalone integral images of a 2^LOG2 grid: "
                          "warm-up plus --steps launches, no bench line")
+    ap.add_argument("--ncu-surrogate", action="store_true",
+                    help="profiler capture of the surrogate's forward at batch 16: warm-up plus --steps passes, "
+                         "no bench line")
     ap.add_argument("--ncu-run", action="store_true",
                     help="only warm-up and timed steps (for profiler captures); prints no bench line")
     args = ap.parse_args()
@@ -1073,6 +1102,8 @@ def main():
     try:
         if args.ncu_inim:
             run_ncu_inim(args)
+        elif args.ncu_surrogate:
+            run_ncu_surrogate(args)
         elif args.impl == "reference":
             run_reference(args, world, rank)
         else:
